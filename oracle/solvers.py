@@ -1,0 +1,90 @@
+"""Oracle linear and nonlinear solvers.
+
+TEST INFRASTRUCTURE ONLY (see the package header).
+
+* ``pcg``: textbook preconditioned conjugate gradients with a Jacobi (diagonal) preconditioner,
+  stopping on ||r||_2 / ||b||_2 <= rtol. With ``mean_zero`` the right-hand side and the result
+  are projected to discrete mean zero (pure-Neumann pressure, reading R7).
+* ``dirichlet``: row/column elimination with identity rows for velocity (H^1_0, Sec. 4).
+* ``direct`` and ``gmres``: library sparse LU (SuperLU) and GMRES used as solver steps.
+* ``newton``: plain Newton on the CH residual (Appendix A uses Newton; Sec. 6.2 reports one
+  iteration at the time steps used).
+
+Pins: pcg against sparse LU on SPD systems; dirichlet elimination against a reduced solve
+(tests/test_oracle_solvers.py).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+
+def pcg(A, b, x0=None, rtol=1e-8, maxit=100000, diag=None, mean_zero=False):
+    """Jacobi-PCG. Returns (x, iterations, final relative residual)."""
+    b = np.asarray(b, dtype=np.float64).copy()
+    if mean_zero:
+        b -= b.mean()
+    x = np.zeros_like(b) if x0 is None else np.asarray(x0, dtype=np.float64).copy()
+    dinv = 1.0 / (A.diagonal() if diag is None else diag)
+    r = b - A @ x
+    bn = np.linalg.norm(b)
+    if bn == 0.0:
+        return np.zeros_like(b), 0, 0.0
+    z = dinv * r
+    p = z.copy()
+    rz = r @ z
+    it = 0
+    rel = np.linalg.norm(r) / bn
+    while rel > rtol and it < maxit:
+        Ap = A @ p
+        alpha = rz / (p @ Ap)
+        x += alpha * p
+        r -= alpha * Ap
+        z = dinv * r
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+        it += 1
+        rel = np.linalg.norm(r) / bn
+    if mean_zero:
+        x -= x.mean()
+    return x, it, rel
+
+
+def dirichlet(A, b, mask, g=None):
+    """Eliminate Dirichlet rows/columns (mask True) with data g (default 0): returns (A', b')
+    with identity rows on the boundary and the known columns moved to the right-hand side."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    g = np.zeros(n) if g is None else np.asarray(g, dtype=np.float64)
+    keep = (~mask).astype(np.float64)
+    Dk = sp.diags(keep)
+    b2 = keep * (b - A @ (g * mask)) + mask * g
+    A2 = Dk @ A @ Dk + sp.diags(mask.astype(np.float64))
+    return A2.tocsr(), b2
+
+
+def direct(A, b):
+    return spla.spsolve(sp.csc_matrix(A), b)
+
+
+def gmres(A, b, x0=None, rtol=1e-12, restart=50, maxiter=2000):
+    M = sp.diags(1.0 / A.diagonal())
+    x, info = spla.gmres(A, b, x0=x0, rtol=rtol, atol=0.0, restart=restart, maxiter=maxiter, M=M)
+    if info != 0:
+        raise RuntimeError(f"gmres did not converge (info={info})")
+    return x
+
+
+def newton(residual, jacobian, x0, rtol=1e-10, atol=1e-13, maxit=20, linsolve=direct):
+    """Plain Newton: x <- x - J(x)^{-1} F(x) until ||F|| <= max(rtol ||F(x0)||, atol)."""
+    x = np.asarray(x0, dtype=np.float64).copy()
+    F = residual(x)
+    f0 = np.linalg.norm(F)
+    its = 0
+    while np.linalg.norm(F) > max(rtol * f0, atol) and its < maxit:
+        x = x - linsolve(jacobian(x), F)
+        F = residual(x)
+        its += 1
+    return x, its, float(np.linalg.norm(F))
