@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark: pressure-Poisson PCG throughput (DOFs/s) and time per CHNS step on one GB300.
+
+Workload: the rising-drop octree (levels 5..8, refined where |phi| < 0.9 around a drop of radius
+0.15 at (0.5, 0.5, 0.3), Cn = 0.01, density ratio 1000, viscosity ratio 100, Re 35, We 1, Fr 1,
+dt 5e-4), seeded synthetic fields. One bench step = one chns_step (two blocks of CH Newton,
+velocity prediction, pressure Poisson, velocity update) to relative residual 1e-8.
+
+value       = n_nodes x (Poisson solves in the timed steps) / (their device time), for the headline
+              path: FP32 Krylov iterations with BF16 coefficient storage inside FP64 refinement;
+plain_fp64  = the same numbers for the all-FP64 path on the same GPU;
+e2e         = one Poisson solve through the C ABI from pinned host buffers (copies timed);
+roofline    = the dominant apply kernel timed alone from a cold L2 (algorithmic bytes / time);
+cpu_baseline= the FP64 CPU oracle (assembled matrix + Jacobi-PCG) on a bounded sample.
+
+Under torchrun (N > 1) every rank runs an independent replica (the method is not sharded) and
+value sums the replicas; timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poisson+PCG DOFs/s and time/step vs plain FP64 GPU at 1e-8 residual; HBM frac"
+UNIT = "DOFs/s"
+WORKLOAD = "rising_drop_levels5-8"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if s[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from chns_workloads import configs
+    from paper_2107_05123_gb300 import capi
+    from paper_2107_05123_gb300.session import DeviceState, Mesh, default_step_params
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    w = configs.rising_drop(5, 8)
+    mesh = Mesh(w.anchors, w.levels, w.extent)
+    N = mesh.n_nodes
+    f0 = w.init(mesh.node_xyz)
+    prm_d = w.params.as_dict()
+    prm = capi.make_params(prm_d)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def flush_l2():
+        flush.fill_(1.0)
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    def run_path(inner, label):
+        ds = DeviceState(dict(phi=f0["phi"], mu=f0["mu"], u=f0["u"], p=f0["p"]))
+        sp = default_step_params(rtol=1e-8, inner=inner, pp_check_every=8)
+        for _ in range(args.warmup):
+            capi.chns_step(mesh.handle, ds.c, prm, sp)
+        step_ms, pp_ms, pp_n, pp_it, stats = [], 0.0, 0, 0, []
+        l0 = capi.chns_kernel_launches()
+        for _ in range(args.steps):
+            flush_l2()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = capi.chns_step(mesh.handle, ds.c, prm, sp)
+            e1.record()
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            for l in range(2):
+                pp_ms += st.pp[l].ms
+                pp_n += 1
+                pp_it += st.pp[l].iterations
+            stats.append(st)
+        launches = capi.chns_kernel_launches() - l0
+        tot_ms = sum(step_ms)
+        tmax = tot_ms
+        if pg:
+            t = torch.tensor([tot_ms, pp_ms], device="cuda", dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            tmax, pp_ms = float(t[0]), float(t[1])
+        last = stats[-1]
+        return dict(label=label, ms_per_step=tmax / args.steps,
+                    value=ws * N * pp_n / (pp_ms * 1e-3),
+                    pp_ms_per_solve=pp_ms / pp_n, pp_iters_per_solve=pp_it / pp_n,
+                    launches=launches,
+                    phases_ms=dict(ch=last.ms_ch, vp=last.ms_vp, pp=last.ms_pp, vu=last.ms_vu),
+                    newton_its=list(last.newton_its),
+                    mass_drift=abs(last.phi_mass_after - last.phi_mass_before),
+                    pp_refinements=last.pp[1].refinements)
+
+    with ClockSampler(local) as clk:
+        headline = run_path(capi.FP32_BF16COEF, "fp32_bf16coef_fp64refine")
+        plain = run_path(capi.FP64, "fp64")
+    clocks = clk.summary()
+
+    # ---- roofline of the dominant kernel: the matrix-free Poisson apply of the headline path,
+    # timed alone from a cold L2 on the launching stream.
+    stream = torch.cuda.current_stream()
+    phit = torch.as_tensor(f0["phi"], device="cuda")
+    coef16 = phit.to(torch.bfloat16)
+    x32 = torch.randn(N, device="cuda", dtype=torch.float32)
+    y32 = torch.empty_like(x32)
+    c16 = capi.make_coef(coef16)
+    times = []
+    for i in range(13):
+        flush_l2()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        capi.chns_apply_poisson(mesh.handle, prm, c16, x32, y32, capi.FP32_BF16COEF, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= 3:
+            times.append(e0.elapsed_time(e1))
+    t_apply = statistics.mean(times) * 1e-3
+    E, H = mesh.n_elem, mesh.n_hanging
+    # algorithmic bytes: x read + y written (4 B each per node), phi~ (2 B per node), the
+    # element table (8 x int32 + level byte per element), the hanging table (16 B per entry)
+    alg_bytes = N * (4 + 4 + 2) + E * 33 + H * 16
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / t_apply / 1e9
+    traffic = args.traffic  # dram bytes per launch from an ncu capture, when supplied
+
+    # ---- end to end: one Poisson solve through the C ABI with pinned host buffers
+    b_dev = torch.zeros(N, dtype=torch.float64, device="cuda")
+    zero3 = [torch.zeros(N, dtype=torch.float64, device="cuda") for _ in range(3)]
+    mu_d = torch.as_tensor(f0["mu"], device="cuda")
+    cpp = capi.make_coef(phit, zero3, mu_d)
+    capi.chns_rhs_poisson(mesh.handle, prm, cpp, zero3, zero3, torch.zeros_like(b_dev), b_dev)
+    b_h = b_dev.cpu().pin_memory()
+    phi_h = phit.cpu().pin_memory()
+    x_h = torch.zeros(N, dtype=torch.float64).pin_memory()
+    bd, xd, pd = torch.empty_like(b_dev), torch.empty_like(b_dev), torch.empty_like(b_dev)
+    solver = capi.make_solver(capi.KSP_CG, capi.PC_JACOBI, 1e-8, 20000, 30, capi.FP32_BF16COEF,
+                              1e-3, 30, check_every=8)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        barrier()
+        t0 = time.perf_counter()
+        bd.copy_(b_h, non_blocking=True)
+        pd.copy_(phi_h, non_blocking=True)
+        xd.zero_()
+        capi.chns_krylov_solve(mesh.handle, capi.OP_POISSON, prm, capi.make_coef(pd), bd, xd,
+                               solver)
+        x_h.copy_(xd, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_val = ws * N / (statistics.mean(e2e_ms) * 1e-3)
+
+    if rank == 0:
+        cpu = cpu_baseline(w, mesh.node_xyz, f0, budget_s=args.cpu_budget) if not args.no_cpu else None
+        line = {
+            "metric": METRIC, "value": headline["value"], "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": headline["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16coef/f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_elem": int(E), "n_nodes": int(N),
+                       "n_hanging": int(H), "rtol": 1e-8, "l2": "flushed before every step",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "plain_fp64": {"value": plain["value"], "ms_per_step": plain["ms_per_step"],
+                           "pp_ms_per_solve": plain["pp_ms_per_solve"],
+                           "pp_iters_per_solve": plain["pp_iters_per_solve"],
+                           "phases_ms": plain["phases_ms"]},
+            "headline_detail": headline,
+            "speedup_vs_plain_fp64": {"pp": headline["value"] / plain["value"],
+                                      "step": plain["ms_per_step"] / headline["ms_per_step"]},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(2 * N * 8),
+                    "d2h_bytes_per_step": int(N * 8)},
+            "roofline": {"kernel": "k_apply<PoissonK<float,bf16>>", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "alg_bytes": int(alg_bytes), "ms": t_apply * 1e3},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": headline["launches"],
+        }
+        print(json.dumps(line))
+    if pg:
+        pg.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def cpu_baseline(w, node_xyz, f0, budget_s=30.0):
+    """Time the oracle's Poisson solve (assembly + Jacobi-PCG to 1e-8) on the same mesh."""
+    import numpy as np
+
+    from oracle import fem, solvers
+    from oracle.mesh import Mesh as OMesh
+
+    t0 = time.perf_counter()
+    om = OMesh(w.anchors, w.levels, w.extent)
+    el, co = fem.Elem(om), fem.Coeffs(w.params.as_dict())
+    N = om.n_nodes
+    z = np.zeros((3, N))
+    vs = fem.VMSState(el, co, f0["phi"], z, f0["mu"])
+    b = fem.pp_rhs(vs, z, z, np.zeros(N))
+    t1 = time.perf_counter()
+    A = fem.poisson(el, co, f0["phi"])
+    t2 = time.perf_counter()
+    x, it, rel = solvers.pcg(A, b, rtol=1e-8, mean_zero=True, maxit=100000)
+    t3 = time.perf_counter()
+    return {"value": N / (t3 - t1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"one pressure-Poisson solve on the same mesh ({N} nodes): scipy CSR "
+                       f"assembly {t2 - t1:.1f} s + Jacobi-PCG {it} its to 1e-8 in {t3 - t2:.1f} s "
+                       f"(value counts assembly + solve; setup {t1 - t0:.1f} s excluded); host "
+                       f"cores {os.cpu_count()}, numpy/scipy single-threaded")}
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+
+    from chns_workloads import configs
+    from oracle import fem, solvers
+    from oracle.mesh import Mesh as OMesh
+
+    w = configs.rising_drop(5, 8)
+    om = OMesh(w.anchors, w.levels, w.extent)
+    f0 = w.init(om.node_xyz)
+    el, co = fem.Elem(om), fem.Coeffs(w.params.as_dict())
+    N = om.n_nodes
+    z = np.zeros((3, N))
+    vs = fem.VMSState(el, co, f0["phi"], z, f0["mu"])
+    b = fem.pp_rhs(vs, z, z, np.zeros(N))
+    times = []
+    its = 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        A = fem.poisson(el, co, f0["phi"])
+        x, its, rel = solvers.pcg(A, b, rtol=1e-8, mean_zero=True, maxit=100000)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    v = N / statistics.mean(times)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_nodes": int(N), "rtol": 1e-8},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": (f"per step: assembly + Jacobi-PCG ({its} its) of one "
+                                    f"pressure-Poisson solve on the full mesh; host cores "
+                                    f"{os.cpu_count()}")},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-budget", type=float, default=30.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the roofline kernel from an ncu capture")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

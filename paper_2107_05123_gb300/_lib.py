@@ -1,0 +1,297 @@
+"""ctypes binding of the C ABI in include/chns.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does nothing but convert
+arguments (numpy host arrays, torch device tensors or raw integer pointers) and raise ChnsError
+on a non-zero status. All computation happens in libchns.so. Importing this module fails loudly
+when the compiled library is missing: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libchns.so")
+
+MAXD = 20
+GMRES_MAX_RESTART = 40
+
+# chns_status
+OK, EINVAL, EUNBALANCED, ENOMEM, ECUDA, ENOTCONV, EBREAKDOWN, ENAN = range(8)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "EUNBALANCED", 3: "ENOMEM", 4: "ECUDA", 5: "ENOTCONV",
+                6: "EBREAKDOWN", 7: "ENAN"}
+# chns_precision
+FP64, FP32, FP32_BF16COEF = 0, 1, 2
+# chns_operator
+OP_POISSON, OP_MASS, OP_CH, OP_MOMENTUM = 0, 1, 2, 3
+OP_NCOMP = {OP_POISSON: 1, OP_MASS: 3, OP_CH: 2, OP_MOMENTUM: 3}
+# chns_ksp / chns_pc
+KSP_CG, KSP_GMRES = 0, 1
+PC_NONE, PC_JACOBI = 0, 1
+
+
+class ChnsError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class chns_mesh_info(C.Structure):
+    _fields_ = [("n_elem", C.c_int64), ("n_nodes", C.c_int64), ("n_hanging", C.c_int64),
+                ("n_boundary", C.c_int64), ("min_level", C.c_int32), ("max_level", C.c_int32),
+                ("extent", C.c_double * 3)]
+
+
+class chns_params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in
+                ("Re", "We", "Cn", "Pe", "Fr", "rho_ratio", "eta_ratio", "dt", "C_I")]
+
+
+class chns_coef(C.Structure):
+    _fields_ = [("phi_tilde", C.c_void_p), ("u_adv", C.c_void_p * 3), ("mu_tilde", C.c_void_p)]
+
+
+class chns_solver_params(C.Structure):
+    _fields_ = [("ksp", C.c_int32), ("pc", C.c_int32), ("rtol", C.c_double),
+                ("max_it", C.c_int32), ("restart", C.c_int32), ("inner_precision", C.c_int32),
+                ("inner_rtol", C.c_double), ("max_refine", C.c_int32),
+                ("check_every", C.c_int32)]
+
+
+class chns_solve_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("refinements", C.c_int32),
+                ("rel_residual", C.c_double), ("b_norm", C.c_double), ("status", C.c_int32),
+                ("ms", C.c_float)]
+
+
+class chns_state(C.Structure):
+    _fields_ = [("phi", C.c_void_p), ("mu", C.c_void_p), ("u", C.c_void_p * 3),
+                ("u_old", C.c_void_p * 3), ("p", C.c_void_p)]
+
+
+class chns_step_params(C.Structure):
+    _fields_ = [("ch", chns_solver_params), ("vp", chns_solver_params),
+                ("pp", chns_solver_params), ("vu", chns_solver_params),
+                ("newton_rtol", C.c_double), ("newton_atol", C.c_double),
+                ("newton_max_it", C.c_int32), ("blocks", C.c_int32)]
+
+
+class chns_step_stats(C.Structure):
+    _fields_ = [("newton_its", C.c_int32 * 2), ("ch", chns_solve_stats * 2),
+                ("vp", chns_solve_stats * 2), ("pp", chns_solve_stats * 2),
+                ("vu", chns_solve_stats * 2), ("phi_mass_before", C.c_double),
+                ("phi_mass_after", C.c_double), ("ms_ch", C.c_float), ("ms_vp", C.c_float),
+                ("ms_pp", C.c_float), ("ms_vu", C.c_float), ("ms_total", C.c_float)]
+
+
+_P = C.c_void_p
+_PP3 = C.POINTER(C.c_void_p)
+_SIGS = {
+    "chns_mesh_create": ([_P, _P, C.c_int64, C.POINTER(C.c_double), _P, C.POINTER(_P)], C.c_int),
+    "chns_mesh_get_info": ([_P, C.POINTER(chns_mesh_info)], C.c_int),
+    "chns_mesh_node_coords": ([_P, _P], C.c_int),
+    "chns_mesh_boundary": ([_P, _P], C.c_int),
+    "chns_mesh_destroy": ([_P], None),
+    "chns_apply_poisson": ([_P, C.POINTER(chns_params), C.POINTER(chns_coef), _P, _P, C.c_int, _P], C.c_int),
+    "chns_apply_mass": ([_P, C.POINTER(chns_params), C.POINTER(chns_coef), _P, _P, C.c_int, _P], C.c_int),
+    "chns_apply_ch": ([_P, C.POINTER(chns_params), C.POINTER(chns_coef), _P, _P, C.c_int, _P], C.c_int),
+    "chns_apply_momentum": ([_P, C.POINTER(chns_params), C.POINTER(chns_coef), _P, _P, C.c_int, _P], C.c_int),
+    "chns_operator_diagonal": ([_P, C.c_int, C.POINTER(chns_params), C.POINTER(chns_coef), _P, C.c_int, _P], C.c_int),
+    "chns_residual_ch": ([_P, C.POINTER(chns_params), _P, _P, _P, _P, _PP3, _P, _P], C.c_int),
+    "chns_rhs_momentum": ([_P, C.POINTER(chns_params), C.POINTER(chns_coef), _PP3, _P, _P, _P], C.c_int),
+    "chns_rhs_poisson": ([_P, C.POINTER(chns_params), C.POINTER(chns_coef), _PP3, _PP3, _P, _P, _P], C.c_int),
+    "chns_rhs_velocity_update": ([_P, C.POINTER(chns_params), C.POINTER(chns_coef), _PP3, _PP3, _P, _P, _P, _P], C.c_int),
+    "chns_phi_mass": ([_P, _P, C.POINTER(C.c_double), _P], C.c_int),
+    "chns_krylov_solve": ([_P, C.c_int, C.POINTER(chns_params), C.POINTER(chns_coef), _P, _P,
+                           C.POINTER(chns_solver_params), C.POINTER(chns_solve_stats), _P], C.c_int),
+    "chns_step": ([_P, C.POINTER(chns_state), C.POINTER(chns_params), C.POINTER(chns_step_params),
+                   C.POINTER(chns_step_stats), _P], C.c_int),
+    "chns_last_error": ([], C.c_char_p),
+    "chns_version": ([], C.c_char_p),
+    "chns_kernel_launches": ([], C.c_uint64),
+}
+DECLARED = tuple(_SIGS)
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2107_05123_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    for name, (args, res) in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+LIB = _load()
+
+
+def _check(st: int, where: str):
+    if st != OK:
+        raise ChnsError(st, where, LIB.chns_last_error().decode())
+
+
+def _ptr(x):
+    """Device/host pointer of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"cannot take the pointer of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _ptr3(xs):
+    arr = (C.c_void_p * 3)(*[_ptr(x) for x in xs])
+    return C.cast(arr, _PP3), arr
+
+
+def make_params(d) -> chns_params:
+    return chns_params(*[float(d[k]) for k in
+                         ("Re", "We", "Cn", "Pe", "Fr", "rho_ratio", "eta_ratio", "dt", "C_I")])
+
+
+def make_coef(phi=None, u=(None, None, None), mu=None) -> chns_coef:
+    return chns_coef(_ptr(phi), (C.c_void_p * 3)(*[_ptr(x) for x in u]), _ptr(mu))
+
+
+def make_solver(ksp=KSP_CG, pc=PC_JACOBI, rtol=1e-8, max_it=10000, restart=30,
+                inner_precision=FP64, inner_rtol=1e-3, max_refine=20, check_every=1):
+    return chns_solver_params(ksp, pc, rtol, max_it, restart, inner_precision, inner_rtol,
+                              max_refine, check_every)
+
+
+# ------------------------------------------------------------------ mesh
+def chns_mesh_create(anchors, levels, extent=(1.0, 1.0, 1.0), stream=None):
+    a = np.ascontiguousarray(anchors, dtype=np.uint32).reshape(-1, 3)
+    lv = np.ascontiguousarray(levels, dtype=np.uint8).reshape(-1)
+    ext = (C.c_double * 3)(*[float(e) for e in extent])
+    out = C.c_void_p()
+    _check(LIB.chns_mesh_create(a.ctypes.data, lv.ctypes.data, len(lv), ext, _stream(stream),
+                                C.byref(out)), "chns_mesh_create")
+    return out.value
+
+
+def chns_mesh_get_info(mesh) -> chns_mesh_info:
+    info = chns_mesh_info()
+    _check(LIB.chns_mesh_get_info(mesh, C.byref(info)), "chns_mesh_get_info")
+    return info
+
+
+def chns_mesh_node_coords(mesh, n_nodes: int) -> np.ndarray:
+    out = np.zeros((n_nodes, 3), dtype=np.uint32)
+    _check(LIB.chns_mesh_node_coords(mesh, out.ctypes.data), "chns_mesh_node_coords")
+    return out
+
+
+def chns_mesh_boundary(mesh, n_nodes: int) -> np.ndarray:
+    out = np.zeros(n_nodes, dtype=np.uint8)
+    _check(LIB.chns_mesh_boundary(mesh, out.ctypes.data), "chns_mesh_boundary")
+    return out
+
+
+def chns_mesh_destroy(mesh):
+    LIB.chns_mesh_destroy(mesh)
+
+
+# ------------------------------------------------------------------ operators
+def _apply(name, mesh, prm, coef, x, y, prec, stream):
+    _check(getattr(LIB, name)(mesh, C.byref(prm), C.byref(coef), _ptr(x), _ptr(y), prec,
+                              _stream(stream)), name)
+
+
+def chns_apply_poisson(mesh, prm, coef, x, y, prec=FP64, stream=None):
+    _apply("chns_apply_poisson", mesh, prm, coef, x, y, prec, stream)
+
+
+def chns_apply_mass(mesh, prm, coef, x, y, prec=FP64, stream=None):
+    _apply("chns_apply_mass", mesh, prm, coef, x, y, prec, stream)
+
+
+def chns_apply_ch(mesh, prm, coef, x, y, prec=FP64, stream=None):
+    _apply("chns_apply_ch", mesh, prm, coef, x, y, prec, stream)
+
+
+def chns_apply_momentum(mesh, prm, coef, x, y, prec=FP64, stream=None):
+    _apply("chns_apply_momentum", mesh, prm, coef, x, y, prec, stream)
+
+
+def chns_operator_diagonal(mesh, op, prm, coef, d, prec=FP64, stream=None):
+    _check(LIB.chns_operator_diagonal(mesh, op, C.byref(prm), C.byref(coef), _ptr(d), prec,
+                                      _stream(stream)), "chns_operator_diagonal")
+
+
+def chns_residual_ch(mesh, prm, phi, mu, phik, muk, u, f, stream=None):
+    up, keep = _ptr3(u)
+    _check(LIB.chns_residual_ch(mesh, C.byref(prm), _ptr(phi), _ptr(mu), _ptr(phik), _ptr(muk),
+                                up, _ptr(f), _stream(stream)), "chns_residual_ch")
+
+
+def chns_rhs_momentum(mesh, prm, coef, uk, pk, b, stream=None):
+    up, keep = _ptr3(uk)
+    _check(LIB.chns_rhs_momentum(mesh, C.byref(prm), C.byref(coef), up, _ptr(pk), _ptr(b),
+                                 _stream(stream)), "chns_rhs_momentum")
+
+
+def chns_rhs_poisson(mesh, prm, coef, v, uk, pk, b, stream=None):
+    vp, k1 = _ptr3(v)
+    up, k2 = _ptr3(uk)
+    _check(LIB.chns_rhs_poisson(mesh, C.byref(prm), C.byref(coef), vp, up, _ptr(pk), _ptr(b),
+                                _stream(stream)), "chns_rhs_poisson")
+
+
+def chns_rhs_velocity_update(mesh, prm, coef, v, uk, pk, pn, b, stream=None):
+    vp, k1 = _ptr3(v)
+    up, k2 = _ptr3(uk)
+    _check(LIB.chns_rhs_velocity_update(mesh, C.byref(prm), C.byref(coef), vp, up, _ptr(pk),
+                                        _ptr(pn), _ptr(b), _stream(stream)),
+           "chns_rhs_velocity_update")
+
+
+def chns_phi_mass(mesh, phi, stream=None) -> float:
+    out = C.c_double()
+    _check(LIB.chns_phi_mass(mesh, _ptr(phi), C.byref(out), _stream(stream)), "chns_phi_mass")
+    return out.value
+
+
+def chns_krylov_solve(mesh, op, prm, coef, b, x, solver, stream=None, check=True):
+    st = chns_solve_stats()
+    rc = LIB.chns_krylov_solve(mesh, op, C.byref(prm), C.byref(coef), _ptr(b), _ptr(x),
+                               C.byref(solver), C.byref(st), _stream(stream))
+    if check:
+        _check(rc, "chns_krylov_solve")
+    return st
+
+
+def chns_step(mesh, state: chns_state, prm, step_params, stream=None) -> chns_step_stats:
+    st = chns_step_stats()
+    _check(LIB.chns_step(mesh, C.byref(state), C.byref(prm), C.byref(step_params), C.byref(st),
+                         _stream(stream)), "chns_step")
+    return st
+
+
+def chns_version() -> str:
+    return LIB.chns_version().decode()
+
+
+def chns_kernel_launches() -> int:
+    return int(LIB.chns_kernel_launches())

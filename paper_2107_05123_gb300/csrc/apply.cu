@@ -1,0 +1,314 @@
+// Matrix-free operator applies and exact operator diagonals.
+//
+// One thread per leaf element, elements in Morton order so that neighbouring threads share most
+// of their nodes in cache. Each thread gathers its 8 corner values (hanging corners interpolated
+// from their parents), applies the element operator with 2x2x2 Gauss quadrature and geometry
+// recomputed from the octant level, and scatter-adds the result (hanging corners distributed
+// back to their parents), i.e. y = P^T (sum_e A_e) P x without storing any matrix.
+#include "ops.cuh"
+
+namespace chns {
+
+constexpr int kApplyThreads = 128;
+
+template <class K, class T, class S, class C>
+__global__ void __launch_bounds__(kApplyThreads) k_apply(MeshDev m, DevParams p, CoefArgs<C> cf,
+                                                         const S* __restrict__ x, S* __restrict__ y) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.n_elem) return;
+  int idx[8];
+  load_corners(m, e, idx);
+  const Geo<T> g = geometry<T>(m, e);
+  K k;
+  k.load(m, p, cf, idx, g);
+  T xin[K::NC][8];
+#pragma unroll
+  for (int c = 0; c < K::NC; ++c) gather<T, K::DIR>(m, idx, x + c * m.n_nodes, xin[c]);
+  T r[K::NC][8];
+  k.apply(g, p, xin, r);
+#pragma unroll
+  for (int c = 0; c < K::NC; ++c) scatter<T, K::DIR>(m, idx, r[c], y + c * m.n_nodes);
+}
+
+// Reference (corner a, slot k) -> node reference with Dirichlet bit and its weight, or -1.
+__device__ __forceinline__ int corner_ref(const MeshDev& m, int v, int k, double& w) {
+  int j = v & kIdxMask;
+  if (j < m.n_nodes) {
+    w = 1.0;
+    return k == 0 ? v : -1;
+  }
+  int4 h = m.hang[j - m.n_nodes];
+  bool four = h.z >= 0;
+  w = four ? 0.25 : 0.5;
+  int r = k == 0 ? h.x : k == 1 ? h.y : k == 2 ? h.z : h.w;
+  return (k >= 2 && !four) ? -1 : r;
+}
+
+// Exact diagonal of P^T (sum_e A_e) P: for every node j touching the element (as a corner or as a
+// hanging-node parent), apply A_e to the local vector of j's basis function and take its j part.
+template <class K, class T, class S, class C>
+__global__ void __launch_bounds__(kApplyThreads) k_diag(MeshDev m, DevParams p, CoefArgs<C> cf,
+                                                        S* __restrict__ d) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.n_elem) return;
+  int idx[8];
+  load_corners(m, e, idx);
+  const Geo<T> g = geometry<T>(m, e);
+  K k;
+  k.load(m, p, cf, idx, g);
+  for (int a = 0; a < 8; ++a) {
+    for (int s = 0; s < 4; ++s) {
+      double w;
+      int ref = corner_ref(m, idx[a], s, w);
+      if (ref < 0) continue;
+      if (K::DIR && (ref & kDirBit)) continue;
+      const int j = ref & kIdxMask;
+      // first occurrence only
+      bool seen = false;
+      for (int a2 = 0; a2 <= a && !seen; ++a2)
+        for (int s2 = 0; s2 < 4; ++s2) {
+          if (a2 == a && s2 >= s) break;
+          double w2;
+          int r2 = corner_ref(m, idx[a2], s2, w2);
+          if (r2 >= 0 && (r2 & kIdxMask) == j) {
+            seen = true;
+            break;
+          }
+        }
+      if (seen) continue;
+      T lv[8];
+      for (int b = 0; b < 8; ++b) {
+        T acc = T(0);
+        for (int s2 = 0; s2 < 4; ++s2) {
+          double w2;
+          int r2 = corner_ref(m, idx[b], s2, w2);
+          if (r2 >= 0 && (r2 & kIdxMask) == j) acc += T(w2);
+        }
+        lv[b] = acc;
+      }
+      const int ncd = K::DIAG_PER_COMP ? K::NC : 1;
+      for (int c = 0; c < ncd; ++c) {
+        T xin[K::NC][8], r[K::NC][8];
+        for (int c2 = 0; c2 < K::NC; ++c2)
+          for (int b = 0; b < 8; ++b) xin[c2][b] = c2 == c ? lv[b] : T(0);
+        k.apply(g, p, xin, r);
+        T dv = T(0);
+        for (int b = 0; b < 8; ++b) dv += lv[b] * r[c][b];
+        if (K::DIAG_PER_COMP) {
+          atomic_add(d + c * m.n_nodes + j, (S)dv);
+        } else {
+          for (int c2 = 0; c2 < K::NC; ++c2) atomic_add(d + c2 * m.n_nodes + j, (S)dv);
+        }
+      }
+    }
+  }
+}
+
+// Dirichlet rows: y[c*N + j] = x[c*N + j] (identity) for boundary nodes j.
+template <class S>
+__global__ void k_dirichlet_copy(const int32_t* __restrict__ bnd, int64_t nb, int64_t N, int nc,
+                                 const S* __restrict__ x, S* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nb * nc) return;
+  const int64_t c = i / nb, j = bnd[i % nb];
+  y[c * N + j] = x ? x[c * N + j] : S(1);
+}
+
+int op_ncomp(chns_operator op) {
+  switch (op) {
+    case CHNS_OP_POISSON: return 1;
+    case CHNS_OP_MASS: return 3;
+    case CHNS_OP_CH: return 2;
+    case CHNS_OP_MOMENTUM: return 3;
+  }
+  return 0;
+}
+bool op_dirichlet(chns_operator op) { return op == CHNS_OP_MASS || op == CHNS_OP_MOMENTUM; }
+
+template <class C>
+static CoefArgs<C> coef_args(const chns_coef* c) {
+  CoefArgs<C> a;
+  a.phi = static_cast<const C*>(c->phi_tilde);
+  for (int d = 0; d < 3; ++d) a.u[d] = static_cast<const C*>(c->u_adv[d]);
+  a.mu = static_cast<const C*>(c->mu_tilde);
+  return a;
+}
+
+static chns_status check_coef(chns_operator op, const chns_coef* c) {
+  CHNS_CHECK(c && c->phi_tilde, CHNS_EINVAL, "coefficient phi_tilde is required");
+  if (op == CHNS_OP_CH || op == CHNS_OP_MOMENTUM)
+    CHNS_CHECK(c->u_adv[0] && c->u_adv[1] && c->u_adv[2], CHNS_EINVAL,
+               "coefficient u_adv[3] is required");
+  if (op == CHNS_OP_MOMENTUM) CHNS_CHECK(c->mu_tilde, CHNS_EINVAL, "coefficient mu_tilde is required");
+  return CHNS_OK;
+}
+
+template <class T, class S, class C>
+static void launch_apply(const chns_mesh* m, chns_operator op, const DevParams& p,
+                         const CoefArgs<C>& cf, const S* x, S* y, cudaStream_t s) {
+  const int64_t E = m->d.n_elem;
+  const unsigned nb = (unsigned)((E + kApplyThreads - 1) / kApplyThreads);
+  switch (op) {
+    case CHNS_OP_POISSON:
+      note_launch();
+      k_apply<PoissonK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cf, x, y);
+      break;
+    case CHNS_OP_MASS:
+      note_launch();
+      k_apply<MassK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cf, x, y);
+      break;
+    case CHNS_OP_CH:
+      note_launch();
+      k_apply<ChK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cf, x, y);
+      break;
+    case CHNS_OP_MOMENTUM:
+      note_launch();
+      k_apply<MomK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cf, x, y);
+      break;
+  }
+}
+
+template <class T, class S, class C>
+static void launch_diag(const chns_mesh* m, chns_operator op, const DevParams& p,
+                        const CoefArgs<C>& cf, S* d, cudaStream_t s) {
+  const int64_t E = m->d.n_elem;
+  const unsigned nb = (unsigned)((E + kApplyThreads - 1) / kApplyThreads);
+  switch (op) {
+    case CHNS_OP_POISSON:
+      note_launch();
+      k_diag<PoissonK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cf, d);
+      break;
+    case CHNS_OP_MASS:
+      note_launch();
+      k_diag<MassK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cf, d);
+      break;
+    case CHNS_OP_CH:
+      note_launch();
+      k_diag<ChK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cf, d);
+      break;
+    case CHNS_OP_MOMENTUM:
+      note_launch();
+      k_diag<MomK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cf, d);
+      break;
+  }
+}
+
+template <class S>
+static chns_status dirichlet_rows(const chns_mesh* m, int nc, const S* x, S* y, cudaStream_t s) {
+  if (m->n_boundary == 0) return CHNS_OK;
+  const int64_t n = m->n_boundary * nc;
+  note_launch();
+  k_dirichlet_copy<S><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m->d_bnd, m->n_boundary,
+                                                                  m->d.n_nodes, nc, x, y);
+  return CHNS_OK;
+}
+
+chns_status apply_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
+                     const chns_coef* coef, const void* x, void* y, chns_precision prec,
+                     cudaStream_t s) {
+  CHNS_CHECK(m && prm && x && y, CHNS_EINVAL, "apply: null argument");
+  CHNS_CHECK(op >= CHNS_OP_POISSON && op <= CHNS_OP_MOMENTUM, CHNS_EINVAL, "apply: bad operator");
+  CHNS_CHECK(x != y, CHNS_EINVAL, "apply: x and y must not alias");
+  chns_status st = check_coef(op, coef);
+  if (st != CHNS_OK) return st;
+  const DevParams p = make_dev_params(*prm);
+  const int nc = op_ncomp(op);
+  const int64_t n = nc * m->d.n_nodes;
+  switch (prec) {
+    case CHNS_FP64: {
+      CHNS_CUDA(cudaMemsetAsync(y, 0, n * sizeof(double), s));
+      launch_apply<double, double, double>(m, op, p, coef_args<double>(coef),
+                                           static_cast<const double*>(x), static_cast<double*>(y), s);
+      if (op_dirichlet(op))
+        dirichlet_rows(m, nc, static_cast<const double*>(x), static_cast<double*>(y), s);
+      break;
+    }
+    case CHNS_FP32: {
+      CHNS_CUDA(cudaMemsetAsync(y, 0, n * sizeof(float), s));
+      launch_apply<float, float, float>(m, op, p, coef_args<float>(coef),
+                                        static_cast<const float*>(x), static_cast<float*>(y), s);
+      if (op_dirichlet(op))
+        dirichlet_rows(m, nc, static_cast<const float*>(x), static_cast<float*>(y), s);
+      break;
+    }
+    case CHNS_FP32_BF16COEF: {
+      CHNS_CUDA(cudaMemsetAsync(y, 0, n * sizeof(float), s));
+      launch_apply<float, float, __nv_bfloat16>(m, op, p, coef_args<__nv_bfloat16>(coef),
+                                                static_cast<const float*>(x),
+                                                static_cast<float*>(y), s);
+      if (op_dirichlet(op))
+        dirichlet_rows(m, nc, static_cast<const float*>(x), static_cast<float*>(y), s);
+      break;
+    }
+    default:
+      set_error("apply: bad precision");
+      return CHNS_EINVAL;
+  }
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
+chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
+                    const chns_coef* coef, void* d, chns_precision prec, cudaStream_t s) {
+  CHNS_CHECK(m && prm && d, CHNS_EINVAL, "diagonal: null argument");
+  CHNS_CHECK(op >= CHNS_OP_POISSON && op <= CHNS_OP_MOMENTUM, CHNS_EINVAL, "diagonal: bad operator");
+  chns_status st = check_coef(op, coef);
+  if (st != CHNS_OK) return st;
+  const DevParams p = make_dev_params(*prm);
+  const int nc = op_ncomp(op);
+  const int64_t n = nc * m->d.n_nodes;
+  switch (prec) {
+    case CHNS_FP64:
+      CHNS_CUDA(cudaMemsetAsync(d, 0, n * sizeof(double), s));
+      launch_diag<double, double, double>(m, op, p, coef_args<double>(coef),
+                                          static_cast<double*>(d), s);
+      if (op_dirichlet(op)) dirichlet_rows<double>(m, nc, nullptr, static_cast<double*>(d), s);
+      break;
+    case CHNS_FP32:
+      CHNS_CUDA(cudaMemsetAsync(d, 0, n * sizeof(float), s));
+      launch_diag<float, float, float>(m, op, p, coef_args<float>(coef), static_cast<float*>(d), s);
+      if (op_dirichlet(op)) dirichlet_rows<float>(m, nc, nullptr, static_cast<float*>(d), s);
+      break;
+    case CHNS_FP32_BF16COEF:
+      CHNS_CUDA(cudaMemsetAsync(d, 0, n * sizeof(float), s));
+      launch_diag<float, float, __nv_bfloat16>(m, op, p, coef_args<__nv_bfloat16>(coef),
+                                               static_cast<float*>(d), s);
+      if (op_dirichlet(op)) dirichlet_rows<float>(m, nc, nullptr, static_cast<float*>(d), s);
+      break;
+    default:
+      set_error("diagonal: bad precision");
+      return CHNS_EINVAL;
+  }
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
+}  // namespace chns
+
+using namespace chns;
+
+extern "C" chns_status chns_apply_poisson(const chns_mesh* m, const chns_params* prm,
+                                          const chns_coef* coef, const void* x, void* y,
+                                          chns_precision prec, void* stream) {
+  return apply_op(m, CHNS_OP_POISSON, prm, coef, x, y, prec, as_stream(stream));
+}
+extern "C" chns_status chns_apply_mass(const chns_mesh* m, const chns_params* prm,
+                                       const chns_coef* coef, const void* x, void* y,
+                                       chns_precision prec, void* stream) {
+  return apply_op(m, CHNS_OP_MASS, prm, coef, x, y, prec, as_stream(stream));
+}
+extern "C" chns_status chns_apply_ch(const chns_mesh* m, const chns_params* prm,
+                                     const chns_coef* coef, const void* x, void* y,
+                                     chns_precision prec, void* stream) {
+  return apply_op(m, CHNS_OP_CH, prm, coef, x, y, prec, as_stream(stream));
+}
+extern "C" chns_status chns_apply_momentum(const chns_mesh* m, const chns_params* prm,
+                                           const chns_coef* coef, const void* x, void* y,
+                                           chns_precision prec, void* stream) {
+  return apply_op(m, CHNS_OP_MOMENTUM, prm, coef, x, y, prec, as_stream(stream));
+}
+extern "C" chns_status chns_operator_diagonal(const chns_mesh* m, chns_operator op,
+                                              const chns_params* prm, const chns_coef* coef,
+                                              void* d, chns_precision prec, void* stream) {
+  return diag_op(m, op, prm, coef, d, prec, as_stream(stream));
+}

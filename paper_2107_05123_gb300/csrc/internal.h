@@ -1,0 +1,136 @@
+// Internal declarations of the CHNS library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/chns.h"
+
+namespace chns {
+
+// Element corner indices carry the Dirichlet flag in bit 30; bit 31 is never set.
+constexpr int32_t kDirBit = 1 << 30;
+constexpr int32_t kIdxMask = kDirBit - 1;
+
+// Device view of the mesh tables (passed by value to kernels).
+struct MeshDev {
+  int64_t n_elem;
+  int64_t n_nodes;
+  int64_t n_hang;
+  const int4* enode;     // [n_elem][2] int4 = 8 corner indices: < n_nodes node, else hanging
+  const uint8_t* level;  // [n_elem]
+  const int4* hang;      // [n_hang] parents (with Dirichlet bit); .z=.w=-1 for edge midpoints
+  const uint32_t* anchor;  // [n_elem*3] (only for diagnostics needing positions)
+  double ext[3];         // physical extent
+};
+
+struct Workspace {
+  // FP64 vectors (sized for 3 components) and FP32 mirrors
+  std::vector<double*> v64;
+  std::vector<float*> v32;
+  double* gm_V = nullptr;      // GMRES basis (restart+1) x (3N) doubles
+  float* gm_V32 = nullptr;     // FP32 GMRES basis
+  double* red = nullptr;       // reduction partials + scalars
+  unsigned int* counter = nullptr;
+  double* h_pinned = nullptr;  // pinned host scalars
+  void* coef32 = nullptr;      // reduced-precision coefficient copies (5 fields, float)
+  void* coef16 = nullptr;      // bf16 copies (5 fields)
+  double* coef64 = nullptr;    // FP64 step coefficients (phi~, u_hat x3, mu~ + scratch)
+};
+
+}  // namespace chns
+
+struct chns_mesh {
+  chns::MeshDev d;
+  int min_level = 0, max_level = 0;
+  int64_t n_boundary = 0;
+  std::vector<uint32_t> node_coords;  // host copy, 3*n_nodes
+  std::vector<uint8_t> node_bnd;      // host copy
+  // device allocations
+  int4* d_enode = nullptr;
+  uint8_t* d_level = nullptr;
+  int4* d_hang = nullptr;
+  uint32_t* d_anchor = nullptr;
+  int32_t* d_bnd = nullptr;          // boundary node indices (n_boundary)
+  chns::Workspace ws;
+  int red_blocks = 0;
+  int sm_count = 0;
+};
+
+namespace chns {
+
+void set_error(const std::string& msg);
+// count of kernel launches issued by the library (diagnostic)
+void note_launch();
+chns_status cuda_fail(cudaError_t e, const char* what);
+
+#define CHNS_CUDA(call)                                          \
+  do {                                                           \
+    cudaError_t _e = (call);                                     \
+    if (_e != cudaSuccess) return ::chns::cuda_fail(_e, #call);  \
+  } while (0)
+
+#define CHNS_CHECK(cond, code, msg)      \
+  do {                                   \
+    if (!(cond)) {                       \
+      ::chns::set_error(msg);            \
+      return code;                       \
+    }                                    \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Number of FP64 workspace vectors of 3*n_nodes
+constexpr int kNumVec64 = 16;
+constexpr int kNumVec32 = 10;
+constexpr int kRedSlots = 4096;   // partial sums per reduction
+constexpr int kScalarBase = 3 * 4096;  // scalars stored after three partial arrays
+
+// ---- apply dispatch (apply.cu)
+chns_status apply_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
+                     const chns_coef* coef, const void* x, void* y, chns_precision prec,
+                     cudaStream_t s);
+chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
+                    const chns_coef* coef, void* d, chns_precision prec, cudaStream_t s);
+int op_ncomp(chns_operator op);
+bool op_dirichlet(chns_operator op);
+
+// ---- vector kernels (krylov.cu)
+void vec_convert_f64_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+void vec_convert_f64_bf16(const double* a, __nv_bfloat16* b, int64_t n, cudaStream_t s);
+void vec_axpby(double a, const double* x, double b, const double* y, double* out, int64_t n,
+               cudaStream_t s);
+void vec_copy(const double* x, double* y, int64_t n, cudaStream_t s);
+void vec_zero(double* x, int64_t n, cudaStream_t s);
+// FP64 dot on device; result written to dst (device) as double
+void dot_dev(const chns_mesh* m, const double* a, const double* b, int64_t n, double* dst,
+             cudaStream_t s);
+chns_status dot_host(const chns_mesh* m, const double* a, const double* b, int64_t n, double* out,
+                     cudaStream_t s);
+chns_status sum_host(const chns_mesh* m, const double* a, int64_t n, double* out, cudaStream_t s);
+void vec_add_scalar(double* x, const double* dev_scalar, double factor, int64_t n, cudaStream_t s);
+
+// ---- right-hand sides (rhs.cu)
+chns_status phi_mass(const chns_mesh* m, const double* phi, double* out, cudaStream_t s);
+chns_status residual_ch(const chns_mesh* m, const chns_params* prm, const double* phi,
+                        const double* mu, const double* phik, const double* muk,
+                        const double* const u[3], double* f, cudaStream_t s);
+chns_status rhs_momentum(const chns_mesh* m, const chns_params* prm, const chns_coef* c,
+                         const double* const uk[3], const double* pk, double* b, cudaStream_t s);
+chns_status rhs_poisson(const chns_mesh* m, const chns_params* prm, const chns_coef* c,
+                        const double* const v[3], const double* const uk[3], const double* pk,
+                        double* b, cudaStream_t s);
+chns_status rhs_vu(const chns_mesh* m, const chns_params* prm, const chns_coef* c,
+                   const double* const v[3], const double* const uk[3], const double* pk,
+                   const double* pn, double* b, cudaStream_t s);
+
+// ---- Krylov (krylov.cu)
+chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params* prm,
+                         const chns_coef* coef, const double* b, double* x,
+                         const chns_solver_params* sp, chns_solve_stats* stats, cudaStream_t s);
+
+}  // namespace chns

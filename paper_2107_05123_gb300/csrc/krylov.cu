@@ -1,0 +1,707 @@
+// Krylov solvers on the matrix-free operators: Jacobi-preconditioned CG (pressure Poisson,
+// velocity update) and right-preconditioned restarted GMRES (Cahn-Hilliard Newton steps,
+// velocity prediction). The paper solves these systems with PETSc Krylov methods (Appendix A);
+// here every vector update and every dot product is a fused device kernel, dot products and norms
+// are accumulated in FP64 with a deterministic two-level reduction (per-block partial sums, then
+// a fixed-order sum in the last block), and CG keeps its scalars on the device so that the host
+// only reads the residual norm every `check_every` iterations.
+//
+// Mixed precision: with an FP32 inner precision the Krylov iteration runs on FP32 vectors and FP32
+// (or BF16-coefficient) applies, with FP64 dot products, inside an FP64 iterative-refinement loop
+// whose residual r = b - A_64 x uses the FP64 operator.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace chns {
+
+constexpr int kVecThreads = 256;
+constexpr int kMdBlocks = 256;  // blocks per multi-dot row (partials: rows x kMdBlocks)
+
+// device scalar slots (offsets from ws.red + kScalarBase)
+enum Slot { S_RZ0 = 0, S_RZ1 = 1, S_PQ = 2, S_RR = 3, S_TMP = 8, S_AUX = 16, S_MD = 64 };
+
+// ------------------------------------------------------------------ device kernels
+// Block reduction of NV sums, partials per block, fixed-order final sum in the last block.
+template <int NV>
+__device__ __forceinline__ void reduce_finalize(double v[NV], double* __restrict__ part,
+                                                unsigned* __restrict__ counter,
+                                                double* __restrict__ out) {
+  __shared__ double sh[NV][kVecThreads];
+  __shared__ bool last;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = v[k];
+  __syncthreads();
+  for (int w = kVecThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) part[k * kRedSlots + blockIdx.x] = sh[k][0];
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += kVecThreads)
+      s += ((volatile double*)part)[k * kRedSlots + b];
+    sh[k][threadIdx.x] = s;
+  }
+  __syncthreads();
+  for (int w = kVecThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = sh[k][0];
+    *counter = 0u;
+  }
+}
+
+#define GRID_LOOP(i, n)                                                     \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); \
+       i += (int64_t)gridDim.x * blockDim.x)
+
+template <class A, class B>
+__global__ void __launch_bounds__(kVecThreads)
+k_dot(const A* __restrict__ a, const B* __restrict__ b, int64_t n, double* part, unsigned* counter,
+      double* out) {
+  double v[1] = {0.0};
+  GRID_LOOP(i, n) v[0] += (double)a[i] * (double)b[i];
+  reduce_finalize<1>(v, part, counter, out);
+}
+
+template <class A>
+__global__ void __launch_bounds__(kVecThreads)
+k_sum(const A* __restrict__ a, int64_t n, double* part, unsigned* counter, double* out) {
+  double v[1] = {0.0};
+  GRID_LOOP(i, n) v[0] += (double)a[i];
+  reduce_finalize<1>(v, part, counter, out);
+}
+
+// out = a x + b y
+template <class T>
+__global__ void k_axpby(double a, const T* __restrict__ x, double b, const T* __restrict__ y,
+                        T* __restrict__ out, int64_t n) {
+  const T ta = (T)a, tb = (T)b;
+  GRID_LOOP(i, n) out[i] = ta * x[i] + tb * y[i];
+}
+
+// out (TO) = scale * in (TI)
+template <class TI, class TO>
+__global__ void k_convert(const TI* __restrict__ a, TO* __restrict__ b, int64_t n, double scale) {
+  GRID_LOOP(i, n) b[i] = (TO)((double)a[i] * scale);
+}
+__global__ void k_convert_bf16(const double* __restrict__ a, __nv_bfloat16* __restrict__ b,
+                               int64_t n) {
+  GRID_LOOP(i, n) b[i] = __float2bfloat16_rn((float)a[i]);
+}
+
+// x += factor * s[0]
+template <class T>
+__global__ void k_add_scalar(T* __restrict__ x, const double* __restrict__ s, double factor,
+                             int64_t n) {
+  const T v = (T)(s[0] * factor);
+  GRID_LOOP(i, n) x[i] += v;
+}
+
+// x64 += scale * d
+template <class T>
+__global__ void k_accumulate(double* __restrict__ x, const T* __restrict__ d, double scale,
+                             int64_t n) {
+  GRID_LOOP(i, n) x[i] += scale * (double)d[i];
+}
+
+template <class T>
+__global__ void k_invert(const double* __restrict__ d, T* __restrict__ dinv, int64_t n) {
+  GRID_LOOP(i, n) {
+    double v = d[i];
+    dinv[i] = (T)(v != 0.0 ? 1.0 / v : 1.0);
+  }
+}
+
+// z = dinv * v (dinv may be null: identity)
+template <class T>
+__global__ void k_mul(const T* __restrict__ dinv, const T* __restrict__ v, T* __restrict__ z,
+                      int64_t n) {
+  GRID_LOOP(i, n) z[i] = dinv ? dinv[i] * v[i] : v[i];
+}
+
+// ---- CG: q = A p given. alpha = rz/pq; x += alpha p; r -= alpha q; z = dinv r;
+// partial sums of r.z and r.r land in S_TMP, S_TMP+1.
+template <class T>
+__global__ void __launch_bounds__(kVecThreads)
+k_cg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __restrict__ p,
+            const T* __restrict__ q, const T* __restrict__ dinv, int64_t n, double* __restrict__ S,
+            int parity, double* part, unsigned* counter) {
+  const double rz = S[S_RZ0 + parity], pq = S[S_PQ];
+  const double alpha = (pq > 0.0 && isfinite(pq)) ? rz / pq : 0.0;
+  const T a = (T)alpha;
+  double v[2] = {0.0, 0.0};
+  GRID_LOOP(i, n) {
+    x[i] += a * p[i];
+    const T ri = r[i] - a * q[i];
+    r[i] = ri;
+    const T zi = dinv ? dinv[i] * ri : ri;
+    z[i] = zi;
+    v[0] += (double)ri * (double)zi;
+    v[1] += (double)ri * (double)ri;
+  }
+  reduce_finalize<2>(v, part, counter, S + S_TMP);
+}
+
+// beta = rz_new / rz_old; p = z + beta p; rotate rz into the other parity slot; publish r.r.
+template <class T>
+__global__ void k_cg_pupdate(T* __restrict__ p, const T* __restrict__ z, int64_t n,
+                             double* __restrict__ S, int parity) {
+  const double rz_old = S[S_RZ0 + parity], rz_new = S[S_TMP];
+  const double beta = rz_old != 0.0 ? rz_new / rz_old : 0.0;
+  const T b = (T)beta;
+  GRID_LOOP(i, n) p[i] = z[i] + b * p[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S[S_RZ0 + (parity ^ 1)] = rz_new;
+    S[S_RR] = S[S_TMP + 1];
+  }
+}
+
+// ---- GMRES: multi-dot of rows V_0..V_{nk-1} with w; partials [nk][gridDim.x]
+template <class T>
+__global__ void __launch_bounds__(kVecThreads)
+k_multidot(const T* __restrict__ V, int64_t ld, const T* __restrict__ w, int64_t n,
+           double* __restrict__ part) {
+  __shared__ double sh[kVecThreads];
+  const T* vk = V + (int64_t)blockIdx.y * ld;
+  double s = 0.0;
+  GRID_LOOP(i, n) s += (double)vk[i] * (double)w[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int q = kVecThreads / 2; q > 0; q >>= 1) {
+    if ((int)threadIdx.x < q) sh[threadIdx.x] += sh[threadIdx.x + q];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = sh[0];
+}
+
+__global__ void k_multidot_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  __shared__ double sh[kVecThreads];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kVecThreads) s += part[(int64_t)blockIdx.x * nb + b];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int q = kVecThreads / 2; q > 0; q >>= 1) {
+    if ((int)threadIdx.x < q) sh[threadIdx.x] += sh[threadIdx.x + q];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
+// w -= sum_k h_k V_k
+template <class T>
+__global__ void k_orth_update(const T* __restrict__ V, int64_t ld, int nk,
+                              const double* __restrict__ h, T* __restrict__ w, int64_t n) {
+  GRID_LOOP(i, n) {
+    double acc = (double)w[i];
+    for (int k = 0; k < nk; ++k) acc -= h[k] * (double)V[(int64_t)k * ld + i];
+    w[i] = (T)acc;
+  }
+}
+
+template <class T>
+__global__ void k_scale(T* __restrict__ a, double s, int64_t n) {
+  GRID_LOOP(i, n) a[i] = (T)((double)a[i] * s);
+}
+
+// x += dinv * (sum_k y_k V_k)   (right preconditioning)
+template <class T>
+__global__ void k_gmres_update(const T* __restrict__ V, int64_t ld, int nk,
+                               const double* __restrict__ y, const T* __restrict__ dinv,
+                               T* __restrict__ x, int64_t n) {
+  GRID_LOOP(i, n) {
+    double acc = 0.0;
+    for (int k = 0; k < nk; ++k) acc += y[k] * (double)V[(int64_t)k * ld + i];
+    if (dinv) acc *= (double)dinv[i];
+    x[i] = (T)((double)x[i] + acc);
+  }
+}
+
+// ------------------------------------------------------------------ host helpers
+static unsigned red_grid(const chns_mesh* m, int64_t n) {
+  int64_t g = (n + kVecThreads - 1) / kVecThreads;
+  int64_t cap = std::min<int64_t>(kRedSlots, 4 * (int64_t)m->sm_count);
+  return (unsigned)std::max<int64_t>(1, std::min(g, cap));
+}
+static unsigned vgrid(const chns_mesh* m, int64_t n) {
+  int64_t g = (n + kVecThreads - 1) / kVecThreads;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 8 * (int64_t)m->sm_count));
+}
+static unsigned vgrid_n(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
+}
+
+void vec_axpby(double a, const double* x, double b, const double* y, double* out, int64_t n,
+               cudaStream_t s) {
+  note_launch();
+  k_axpby<double><<<vgrid_n(n), kVecThreads, 0, s>>>(a, x, b, y, out, n);
+}
+void vec_copy(const double* x, double* y, int64_t n, cudaStream_t s) {
+  cudaMemcpyAsync(y, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+void vec_zero(double* x, int64_t n, cudaStream_t s) { cudaMemsetAsync(x, 0, n * sizeof(double), s); }
+void vec_convert_f64_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
+  note_launch();
+  k_convert<double, float><<<vgrid_n(n), kVecThreads, 0, s>>>(a, b, n, 1.0);
+}
+void vec_convert_f64_bf16(const double* a, __nv_bfloat16* b, int64_t n, cudaStream_t s) {
+  note_launch();
+  k_convert_bf16<<<vgrid_n(n), kVecThreads, 0, s>>>(a, b, n);
+}
+void vec_add_scalar(double* x, const double* dev_scalar, double factor, int64_t n, cudaStream_t s) {
+  note_launch();
+  k_add_scalar<double><<<vgrid_n(n), kVecThreads, 0, s>>>(x, dev_scalar, factor, n);
+}
+
+static double* scal(const chns_mesh* m) { return m->ws.red + kScalarBase; }
+
+void dot_dev(const chns_mesh* m, const double* a, const double* b, int64_t n, double* dst,
+             cudaStream_t s) {
+  note_launch();
+  k_dot<double, double><<<red_grid(m, n), kVecThreads, 0, s>>>(a, b, n, m->ws.red, m->ws.counter, dst);
+}
+
+static chns_status read_dev(const chns_mesh* m, const double* d, double* h, int count,
+                            cudaStream_t s) {
+  CHNS_CUDA(cudaMemcpyAsync(m->ws.h_pinned, d, count * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CHNS_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < count; ++i) h[i] = m->ws.h_pinned[i];
+  return CHNS_OK;
+}
+
+chns_status dot_host(const chns_mesh* m, const double* a, const double* b, int64_t n, double* out,
+                     cudaStream_t s) {
+  double* dst = scal(m) + S_AUX;
+  dot_dev(m, a, b, n, dst, s);
+  CHNS_CUDA(cudaGetLastError());
+  return read_dev(m, dst, out, 1, s);
+}
+
+chns_status sum_host(const chns_mesh* m, const double* a, int64_t n, double* out, cudaStream_t s) {
+  double* dst = scal(m) + S_AUX + 1;
+  note_launch();
+  k_sum<double><<<red_grid(m, n), kVecThreads, 0, s>>>(a, n, m->ws.red, m->ws.counter, dst);
+  CHNS_CUDA(cudaGetLastError());
+  return read_dev(m, dst, out, 1, s);
+}
+
+// ------------------------------------------------------------------ solvers
+namespace {
+
+struct Ctx {
+  const chns_mesh* m;
+  chns_operator op;
+  const chns_params* prm;
+  const chns_coef* coef64;  // FP64 coefficients
+  chns_coef coefR;          // reduced-precision coefficients for the FP32 apply
+  chns_precision inner;     // precision of the FP32 apply (FP32 or FP32_BF16COEF)
+  cudaStream_t s;
+  int64_t n;                // vector length (components * n_nodes)
+  double* S;                // device scalars
+};
+
+template <class T>
+chns_status apply_T(const Ctx& c, const T* x, T* y) {
+  if (sizeof(T) == sizeof(double)) return apply_op(c.m, c.op, c.prm, c.coef64, x, y, CHNS_FP64, c.s);
+  return apply_op(c.m, c.op, c.prm, &c.coefR, x, y, c.inner, c.s);
+}
+
+template <class T>
+chns_status dot_to_host(const Ctx& c, const T* a, const T* b, double* out) {
+  double* dst = c.S + S_AUX + 2;
+  note_launch();
+  k_dot<T, T><<<red_grid(c.m, c.n), kVecThreads, 0, c.s>>>(a, b, c.n, c.m->ws.red, c.m->ws.counter, dst);
+  CHNS_CUDA(cudaGetLastError());
+  return read_dev(c.m, dst, out, 1, c.s);
+}
+
+// v -= mean(v) (discrete mean over the nodes; pure-Neumann pressure)
+template <class T>
+chns_status project_mean(const Ctx& c, T* v) {
+  double* dst = c.S + S_AUX + 3;
+  note_launch();
+  k_sum<T><<<red_grid(c.m, c.n), kVecThreads, 0, c.s>>>(v, c.n, c.m->ws.red, c.m->ws.counter, dst);
+  note_launch();
+  k_add_scalar<T><<<vgrid(c.m, c.n), kVecThreads, 0, c.s>>>(v, dst, -1.0 / (double)c.n, c.n);
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
+// Preconditioned CG on A x = b (type T); x holds the initial guess. Runs until sqrt(r.r) <= tol_abs
+// (checked every check_every iterations) or max_it iterations.
+template <class T>
+chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, int max_it,
+                int check_every, T* r, T* z, T* p, T* q, int* iters, double* rnorm) {
+  const int64_t n = c.n;
+  const unsigned rg = red_grid(c.m, n), vg = vgrid(c.m, n);
+  chns_status st = apply_T<T>(c, x, q);
+  if (st != CHNS_OK) return st;
+  note_launch();
+  k_axpby<T><<<vg, kVecThreads, 0, c.s>>>(1.0, b, -1.0, q, r, n);
+  if (c.op == CHNS_OP_POISSON) project_mean<T>(c, r);
+  note_launch();
+  k_mul<T><<<vg, kVecThreads, 0, c.s>>>(dinv, r, z, n);
+  CHNS_CUDA(cudaMemcpyAsync(p, z, n * sizeof(T), cudaMemcpyDeviceToDevice, c.s));
+  note_launch();
+  k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, z, n, c.m->ws.red, c.m->ws.counter, c.S + S_RZ0);
+  note_launch();
+  k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, r, n, c.m->ws.red, c.m->ws.counter, c.S + S_RR);
+  CHNS_CUDA(cudaGetLastError());
+  int it = 0;
+  double rr = 0.0;
+  check_every = std::max(1, check_every);
+  for (;;) {
+    if (it % check_every == 0 || it >= max_it) {
+      st = read_dev(c.m, c.S + S_RR, &rr, 1, c.s);
+      if (st != CHNS_OK) return st;
+      if (!std::isfinite(rr)) {
+        *iters = it;
+        *rnorm = rr;
+        set_error("krylov: NaN/Inf in the residual norm");
+        return CHNS_ENAN;
+      }
+      if (std::sqrt(rr) <= tol_abs || it >= max_it) break;
+    }
+    const int par = it & 1;
+    st = apply_T<T>(c, p, q);
+    if (st != CHNS_OK) return st;
+    note_launch();
+    k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(p, q, n, c.m->ws.red, c.m->ws.counter, c.S + S_PQ);
+    note_launch();
+    k_cg_update<T><<<rg, kVecThreads, 0, c.s>>>(x, r, z, p, q, dinv, n, c.S, par, c.m->ws.red,
+                                                c.m->ws.counter);
+    note_launch();
+    k_cg_pupdate<T><<<vg, kVecThreads, 0, c.s>>>(p, z, n, c.S, par);
+    ++it;
+  }
+  CHNS_CUDA(cudaGetLastError());
+  *iters = it;
+  *rnorm = std::sqrt(rr);
+  return std::sqrt(rr) <= tol_abs ? CHNS_OK : CHNS_ENOTCONV;
+}
+
+// Right-preconditioned restarted GMRES with classical Gram-Schmidt and one re-orthogonalisation
+// pass; the second pass also returns w.w so that the new norm needs no extra reduction.
+template <class T>
+chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, int max_it,
+                  int restart, T* V, T* z, int* iters, double* rnorm) {
+  const int64_t n = c.n, ld = n;
+  const unsigned vg = vgrid(c.m, n);
+  const unsigned mdb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(kMdBlocks, (n + 255) / 256));
+  double* hdev = c.S + S_MD;
+  std::vector<double> H((size_t)(restart + 1) * restart, 0.0), cs(restart), sn(restart),
+      g(restart + 1), y(restart), h(restart + 2);
+  int it = 0;
+  double beta = 0.0;
+  chns_status st;
+  auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * restart + j]; };
+  for (;;) {
+    // r = b - A x into V_0
+    st = apply_T<T>(c, x, z);
+    if (st != CHNS_OK) return st;
+    note_launch();
+    k_axpby<T><<<vg, kVecThreads, 0, c.s>>>(1.0, b, -1.0, z, V, n);
+    st = dot_to_host<T>(c, V, V, &beta);
+    if (st != CHNS_OK) return st;
+    beta = std::sqrt(beta);
+    if (!std::isfinite(beta)) {
+      set_error("krylov: NaN/Inf in the residual norm");
+      *iters = it;
+      *rnorm = beta;
+      return CHNS_ENAN;
+    }
+    if (beta <= tol_abs || it >= max_it) break;
+    note_launch();
+    k_scale<T><<<vg, kVecThreads, 0, c.s>>>(V, 1.0 / beta, n);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jend = 0;
+    for (int j = 0; j < restart; ++j) {
+      T* vj = V + (int64_t)j * ld;
+      T* w = V + (int64_t)(j + 1) * ld;
+      note_launch();
+      k_mul<T><<<vg, kVecThreads, 0, c.s>>>(dinv, vj, z, n);
+      st = apply_T<T>(c, z, w);
+      if (st != CHNS_OK) return st;
+      for (int i = 0; i <= j; ++i) Hij(i, j) = 0.0;
+      double ww = 0.0;
+      for (int pass = 0; pass < 2; ++pass) {
+        const int nk = pass == 0 ? j + 1 : j + 2;  // second pass also computes w.w
+        note_launch();
+        k_multidot<T><<<dim3(mdb, nk), kVecThreads, 0, c.s>>>(V, ld, w, n, c.m->ws.red);
+        note_launch();
+        k_multidot_final<<<nk, kVecThreads, 0, c.s>>>(c.m->ws.red, (int)mdb, hdev);
+        note_launch();
+        k_orth_update<T><<<vg, kVecThreads, 0, c.s>>>(V, ld, j + 1, hdev, w, n);
+        CHNS_CUDA(cudaGetLastError());
+        st = read_dev(c.m, hdev, h.data(), nk, c.s);
+        if (st != CHNS_OK) return st;
+        double hh = 0.0;
+        for (int i = 0; i <= j; ++i) {
+          Hij(i, j) += h[i];
+          hh += h[i] * h[i];
+        }
+        if (pass == 1) ww = std::max(0.0, h[j + 1] - hh);
+      }
+      const double hn = std::sqrt(ww);
+      Hij(j + 1, j) = hn;
+      if (!std::isfinite(hn)) {
+        set_error("krylov: NaN/Inf in GMRES");
+        *iters = it;
+        *rnorm = hn;
+        return CHNS_ENAN;
+      }
+      if (hn > 0.0) note_launch(), k_scale<T><<<vg, kVecThreads, 0, c.s>>>(w, 1.0 / hn, n);
+      // Givens rotations
+      for (int i = 0; i < j; ++i) {
+        double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+        Hij(i, j) = t;
+      }
+      double a = Hij(j, j), bb = Hij(j + 1, j);
+      double rden = std::hypot(a, bb);
+      cs[j] = rden > 0.0 ? a / rden : 1.0;
+      sn[j] = rden > 0.0 ? bb / rden : 0.0;
+      Hij(j, j) = rden;
+      Hij(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      jend = j + 1;
+      if (std::fabs(g[j + 1]) <= tol_abs || it >= max_it || hn == 0.0) break;
+    }
+    // back substitution and update x += M^-1 V y
+    for (int i = jend - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int k = i + 1; k < jend; ++k) acc -= Hij(i, k) * y[k];
+      y[i] = Hij(i, i) != 0.0 ? acc / Hij(i, i) : 0.0;
+    }
+    CHNS_CUDA(cudaMemcpyAsync(hdev, y.data(), jend * sizeof(double), cudaMemcpyHostToDevice, c.s));
+    note_launch();
+    k_gmres_update<T><<<vg, kVecThreads, 0, c.s>>>(V, ld, jend, hdev, dinv, x, n);
+    CHNS_CUDA(cudaGetLastError());
+    CHNS_CUDA(cudaStreamSynchronize(c.s));  // y (host) is reused next cycle
+  }
+  *iters = it;
+  *rnorm = beta;
+  return beta <= tol_abs ? CHNS_OK : CHNS_ENOTCONV;
+}
+
+}  // namespace
+
+// Convert the FP64 coefficient fields of an operator to the inner precision (workspace copies).
+static chns_status make_reduced_coef(const chns_mesh* m, const chns_coef* c, chns_precision prec,
+                                     chns_coef* out, cudaStream_t s) {
+  const int64_t N = m->d.n_nodes;
+  const void* src[5] = {c->phi_tilde, c->u_adv[0], c->u_adv[1], c->u_adv[2], c->mu_tilde};
+  void* dst[5];
+  for (int k = 0; k < 5; ++k) {
+    dst[k] = nullptr;
+    if (!src[k]) continue;
+    if (prec == CHNS_FP32) {
+      float* d = static_cast<float*>(m->ws.coef32) + k * N;
+      vec_convert_f64_f32(static_cast<const double*>(src[k]), d, N, s);
+      dst[k] = d;
+    } else {
+      __nv_bfloat16* d = static_cast<__nv_bfloat16*>(m->ws.coef16) + k * N;
+      vec_convert_f64_bf16(static_cast<const double*>(src[k]), d, N, s);
+      dst[k] = d;
+    }
+  }
+  out->phi_tilde = dst[0];
+  out->u_adv[0] = dst[1];
+  out->u_adv[1] = dst[2];
+  out->u_adv[2] = dst[3];
+  out->mu_tilde = dst[4];
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
+chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params* prm,
+                         const chns_coef* coef, const double* b_in, double* x,
+                         const chns_solver_params* sp, chns_solve_stats* stats, cudaStream_t s) {
+  CHNS_CHECK(m && prm && coef && b_in && x && sp, CHNS_EINVAL, "chns_krylov_solve: null argument");
+  CHNS_CHECK(op >= CHNS_OP_POISSON && op <= CHNS_OP_MOMENTUM, CHNS_EINVAL, "bad operator");
+  CHNS_CHECK(sp->ksp == CHNS_KSP_CG || sp->ksp == CHNS_KSP_GMRES, CHNS_EINVAL, "bad ksp");
+  CHNS_CHECK(sp->pc == CHNS_PC_NONE || sp->pc == CHNS_PC_JACOBI, CHNS_EINVAL, "bad preconditioner");
+  CHNS_CHECK(sp->rtol > 0.0 && sp->max_it >= 0, CHNS_EINVAL, "bad tolerance / max_it");
+  CHNS_CHECK(sp->ksp != CHNS_KSP_GMRES ||
+                 (sp->restart >= 1 && sp->restart <= CHNS_GMRES_MAX_RESTART),
+             CHNS_EINVAL, "GMRES restart out of range");
+  CHNS_CHECK(sp->inner_precision >= CHNS_FP64 && sp->inner_precision <= CHNS_FP32_BF16COEF,
+             CHNS_EINVAL, "bad inner precision");
+  const Workspace& ws = m->ws;
+  const int nc = op_ncomp(op);
+  const int64_t n = nc * m->d.n_nodes;
+  cudaEvent_t e0, e1;
+  CHNS_CUDA(cudaEventCreate(&e0));
+  CHNS_CUDA(cudaEventCreate(&e1));
+  CHNS_CUDA(cudaEventRecord(e0, s));
+
+  Ctx c;
+  c.m = m;
+  c.op = op;
+  c.prm = prm;
+  c.coef64 = coef;
+  c.inner = (chns_precision)sp->inner_precision;
+  c.s = s;
+  c.n = n;
+  c.S = scal(m);
+
+  // workspace layout (FP64): 0 b (projected), 1 r64, 2 dinv64/diag, 3..6 CG vectors,
+  // 7 GMRES z; (FP32): 0 r32, 1 d32, 2 dinv32, 3..6 CG vectors, 7 GMRES z
+  double* b = ws.v64[0];
+  double* r64 = ws.v64[1];
+  double* d64 = ws.v64[2];
+  CHNS_CUDA(cudaMemcpyAsync(b, b_in, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  chns_status st = CHNS_OK;
+  if (op == CHNS_OP_POISSON) {
+    st = project_mean<double>(c, b);
+    if (st != CHNS_OK) return st;
+  }
+  double bn2 = 0.0;
+  st = dot_to_host<double>(c, b, b, &bn2);
+  if (st != CHNS_OK) return st;
+  const double bnorm = std::sqrt(bn2);
+  chns_solve_stats out{};
+  out.b_norm = bnorm;
+  if (bnorm == 0.0) {
+    CHNS_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  } else {
+    // Jacobi preconditioner from the exact FP64 diagonal
+    const double* dinv64 = nullptr;
+    if (sp->pc == CHNS_PC_JACOBI) {
+      st = diag_op(m, op, prm, coef, d64, CHNS_FP64, s);
+      if (st != CHNS_OK) return st;
+      note_launch();
+      k_invert<double><<<vgrid(m, n), kVecThreads, 0, s>>>(d64, d64, n);
+      dinv64 = d64;
+    }
+    const double tol = sp->rtol * bnorm;
+    if (c.inner == CHNS_FP64) {
+      int its = 0;
+      double rn = 0.0;
+      if (sp->ksp == CHNS_KSP_CG)
+        st = pcg<double>(c, b, x, dinv64, tol, sp->max_it, sp->check_every, r64, ws.v64[3],
+                         ws.v64[4], ws.v64[5], &its, &rn);
+      else
+        st = gmres<double>(c, b, x, dinv64, tol, sp->max_it, sp->restart, ws.gm_V, ws.v64[7],
+                           &its, &rn);
+      out.iterations = its;
+    } else {
+      st = make_reduced_coef(m, coef, c.inner, &c.coefR, s);
+      if (st != CHNS_OK) return st;
+      float* r32 = ws.v32[0];
+      float* d32 = ws.v32[1];
+      float* dinv32 = nullptr;
+      if (dinv64) {
+        dinv32 = ws.v32[2];
+        note_launch();
+        k_convert<double, float><<<vgrid(m, n), kVecThreads, 0, s>>>(dinv64, dinv32, n, 1.0);
+      }
+      int total = 0, refine = 0;
+      for (;;) {
+        // r64 = b - A_64 x
+        st = apply_op(m, op, prm, coef, x, r64, CHNS_FP64, s);
+        if (st != CHNS_OK) return st;
+        note_launch();
+        k_axpby<double><<<vgrid(m, n), kVecThreads, 0, s>>>(1.0, b, -1.0, r64, r64, n);
+        if (op == CHNS_OP_POISSON) project_mean<double>(c, r64);
+        double rn2 = 0.0;
+        st = dot_to_host<double>(c, r64, r64, &rn2);
+        if (st != CHNS_OK) return st;
+        const double rn = std::sqrt(rn2);
+        if (!std::isfinite(rn)) {
+          set_error("krylov: NaN/Inf in the refinement residual");
+          st = CHNS_ENAN;
+          break;
+        }
+        if (rn <= tol) {
+          st = CHNS_OK;
+          break;
+        }
+        if (total >= sp->max_it || refine >= sp->max_refine) {
+          st = CHNS_ENOTCONV;
+          break;
+        }
+        const double scale = 1.0 / rn;
+        note_launch();
+        k_convert<double, float><<<vgrid(m, n), kVecThreads, 0, s>>>(r64, r32, n, scale);
+        CHNS_CUDA(cudaMemsetAsync(d32, 0, n * sizeof(float), s));
+        int its = 0;
+        double irn = 0.0;
+        const double itol = std::max(sp->inner_rtol, 0.5 * tol / rn);
+        chns_status ist;
+        if (sp->ksp == CHNS_KSP_CG)
+          ist = pcg<float>(c, r32, d32, dinv32, itol, sp->max_it - total, sp->check_every,
+                           ws.v32[3], ws.v32[4], ws.v32[5], ws.v32[6], &its, &irn);
+        else
+          ist = gmres<float>(c, r32, d32, dinv32, itol, sp->max_it - total, sp->restart,
+                             ws.gm_V32, ws.v32[7], &its, &irn);
+        if (ist != CHNS_OK && ist != CHNS_ENOTCONV) return ist;
+        total += its;
+        ++refine;
+        note_launch();
+        k_accumulate<float><<<vgrid(m, n), kVecThreads, 0, s>>>(x, d32, rn, n);
+        if (its == 0) {
+          st = CHNS_ENOTCONV;
+          break;
+        }
+      }
+      out.iterations = total;
+      out.refinements = refine;
+    }
+    if (op == CHNS_OP_POISSON) project_mean<double>(c, x);
+    // true FP64 residual
+    chns_status st2 = apply_op(m, op, prm, coef, x, r64, CHNS_FP64, s);
+    if (st2 != CHNS_OK) return st2;
+    note_launch();
+    k_axpby<double><<<vgrid(m, n), kVecThreads, 0, s>>>(1.0, b, -1.0, r64, r64, n);
+    if (op == CHNS_OP_POISSON) project_mean<double>(c, r64);
+    double rr = 0.0;
+    st2 = dot_to_host<double>(c, r64, r64, &rr);
+    if (st2 != CHNS_OK) return st2;
+    out.rel_residual = std::sqrt(rr) / bnorm;
+    if (st == CHNS_ENOTCONV && out.rel_residual <= sp->rtol) st = CHNS_OK;
+  }
+  CHNS_CUDA(cudaEventRecord(e1, s));
+  CHNS_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  out.ms = ms;
+  out.status = st;
+  if (stats) *stats = out;
+  if (st == CHNS_ENOTCONV) set_error("krylov: iteration limit reached before the tolerance");
+  return st;
+}
+
+}  // namespace chns
+
+extern "C" chns_status chns_krylov_solve(const chns_mesh* m, chns_operator op,
+                                         const chns_params* prm, const chns_coef* coef,
+                                         const double* b, double* x, const chns_solver_params* sp,
+                                         chns_solve_stats* stats, void* stream) {
+  return chns::krylov_solve(m, op, prm, coef, b, x, sp, stats, chns::as_stream(stream));
+}

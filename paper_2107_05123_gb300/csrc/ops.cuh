@@ -1,0 +1,238 @@
+// Element operators of the CHNS scheme (Sec. 4.1), each as a small struct with
+//   load(...)  : gather the element's coefficient fields (hanging-interpolated) and prepare
+//                per-quadrature-point data,
+//   apply(...) : local y_e = A_e x_e for NC components.
+// The same structs drive the matrix-free apply kernel and the exact diagonal kernel.
+#pragma once
+
+#include "elem.cuh"
+
+namespace chns {
+
+template <class C>
+struct CoefArgs {
+  const C* phi;     // phi~
+  const C* u[3];    // advecting velocity (u_hat or u~)
+  const C* mu;      // mu~
+};
+
+// ---------------------------------------------------------------- pressure Poisson
+// (grad q, (1/rho(phi~*)) grad p) (Def. weak_VMS_disc_pp_vel, scalar test q).
+template <class T>
+__device__ __forceinline__ void poisson_coef(const T pe[8], const Geo<T>& g, const DevParams& p,
+                                             T c[8]) {
+  T pq[8];
+  interp3(pe, pq);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) c[q] = g.detJ / (T(p.alpha) * clamp1(pq[q]) + T(p.beta));
+}
+
+// Sum-factorised local stiffness apply with a per-quadrature-point coefficient c[q]:
+// r_a = sum_q c_q grad N_a(q) . grad u(q).
+template <class T>
+__device__ __forceinline__ void stiff_local(const T c[8], const Geo<T>& g, const T u[8], T r[8]) {
+  T gx[4], gy[4], gz[4];
+  grad_compact(u, gx, gy, gz);
+  T sx[4], sy[4], sz[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sx[j] = gx[j] * (c[2 * j] + c[2 * j + 1]);
+#pragma unroll
+  for (int z = 0; z < 2; ++z)
+#pragma unroll
+    for (int x = 0; x < 2; ++x) sy[x + 2 * z] = gy[x + 2 * z] * (c[x + 4 * z] + c[x + 2 + 4 * z]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sz[k] = gz[k] * (c[k] + c[k + 4]);
+  const T sc[3] = {g.ih[0] * g.ih[0], g.ih[1] * g.ih[1], g.ih[2] * g.ih[2]};
+#pragma unroll
+  for (int a = 0; a < 8; ++a) r[a] = T(0);
+  grad_compact_T(sx, sy, sz, sc, r);
+}
+
+template <class T, class C>
+struct PoissonK {
+  static constexpr int NC = 1;
+  static constexpr bool DIR = false;
+  static constexpr bool DIAG_PER_COMP = false;
+  T c[8];
+  __device__ __forceinline__ void load(const MeshDev& m, const DevParams& p, const CoefArgs<C>& cf,
+                                       const int idx[8], const Geo<T>& g) {
+    T pe[8];
+    gather<T, false>(m, idx, cf.phi, pe);
+    poisson_coef(pe, g, p, c);
+  }
+  __device__ __forceinline__ void apply(const Geo<T>& g, const DevParams&, const T x[NC][8],
+                                        T r[NC][8]) const {
+    stiff_local(c, g, x[0], r[0]);
+  }
+};
+
+// ---------------------------------------------------------------- velocity update mass
+// (w, rho~ u) per component (Def. weak_VMS_disc_vel_update); Dirichlet rows are identity.
+template <class T, class C>
+struct MassK {
+  static constexpr int NC = 3;
+  static constexpr bool DIR = true;
+  static constexpr bool DIAG_PER_COMP = false;
+  T c[8];
+  __device__ __forceinline__ void load(const MeshDev& m, const DevParams& p, const CoefArgs<C>& cf,
+                                       const int idx[8], const Geo<T>& g) {
+    T pe[8], pq[8];
+    gather<T, false>(m, idx, cf.phi, pe);
+    interp3(pe, pq);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) c[q] = g.detJ * (T(p.alpha) * clamp1(pq[q]) + T(p.beta));
+  }
+  __device__ __forceinline__ void apply(const Geo<T>&, const DevParams&, const T x[NC][8],
+                                        T r[NC][8]) const {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      T v[8];
+      interp3(x[k], v);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] *= c[q];
+      interp3(v, r[k]);
+    }
+  }
+};
+
+// ---------------------------------------------------------------- Cahn-Hilliard Jacobian
+// Newton Jacobian of Def. weak_VMS_disc_CH in (dphi, dmu), with phi~ the current iterate and
+// u~ the advecting velocity (diffusion term with a plus sign, as in the strong form):
+//   row phi: (q, dphi)/dt - 1/2 (grad q, u~ dphi) + 1/(2 Pe Cn) (grad q, grad dmu)
+//   row mu : -1/2 (q, dmu) + 1/2 (q, psi''(phi~) dphi) + Cn^2/2 (grad q, grad dphi)
+template <class T, class C>
+struct ChK {
+  static constexpr int NC = 2;
+  static constexpr bool DIR = false;
+  static constexpr bool DIAG_PER_COMP = true;
+  T pe[8];
+  T ue[3][8];
+  __device__ __forceinline__ void load(const MeshDev& m, const DevParams&, const CoefArgs<C>& cf,
+                                       const int idx[8], const Geo<T>&) {
+    gather<T, false>(m, idx, cf.phi, pe);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gather<T, false>(m, idx, cf.u[d], ue[d]);
+  }
+  __device__ __forceinline__ void apply(const Geo<T>& g, const DevParams& p, const T x[NC][8],
+                                        T r[NC][8]) const {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) r[0][a] = r[1][a] = T(0);
+    const T idt = T(1.0 / p.dt), kmu = T(0.5 / (p.Pe * p.Cn)), kphi = T(0.5 * p.Cn * p.Cn);
+    const T J = g.detJ;
+    for_qp([&](auto QC) {
+      constexpr int Q = decltype(QC)::value;
+      T pq = val_at<Q>(pe);
+      T psi2 = T(3) * pq * pq - T(1);
+      T uq[3] = {val_at<Q>(ue[0]), val_at<Q>(ue[1]), val_at<Q>(ue[2])};
+      T fv, fg[3], mv, mg[3];
+      vg_at<Q>(x[0], g, fv, fg);
+      vg_at<Q>(x[1], g, mv, mg);
+      T V0[3], V1[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        V0[d] = J * (T(-0.5) * uq[d] * fv + kmu * mg[d]);
+        V1[d] = J * kphi * fg[d];
+      }
+      add_test<Q>(r[0], J * fv * idt, V0, g);
+      add_test<Q>(r[1], J * (T(-0.5) * mv + T(0.5) * psi2 * fv), V1, g);
+    });
+  }
+};
+
+// ---------------------------------------------------------------- velocity prediction (RBVMS)
+// Per-quadrature-point coefficients of the momentum operator (Def. weak_VMS_disc):
+//   rho~, eta~ from clamp(phi~); grad eta~ = gamma grad phi~ where |phi~| < 1;
+//   J_hat = -(alpha/Cn) grad mu~; G = diag(4/h^2);
+//   tau_m = (4/dt^2 + u.G.u + u.G.J/(rho Pe) + C_I (eta/(rho Re))^2 G:G)^(-1/2).
+// The operator on one velocity component v (the same for each component):
+//   s = rho/dt v + 1/2 rho u.grad v + 1/(2Pe) J.grad v                       (tested with N_a)
+//   R = s - 1/(2Re) grad eta . grad v                                        (R^lin)
+//   V = eta/(2Re) grad v + tau R (u/2 + J/(2 Pe rho))                       (tested with grad N_a)
+template <class T>
+struct VmsQ {
+  T rho, eta, a0, b[3], bp[3], e, t[3], tau, uq[3], J[3], ge[3], gphi[3];
+};
+
+template <int Q, class T>
+__device__ __forceinline__ VmsQ<T> vms_at(const T pe[8], const T ue[3][8], const T me[8],
+                                          const Geo<T>& g, const DevParams& p) {
+  VmsQ<T> o;
+  T pv, mv;
+  vg_at<Q>(pe, g, pv, o.gphi);
+  T mg[3];
+  vg_at<Q>(me, g, mv, mg);
+  (void)mv;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) o.uq[d] = val_at<Q>(ue[d]);
+  T pc = clamp1(pv);
+  o.rho = T(p.alpha) * pc + T(p.beta);
+  o.eta = T(p.gamma) * pc + T(p.xi);
+  const bool inside = pv < T(1) && pv > T(-1);
+  const T ka = T(-p.alpha / p.Cn);
+  T ugu = T(0), ugj = T(0), gg = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    o.ge[d] = inside ? T(p.gamma) * o.gphi[d] : T(0);
+    o.J[d] = ka * mg[d];
+    T Gd = T(4) * g.ih[d] * g.ih[d];
+    ugu += o.uq[d] * Gd * o.uq[d];
+    ugj += o.uq[d] * Gd * o.J[d];
+    gg += Gd * Gd;
+  }
+  const T ir = T(1) / o.rho;
+  const T er = o.eta * ir / T(p.Re);
+  const T idt = T(1.0 / p.dt);
+  o.tau = rsqrt(T(4) * idt * idt + ugu + ugj * ir / T(p.Pe) + T(p.C_I) * er * er * gg);
+  o.a0 = o.rho * idt;
+  o.e = o.eta * T(0.5 / p.Re);
+  const T h2pe = T(0.5 / p.Pe), h2re = T(0.5 / p.Re);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    o.b[d] = T(0.5) * o.rho * o.uq[d] + h2pe * o.J[d];
+    o.bp[d] = o.b[d] - h2re * o.ge[d];
+    o.t[d] = o.tau * (T(0.5) * o.uq[d] + h2pe * ir * o.J[d]);
+  }
+  return o;
+}
+
+template <class T, class C>
+struct MomK {
+  static constexpr int NC = 3;
+  static constexpr bool DIR = true;
+  static constexpr bool DIAG_PER_COMP = false;
+  T pe[8];
+  T ue[3][8];
+  T me[8];
+  __device__ __forceinline__ void load(const MeshDev& m, const DevParams&, const CoefArgs<C>& cf,
+                                       const int idx[8], const Geo<T>&) {
+    gather<T, false>(m, idx, cf.phi, pe);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gather<T, false>(m, idx, cf.u[d], ue[d]);
+    gather<T, false>(m, idx, cf.mu, me);
+  }
+  __device__ __forceinline__ void apply(const Geo<T>& g, const DevParams& p, const T x[NC][8],
+                                        T r[NC][8]) const {
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) r[k][a] = T(0);
+    const T J = g.detJ;
+    for_qp([&](auto QC) {
+      constexpr int Q = decltype(QC)::value;
+      VmsQ<T> c = vms_at<Q>(pe, ue, me, g, p);
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        T v, vg[3];
+        vg_at<Q>(x[k], g, v, vg);
+        T s = c.a0 * v + c.b[0] * vg[0] + c.b[1] * vg[1] + c.b[2] * vg[2];
+        T R = c.a0 * v + c.bp[0] * vg[0] + c.bp[1] * vg[1] + c.bp[2] * vg[2];
+        T V[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) V[d] = J * (c.e * vg[d] + R * c.t[d]);
+        add_test<Q>(r[k], J * s, V, g);
+      }
+    });
+  }
+};
+
+}  // namespace chns

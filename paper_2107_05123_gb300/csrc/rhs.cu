@@ -1,0 +1,385 @@
+// Right-hand sides and nonlinear residuals of the time step (FP64), and the phi mass integral.
+// These are the "vector assembly" traversals of the paper (Sec. 5.4), done matrix-free with the
+// same gather / element quadrature / scatter-add skeleton as the operator applies.
+#include <vector>
+
+#include "ops.cuh"
+
+namespace chns {
+
+constexpr int kRhsThreads = 128;
+// gravity direction g_hat = (0, -1, 0) (Sec. 3)
+__device__ __forceinline__ double ghat(int i) { return i == 1 ? -1.0 : 0.0; }
+
+struct Ptr3 {
+  const double* c[3];
+};
+
+// ---- CH residual at the new-time iterate (Def. weak_VMS_disc_CH):
+//   F_phi = (q, (phi - phi_k)/dt) - (grad q, u~ phi~) + 1/(Pe Cn) (grad q, grad mu~)
+//   F_mu  = -(q, mu~) + (q, psi'(phi~)) + Cn^2 (grad q, grad phi~)
+__global__ void __launch_bounds__(kRhsThreads)
+k_residual_ch(MeshDev m, DevParams p, const double* __restrict__ phi, const double* __restrict__ mu,
+              const double* __restrict__ phik, const double* __restrict__ muk, Ptr3 u,
+              double* __restrict__ f) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.n_elem) return;
+  int idx[8];
+  load_corners(m, e, idx);
+  const Geo<double> g = geometry<double>(m, e);
+  double a[8], b[8], pt[8], mt[8], dp[8], ue[3][8];
+  gather<double, false>(m, idx, phi, a);
+  gather<double, false>(m, idx, phik, b);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    pt[i] = 0.5 * (a[i] + b[i]);
+    dp[i] = (a[i] - b[i]) / p.dt;
+  }
+  gather<double, false>(m, idx, mu, a);
+  gather<double, false>(m, idx, muk, b);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) mt[i] = 0.5 * (a[i] + b[i]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) gather<double, false>(m, idx, u.c[d], ue[d]);
+  double r0[8] = {0}, r1[8] = {0};
+  const double J = g.detJ, kmu = 1.0 / (p.Pe * p.Cn), c2 = p.Cn * p.Cn;
+  for_qp([&](auto QC) {
+    constexpr int Q = decltype(QC)::value;
+    double pv, pg[3], mv, mg[3];
+    vg_at<Q>(pt, g, pv, pg);
+    vg_at<Q>(mt, g, mv, mg);
+    double dv = val_at<Q>(dp);
+    double V0[3], V1[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      V0[d] = J * (-val_at<Q>(ue[d]) * pv + kmu * mg[d]);
+      V1[d] = J * c2 * pg[d];
+    }
+    add_test<Q>(r0, J * dv, V0, g);
+    add_test<Q>(r1, J * (-mv + pv * pv * pv - pv), V1, g);
+  });
+  scatter<double, false>(m, idx, r0, f);
+  scatter<double, false>(m, idx, r1, f + m.n_nodes);
+}
+
+// Forcing d_j(d_i phi d_j phi) of the trilinear interpolant at Q (pure second derivatives vanish
+// on box elements): F_i = sum_{j != i} H_ij d_j phi.
+template <int Q>
+__device__ __forceinline__ void forcing_at(const double pe[8], const Geo<double>& g,
+                                           const double gp[3], double F[3]) {
+  double hxy, hxz, hyz;
+  hess_at<Q>(pe, g, hxy, hxz, hyz);
+  F[0] = hxy * gp[1] + hxz * gp[2];
+  F[1] = hxy * gp[0] + hyz * gp[2];
+  F[2] = hxz * gp[0] + hyz * gp[1];
+}
+
+// ---- velocity-prediction right-hand side (Def. weak_VMS_disc), per component i:
+//   (w, rho u_i/dt) - 1/2 (w, rho u.grad u_i) - 1/(2Pe) (w, J.grad u_i) - 1/(2Re) (grad w, eta grad u_i)
+//   + Cn/We (d_j w, d_i phi d_j phi) - (w, d_i p) + (w, rho g_i/Fr) - (grad w . t, R0_i)
+// with R0_i the part of R_m that does not depend on v^{k+1}.
+__global__ void __launch_bounds__(kRhsThreads)
+k_rhs_momentum(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 uk,
+               const double* __restrict__ pk, double* __restrict__ b) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.n_elem) return;
+  int idx[8];
+  load_corners(m, e, idx);
+  const Geo<double> g = geometry<double>(m, e);
+  double pe[8], ue[3][8], me[8], pp[8];
+  gather<double, false>(m, idx, cf.phi, pe);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) gather<double, false>(m, idx, cf.u[d], ue[d]);
+  gather<double, false>(m, idx, cf.mu, me);
+  gather<double, false>(m, idx, pk, pp);
+  const double J = g.detJ, cw = p.Cn / p.We;
+  for (int i = 0; i < 3; ++i) {
+    double ui[8], r[8] = {0};
+    gather<double, false>(m, idx, uk.c[i], ui);
+    for_qp([&](auto QC) {
+      constexpr int Q = decltype(QC)::value;
+      VmsQ<double> c = vms_at<Q>(pe, ue, me, g, p);
+      double F[3];
+      forcing_at<Q>(pe, g, c.gphi, F);
+      double pv, pg[3], v, vg[3];
+      vg_at<Q>(pp, g, pv, pg);
+      vg_at<Q>(ui, g, v, vg);
+      const double grav = c.rho * ghat(i) / p.Fr;
+      double bdot = c.b[0] * vg[0] + c.b[1] * vg[1] + c.b[2] * vg[2];
+      double bpdot = c.bp[0] * vg[0] + c.bp[1] * vg[1] + c.bp[2] * vg[2];
+      double r0 = -c.a0 * v + bpdot + cw * F[i] + pg[i] - grav;
+      double fn = c.a0 * v - bdot - pg[i] + grav;
+      double V[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) V[d] = J * (-c.e * vg[d] + cw * c.gphi[i] * c.gphi[d] - c.t[d] * r0);
+      add_test<Q>(r, J * fn, V, g);
+    });
+    scatter<double, true>(m, idx, r, b + i * m.n_nodes);
+  }
+}
+
+// Full R_m,i(v) at Q (Def. of R_m) with v~ = (v + u_k)/2.
+template <int Q>
+__device__ __forceinline__ void rm_at(const VmsQ<double>& c, const DevParams& p, const double F[3],
+                                      const double pg[3], const double ve[3][8],
+                                      const double ue[3][8], const Geo<double>& g, double R[3],
+                                      double vq[3], double& div) {
+  div = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    double vv, vgr[3], uv, ug[3];
+    vg_at<Q>(ve[i], g, vv, vgr);
+    vg_at<Q>(ue[i], g, uv, ug);
+    div += vgr[i];
+    vq[i] = vv;
+    double tg[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) tg[d] = 0.5 * (vgr[d] + ug[d]);
+    double adv = c.uq[0] * tg[0] + c.uq[1] * tg[1] + c.uq[2] * tg[2];
+    double jdv = c.J[0] * tg[0] + c.J[1] * tg[1] + c.J[2] * tg[2];
+    double edv = c.ge[0] * tg[0] + c.ge[1] * tg[1] + c.ge[2] * tg[2];
+    R[i] = c.rho * (vv - uv) / p.dt + c.rho * adv + jdv / p.Pe + (p.Cn / p.We) * F[i] + pg[i] -
+           edv / p.Re - c.rho * ghat(i) / p.Fr;
+  }
+}
+
+// ---- pressure-Poisson right-hand side (Def. weak_VMS_disc_pp_vel, scalar test q):
+//   -(2/dt)(q, div v) - (2/dt)(grad q, tau R_m / rho~) + (grad q, grad p_k / rho~)
+__global__ void __launch_bounds__(kRhsThreads)
+k_rhs_poisson(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 v, Ptr3 uk,
+              const double* __restrict__ pk, double* __restrict__ b) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.n_elem) return;
+  int idx[8];
+  load_corners(m, e, idx);
+  const Geo<double> g = geometry<double>(m, e);
+  double pe[8], ue[3][8], me[8], pp[8], ve[3][8], uke[3][8];
+  gather<double, false>(m, idx, cf.phi, pe);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    gather<double, false>(m, idx, cf.u[d], ue[d]);
+    gather<double, false>(m, idx, v.c[d], ve[d]);
+    gather<double, false>(m, idx, uk.c[d], uke[d]);
+  }
+  gather<double, false>(m, idx, cf.mu, me);
+  gather<double, false>(m, idx, pk, pp);
+  double r[8] = {0};
+  const double J = g.detJ, k2 = 2.0 / p.dt;
+  for_qp([&](auto QC) {
+    constexpr int Q = decltype(QC)::value;
+    VmsQ<double> c = vms_at<Q>(pe, ue, me, g, p);
+    double F[3], pv, pg[3], R[3], vq[3], div;
+    forcing_at<Q>(pe, g, c.gphi, F);
+    vg_at<Q>(pp, g, pv, pg);
+    rm_at<Q>(c, p, F, pg, ve, uke, g, R, vq, div);
+    double V[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) V[d] = J * (-k2 * c.tau * R[d] + pg[d]) / c.rho;
+    add_test<Q>(r, J * (-k2 * div), V, g);
+  });
+  scatter<double, false>(m, idx, r, b);
+}
+
+// ---- velocity-update right-hand side (Def. weak_VMS_disc_vel_update), per component:
+//   (w, rho~ v_i) - (w, tau R_m,i) - (dt/2)(w, d_i (p_new - p_k))
+__global__ void __launch_bounds__(kRhsThreads)
+k_rhs_vu(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 v, Ptr3 uk,
+         const double* __restrict__ pk, const double* __restrict__ pn, double* __restrict__ b) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.n_elem) return;
+  int idx[8];
+  load_corners(m, e, idx);
+  const Geo<double> g = geometry<double>(m, e);
+  double pe[8], ue[3][8], me[8], pp[8], dpe[8], ve[3][8], uke[3][8];
+  gather<double, false>(m, idx, cf.phi, pe);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    gather<double, false>(m, idx, cf.u[d], ue[d]);
+    gather<double, false>(m, idx, v.c[d], ve[d]);
+    gather<double, false>(m, idx, uk.c[d], uke[d]);
+  }
+  gather<double, false>(m, idx, cf.mu, me);
+  gather<double, false>(m, idx, pk, pp);
+  gather<double, false>(m, idx, pn, dpe);
+#pragma unroll
+  for (int a = 0; a < 8; ++a) dpe[a] -= pp[a];
+  double r[3][8] = {{0}};
+  const double J = g.detJ;
+  for_qp([&](auto QC) {
+    constexpr int Q = decltype(QC)::value;
+    VmsQ<double> c = vms_at<Q>(pe, ue, me, g, p);
+    double F[3], pv, pg[3], R[3], vq[3], div, dv, dg[3];
+    forcing_at<Q>(pe, g, c.gphi, F);
+    vg_at<Q>(pp, g, pv, pg);
+    rm_at<Q>(c, p, F, pg, ve, uke, g, R, vq, div);
+    vg_at<Q>(dpe, g, dv, dg);
+    const double V0[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < 3; ++i)
+      add_test<Q>(r[i], J * (c.rho * vq[i] - c.tau * R[i] - 0.5 * p.dt * dg[i]), V0, g);
+  });
+  for (int i = 0; i < 3; ++i) scatter<double, true>(m, idx, r[i], b + i * m.n_nodes);
+}
+
+// ---- phi mass: sum_e detJ sum_q phi(q) = sum_e detJ sum_a phi_a (2-point Gauss weights sum to 1
+// per corner). Block partial sums, then a deterministic final sum on the host.
+__global__ void k_phi_mass(MeshDev m, const double* __restrict__ phi, double* __restrict__ part) {
+  __shared__ double sh[kRhsThreads];
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (e < m.n_elem) {
+    int idx[8];
+    load_corners(m, e, idx);
+    const Geo<double> g = geometry<double>(m, e);
+    double pe[8];
+    gather<double, false>(m, idx, phi, pe);
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) s += pe[a];
+    v = g.detJ * s;
+  }
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = kRhsThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+static unsigned nblk(const chns_mesh* m) {
+  return (unsigned)((m->d.n_elem + kRhsThreads - 1) / kRhsThreads);
+}
+
+static chns_status need(bool ok, const char* what) {
+  if (!ok) {
+    set_error(what);
+    return CHNS_EINVAL;
+  }
+  return CHNS_OK;
+}
+
+chns_status phi_mass(const chns_mesh* m, const double* phi, double* out, cudaStream_t s) {
+  const unsigned nb = nblk(m);
+  // partials live in the second v64 workspace slot tail-free region (n_elem/128 <= 3N)
+  double* part = m->ws.v64[kNumVec64 - 1];
+  note_launch();
+  k_phi_mass<<<nb, kRhsThreads, 0, s>>>(m->d, phi, part);
+  CHNS_CUDA(cudaGetLastError());
+  std::vector<double> h(nb);
+  CHNS_CUDA(cudaMemcpyAsync(h.data(), part, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CHNS_CUDA(cudaStreamSynchronize(s));
+  double acc = 0.0;
+  for (double v : h) acc += v;
+  *out = acc;
+  return CHNS_OK;
+}
+
+chns_status residual_ch(const chns_mesh* m, const chns_params* prm, const double* phi,
+                        const double* mu, const double* phik, const double* muk,
+                        const double* const u[3], double* f, cudaStream_t s) {
+  const DevParams p = make_dev_params(*prm);
+  Ptr3 up{{u[0], u[1], u[2]}};
+  CHNS_CUDA(cudaMemsetAsync(f, 0, 2 * m->d.n_nodes * sizeof(double), s));
+  note_launch();
+  k_residual_ch<<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, phi, mu, phik, muk, up, f);
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
+static CoefArgs<double> cargs(const chns_coef* c) {
+  CoefArgs<double> a;
+  a.phi = static_cast<const double*>(c->phi_tilde);
+  for (int d = 0; d < 3; ++d) a.u[d] = static_cast<const double*>(c->u_adv[d]);
+  a.mu = static_cast<const double*>(c->mu_tilde);
+  return a;
+}
+
+chns_status rhs_momentum(const chns_mesh* m, const chns_params* prm, const chns_coef* c,
+                         const double* const uk[3], const double* pk, double* b, cudaStream_t s) {
+  const DevParams p = make_dev_params(*prm);
+  CHNS_CUDA(cudaMemsetAsync(b, 0, 3 * m->d.n_nodes * sizeof(double), s));
+  note_launch();
+  k_rhs_momentum<<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, cargs(c), Ptr3{{uk[0], uk[1], uk[2]}},
+                                                 pk, b);
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
+chns_status rhs_poisson(const chns_mesh* m, const chns_params* prm, const chns_coef* c,
+                        const double* const v[3], const double* const uk[3], const double* pk,
+                        double* b, cudaStream_t s) {
+  const DevParams p = make_dev_params(*prm);
+  CHNS_CUDA(cudaMemsetAsync(b, 0, m->d.n_nodes * sizeof(double), s));
+  note_launch();
+  k_rhs_poisson<<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, cargs(c), Ptr3{{v[0], v[1], v[2]}},
+                                                Ptr3{{uk[0], uk[1], uk[2]}}, pk, b);
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
+chns_status rhs_vu(const chns_mesh* m, const chns_params* prm, const chns_coef* c,
+                   const double* const v[3], const double* const uk[3], const double* pk,
+                   const double* pn, double* b, cudaStream_t s) {
+  const DevParams p = make_dev_params(*prm);
+  CHNS_CUDA(cudaMemsetAsync(b, 0, 3 * m->d.n_nodes * sizeof(double), s));
+  note_launch();
+  k_rhs_vu<<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, cargs(c), Ptr3{{v[0], v[1], v[2]}},
+                                           Ptr3{{uk[0], uk[1], uk[2]}}, pk, pn, b);
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
+static bool coef_ok(const chns_coef* c) {
+  return c && c->phi_tilde && c->u_adv[0] && c->u_adv[1] && c->u_adv[2] && c->mu_tilde;
+}
+
+}  // namespace chns
+
+using namespace chns;
+
+extern "C" chns_status chns_residual_ch(const chns_mesh* m, const chns_params* prm,
+                                        const double* phi, const double* mu, const double* phik,
+                                        const double* muk, const double* const u[3], double* f,
+                                        void* stream) {
+  chns_status st = need(m && prm && phi && mu && phik && muk && u && u[0] && u[1] && u[2] && f,
+                        "chns_residual_ch: null argument");
+  if (st != CHNS_OK) return st;
+  return residual_ch(m, prm, phi, mu, phik, muk, u, f, as_stream(stream));
+}
+
+extern "C" chns_status chns_rhs_momentum(const chns_mesh* m, const chns_params* prm,
+                                         const chns_coef* c, const double* const uk[3],
+                                         const double* pk, double* b, void* stream) {
+  chns_status st = need(m && prm && coef_ok(c) && uk && uk[0] && uk[1] && uk[2] && pk && b,
+                        "chns_rhs_momentum: null argument");
+  if (st != CHNS_OK) return st;
+  return rhs_momentum(m, prm, c, uk, pk, b, as_stream(stream));
+}
+
+extern "C" chns_status chns_rhs_poisson(const chns_mesh* m, const chns_params* prm,
+                                        const chns_coef* c, const double* const v[3],
+                                        const double* const uk[3], const double* pk, double* b,
+                                        void* stream) {
+  chns_status st = need(m && prm && coef_ok(c) && v && v[0] && v[1] && v[2] && uk && uk[0] &&
+                            uk[1] && uk[2] && pk && b,
+                        "chns_rhs_poisson: null argument");
+  if (st != CHNS_OK) return st;
+  return rhs_poisson(m, prm, c, v, uk, pk, b, as_stream(stream));
+}
+
+extern "C" chns_status chns_rhs_velocity_update(const chns_mesh* m, const chns_params* prm,
+                                                const chns_coef* c, const double* const v[3],
+                                                const double* const uk[3], const double* pk,
+                                                const double* pn, double* b, void* stream) {
+  chns_status st = need(m && prm && coef_ok(c) && v && v[0] && v[1] && v[2] && uk && uk[0] &&
+                            uk[1] && uk[2] && pk && pn && b,
+                        "chns_rhs_velocity_update: null argument");
+  if (st != CHNS_OK) return st;
+  return rhs_vu(m, prm, c, v, uk, pk, pn, b, as_stream(stream));
+}
+
+extern "C" chns_status chns_phi_mass(const chns_mesh* m, const double* phi, double* out,
+                                     void* stream) {
+  chns_status st = need(m && phi && out, "chns_phi_mass: null argument");
+  if (st != CHNS_OK) return st;
+  return phi_mass(m, phi, out, as_stream(stream));
+}
