@@ -144,9 +144,11 @@ def run_ours(args):
             flush_l2()
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push("timed_step")
             e0.record()
             st = capi.chns_step(mesh.handle, ds.c, prm, sp)
             e1.record()
+            torch.cuda.nvtx.range_pop()
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
             for l in range(2):
@@ -172,15 +174,22 @@ def run_ours(args):
                     pp_refinements=last.pp[1].refinements)
 
     with ClockSampler(local) as clk:
-        headline = run_path(capi.FP32_BF16COEF, "fp32_bf16coef_fp64refine")
-        plain = run_path(capi.FP64, "fp64")
+        headline = plain = None
+        if args.paths in ("both", "headline"):
+            headline = run_path(capi.FP32_BF16COEF, "fp32_bf16coef_fp64refine")
+        if args.paths in ("both", "plain"):
+            plain = run_path(capi.FP64, "fp64")
     clocks = clk.summary()
+    if args.paths != "both":
+        if rank == 0:
+            print(json.dumps({"paths": args.paths, "detail": headline or plain, "clocks": clocks}))
+        return
 
     # ---- roofline of the dominant kernel: the matrix-free Poisson apply of the headline path,
     # timed alone from a cold L2 on the launching stream.
     stream = torch.cuda.current_stream()
     phit = torch.as_tensor(f0["phi"], device="cuda")
-    coef16 = phit.to(torch.bfloat16)
+    coef16 = (phit + 1.0).to(torch.bfloat16)  # BF16 storage holds 1 + phi~
     x32 = torch.randn(N, device="cuda", dtype=torch.float32)
     y32 = torch.empty_like(x32)
     c16 = capi.make_coef(coef16)
@@ -340,6 +349,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--paths", choices=["both", "headline", "plain"], default="both",
+                    help="time only one path and print a detail line (profiling runs)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the roofline kernel from an ncu capture")
     args = ap.parse_args()

@@ -21,7 +21,9 @@
  *     (component-major), e.g. the CH pair is [phi(0..N-1), mu(0..N-1)].
  *   - Memory: every vector/field pointer is a DEVICE pointer owned by the caller, contiguous,
  *     of the element type selected by the precision argument (double for CHNS_FP64, float for
- *     the FP32 modes; coefficient fields are uint16 bfloat16 for CHNS_FP32_BF16COEF). The
+ *     the FP32 modes; coefficient fields are uint16 bfloat16 for CHNS_FP32_BF16COEF, where the
+ *     phase field is stored shifted as bfloat16(1 + phi~) so that the relative error of
+ *     rho(phi) stays below 2^-8 even for large density ratios). The
  *     library owns the mesh tables and a device workspace allocated by chns_mesh_create;
  *     nothing is allocated on later calls.
  *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream). Applies are
@@ -69,6 +71,8 @@ typedef enum {
 } chns_operator;
 
 typedef enum { CHNS_KSP_CG = 0, CHNS_KSP_GMRES = 1 } chns_ksp;
+/* JACOBI: inverse of the exact diagonal; for CHNS_OP_CH the inverse of the exact 2x2 nodal
+ * (phi, mu) blocks. */
 typedef enum { CHNS_PC_NONE = 0, CHNS_PC_JACOBI = 1 } chns_pc;
 
 typedef struct chns_mesh chns_mesh;   /* opaque; owns device tables and workspace */
@@ -162,7 +166,9 @@ chns_status chns_phi_mass(const chns_mesh* mesh, const double* phi, double* out_
  * POISSON: b is projected to mean zero and x is returned with mean zero (pure Neumann).
  * inner_precision = CHNS_FP64 runs the whole Krylov iteration in FP64. The FP32 modes run the
  * Krylov iterations with FP32 vectors and applies, FP64 dot products, inside an FP64 iterative
- * refinement loop (r = b - A_64 x in FP64, correction solved to inner_rtol).
+ * refinement loop (r = b - A_64 x in FP64, correction solved to inner_rtol). A refinement cycle
+ * that fails to halve the FP64 residual raises the inner precision (BF16 coefficients -> FP32
+ * -> FP64 Krylov for the rest of the solve); stats report how often.
  * coef arrays are FP64; reduced-precision copies are made in the mesh workspace. */
 typedef struct {
   int32_t ksp;              /* chns_ksp */
@@ -183,6 +189,8 @@ typedef struct {
   double b_norm;
   int32_t status;           /* chns_status of the solve */
   float ms;                 /* device time of the solve (CUDA events) */
+  int32_t escalations;      /* refinement cycles that raised the inner precision */
+  int32_t final_precision;  /* chns_precision of the last inner iterations */
 } chns_solve_stats;
 
 chns_status chns_krylov_solve(const chns_mesh* mesh, chns_operator op, const chns_params* prm,

@@ -63,7 +63,7 @@ class chns_solver_params(C.Structure):
 class chns_solve_stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("refinements", C.c_int32),
                 ("rel_residual", C.c_double), ("b_norm", C.c_double), ("status", C.c_int32),
-                ("ms", C.c_float)]
+                ("ms", C.c_float), ("escalations", C.c_int32), ("final_precision", C.c_int32)]
 
 
 class chns_state(C.Structure):
@@ -171,7 +171,10 @@ def make_params(d) -> chns_params:
 
 
 def make_coef(phi=None, u=(None, None, None), mu=None) -> chns_coef:
-    return chns_coef(_ptr(phi), (C.c_void_p * 3)(*[_ptr(x) for x in u]), _ptr(mu))
+    """The C struct holds raw pointers; the returned object also keeps the arrays alive."""
+    c = chns_coef(_ptr(phi), (C.c_void_p * 3)(*[_ptr(x) for x in u]), _ptr(mu))
+    c._keep = (phi, tuple(u), mu)
+    return c
 
 
 def make_solver(ksp=KSP_CG, pc=PC_JACOBI, rtol=1e-8, max_it=10000, restart=30,

@@ -46,7 +46,8 @@ __device__ __forceinline__ int corner_ref(const MeshDev& m, int v, int k, double
 
 // Exact diagonal of P^T (sum_e A_e) P: for every node j touching the element (as a corner or as a
 // hanging-node parent), apply A_e to the local vector of j's basis function and take its j part.
-template <class K, class T, class S, class C>
+// BLOCK: the NC x NC nodal block instead, stored as d[(row*NC + col)*N + j].
+template <class K, class T, class S, class C, bool BLOCK = false>
 __global__ void __launch_bounds__(kApplyThreads) k_diag(MeshDev m, DevParams p, CoefArgs<C> cf,
                                                         S* __restrict__ d) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -92,6 +93,14 @@ __global__ void __launch_bounds__(kApplyThreads) k_diag(MeshDev m, DevParams p, 
         for (int c2 = 0; c2 < K::NC; ++c2)
           for (int b = 0; b < 8; ++b) xin[c2][b] = c2 == c ? lv[b] : T(0);
         k.apply(g, p, xin, r);
+        if (BLOCK) {
+          for (int r2 = 0; r2 < K::NC; ++r2) {
+            T bv = T(0);
+            for (int b = 0; b < 8; ++b) bv += lv[b] * r[r2][b];
+            atomic_add(d + (r2 * K::NC + c) * m.n_nodes + j, (S)bv);
+          }
+          continue;
+        }
         T dv = T(0);
         for (int b = 0; b < 8; ++b) dv += lv[b] * r[c][b];
         if (K::DIAG_PER_COMP) {
@@ -131,6 +140,7 @@ static CoefArgs<C> coef_args(const chns_coef* c) {
   a.phi = static_cast<const C*>(c->phi_tilde);
   for (int d = 0; d < 3; ++d) a.u[d] = static_cast<const C*>(c->u_adv[d]);
   a.mu = static_cast<const C*>(c->mu_tilde);
+  a.phi_shift = std::is_same<C, __nv_bfloat16>::value ? -1.0f : 0.0f;
   return a;
 }
 
@@ -279,6 +289,21 @@ chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm
       set_error("diagonal: bad precision");
       return CHNS_EINVAL;
   }
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
+// 2x2 nodal blocks of the CH Jacobian (FP64), d4 = [d_pp, d_pm, d_mp, d_mm] x N.
+chns_status block_diag_ch(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
+                          double* d4, cudaStream_t s) {
+  chns_status st = check_coef(CHNS_OP_CH, coef);
+  if (st != CHNS_OK) return st;
+  const DevParams p = make_dev_params(*prm);
+  CHNS_CUDA(cudaMemsetAsync(d4, 0, 4 * m->d.n_nodes * sizeof(double), s));
+  const unsigned nb = (unsigned)((m->d.n_elem + kApplyThreads - 1) / kApplyThreads);
+  note_launch();
+  k_diag<ChK<double, double>, double, double, double, true>
+      <<<nb, kApplyThreads, 0, s>>>(m->d, p, coef_args<double>(coef), d4);
   CHNS_CUDA(cudaGetLastError());
   return CHNS_OK;
 }

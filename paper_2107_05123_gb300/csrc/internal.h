@@ -96,12 +96,17 @@ chns_status apply_op(const chns_mesh* m, chns_operator op, const chns_params* pr
                      cudaStream_t s);
 chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
                     const chns_coef* coef, void* d, chns_precision prec, cudaStream_t s);
+// 2x2 nodal blocks of the CH Jacobian, d4 = [d_pp, d_pm, d_mp, d_mm] x n_nodes (FP64)
+chns_status block_diag_ch(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
+                          double* d4, cudaStream_t s);
 int op_ncomp(chns_operator op);
 bool op_dirichlet(chns_operator op);
 
 // ---- vector kernels (krylov.cu)
 void vec_convert_f64_f32(const double* a, float* b, int64_t n, cudaStream_t s);
-void vec_convert_f64_bf16(const double* a, __nv_bfloat16* b, int64_t n, cudaStream_t s);
+// b = bfloat16(a + offset)
+void vec_convert_f64_bf16(const double* a, __nv_bfloat16* b, int64_t n, double offset,
+                          cudaStream_t s);
 void vec_axpby(double a, const double* x, double b, const double* y, double* out, int64_t n,
                cudaStream_t s);
 void vec_copy(const double* x, double* y, int64_t n, cudaStream_t s);

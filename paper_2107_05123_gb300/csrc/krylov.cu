@@ -106,8 +106,8 @@ __global__ void k_convert(const TI* __restrict__ a, TO* __restrict__ b, int64_t 
   GRID_LOOP(i, n) b[i] = (TO)((double)a[i] * scale);
 }
 __global__ void k_convert_bf16(const double* __restrict__ a, __nv_bfloat16* __restrict__ b,
-                               int64_t n) {
-  GRID_LOOP(i, n) b[i] = __float2bfloat16_rn((float)a[i]);
+                               int64_t n, double offset) {
+  GRID_LOOP(i, n) b[i] = __float2bfloat16_rn((float)(a[i] + offset));
 }
 
 // x += factor * s[0]
@@ -138,6 +138,38 @@ template <class T>
 __global__ void k_mul(const T* __restrict__ dinv, const T* __restrict__ v, T* __restrict__ z,
                       int64_t n) {
   GRID_LOOP(i, n) z[i] = dinv ? dinv[i] * v[i] : v[i];
+}
+
+// Inverse of the 2x2 nodal blocks [a b; c d] (stored as 4 arrays of N), in place into `inv`.
+template <class T>
+__global__ void k_invert_b2(const double* d, T* inv, int64_t N) {  // d may alias inv
+  GRID_LOOP(i, N) {
+    const double a = d[i], b = d[N + i], c = d[2 * N + i], e = d[3 * N + i];
+    const double det = a * e - b * c;
+    const double scale = fabs(a * e) + fabs(b * c);
+    if (det != 0.0 && fabs(det) > 1e-14 * scale) {
+      inv[i] = (T)(e / det);
+      inv[N + i] = (T)(-b / det);
+      inv[2 * N + i] = (T)(-c / det);
+      inv[3 * N + i] = (T)(a / det);
+    } else {
+      inv[i] = (T)(a != 0.0 ? 1.0 / a : 1.0);
+      inv[N + i] = T(0);
+      inv[2 * N + i] = T(0);
+      inv[3 * N + i] = (T)(e != 0.0 ? 1.0 / e : 1.0);
+    }
+  }
+}
+
+// z = B^-1 v with 2x2 nodal blocks (the CH pair [phi; mu], N nodes)
+template <class T>
+__global__ void k_mul_b2(const T* __restrict__ inv, const T* __restrict__ v, T* __restrict__ z,
+                         int64_t N) {
+  GRID_LOOP(i, N) {
+    const T v0 = v[i], v1 = v[N + i];
+    z[i] = inv[i] * v0 + inv[N + i] * v1;
+    z[N + i] = inv[2 * N + i] * v0 + inv[3 * N + i] * v1;
+  }
 }
 
 // ---- CG: q = A p given. alpha = rz/pq; x += alpha p; r -= alpha q; z = dinv r;
@@ -219,6 +251,24 @@ __global__ void k_orth_update(const T* __restrict__ V, int64_t ld, int nk,
   }
 }
 
+// x += B^-1 (sum_k y_k V_k) with 2x2 nodal blocks
+template <class T>
+__global__ void k_gmres_update_b2(const T* __restrict__ V, int64_t ld, int nk,
+                                  const double* __restrict__ y, const T* __restrict__ inv,
+                                  T* __restrict__ x, int64_t N) {
+  GRID_LOOP(i, N) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int k = 0; k < nk; ++k) {
+      a0 += y[k] * (double)V[(int64_t)k * ld + i];
+      a1 += y[k] * (double)V[(int64_t)k * ld + N + i];
+    }
+    const double z0 = (double)inv[i] * a0 + (double)inv[N + i] * a1;
+    const double z1 = (double)inv[2 * N + i] * a0 + (double)inv[3 * N + i] * a1;
+    x[i] = (T)((double)x[i] + z0);
+    x[N + i] = (T)((double)x[N + i] + z1);
+  }
+}
+
 template <class T>
 __global__ void k_scale(T* __restrict__ a, double s, int64_t n) {
   GRID_LOOP(i, n) a[i] = (T)((double)a[i] * s);
@@ -264,9 +314,10 @@ void vec_convert_f64_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
   note_launch();
   k_convert<double, float><<<vgrid_n(n), kVecThreads, 0, s>>>(a, b, n, 1.0);
 }
-void vec_convert_f64_bf16(const double* a, __nv_bfloat16* b, int64_t n, cudaStream_t s) {
+void vec_convert_f64_bf16(const double* a, __nv_bfloat16* b, int64_t n, double offset,
+                          cudaStream_t s) {
   note_launch();
-  k_convert_bf16<<<vgrid_n(n), kVecThreads, 0, s>>>(a, b, n);
+  k_convert_bf16<<<vgrid_n(n), kVecThreads, 0, s>>>(a, b, n, offset);
 }
 void vec_add_scalar(double* x, const double* dev_scalar, double factor, int64_t n, cudaStream_t s) {
   note_launch();
@@ -403,8 +454,8 @@ chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, i
 // Right-preconditioned restarted GMRES with classical Gram-Schmidt and one re-orthogonalisation
 // pass; the second pass also returns w.w so that the new norm needs no extra reduction.
 template <class T>
-chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, int max_it,
-                  int restart, T* V, T* z, int* iters, double* rnorm) {
+chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, double tol_abs,
+                  int max_it, int restart, T* V, T* z, int* iters, double* rnorm) {
   const int64_t n = c.n, ld = n;
   const unsigned vg = vgrid(c.m, n);
   const unsigned mdb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(kMdBlocks, (n + 255) / 256));
@@ -440,7 +491,10 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs,
       T* vj = V + (int64_t)j * ld;
       T* w = V + (int64_t)(j + 1) * ld;
       note_launch();
-      k_mul<T><<<vg, kVecThreads, 0, c.s>>>(dinv, vj, z, n);
+      if (block2)
+        k_mul_b2<T><<<vg, kVecThreads, 0, c.s>>>(dinv, vj, z, n / 2);
+      else
+        k_mul<T><<<vg, kVecThreads, 0, c.s>>>(dinv, vj, z, n);
       st = apply_T<T>(c, z, w);
       if (st != CHNS_OK) return st;
       for (int i = 0; i <= j; ++i) Hij(i, j) = 0.0;
@@ -498,7 +552,10 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs,
     }
     CHNS_CUDA(cudaMemcpyAsync(hdev, y.data(), jend * sizeof(double), cudaMemcpyHostToDevice, c.s));
     note_launch();
-    k_gmres_update<T><<<vg, kVecThreads, 0, c.s>>>(V, ld, jend, hdev, dinv, x, n);
+    if (block2)
+      k_gmres_update_b2<T><<<vg, kVecThreads, 0, c.s>>>(V, ld, jend, hdev, dinv, x, n / 2);
+    else
+      k_gmres_update<T><<<vg, kVecThreads, 0, c.s>>>(V, ld, jend, hdev, dinv, x, n);
     CHNS_CUDA(cudaGetLastError());
     CHNS_CUDA(cudaStreamSynchronize(c.s));  // y (host) is reused next cycle
   }
@@ -524,7 +581,8 @@ static chns_status make_reduced_coef(const chns_mesh* m, const chns_coef* c, chn
       dst[k] = d;
     } else {
       __nv_bfloat16* d = static_cast<__nv_bfloat16*>(m->ws.coef16) + k * N;
-      vec_convert_f64_bf16(static_cast<const double*>(src[k]), d, N, s);
+      // phi~ is stored as 1 + phi~ (see gather_phi), the other fields as they are
+      vec_convert_f64_bf16(static_cast<const double*>(src[k]), d, N, k == 0 ? 1.0 : 0.0, s);
       dst[k] = d;
     }
   }
@@ -558,7 +616,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
   CHNS_CUDA(cudaEventCreate(&e1));
   CHNS_CUDA(cudaEventRecord(e0, s));
 
-  Ctx c;
+  Ctx c{};
   c.m = m;
   c.op = op;
   c.prm = prm;
@@ -585,12 +643,23 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
   const double bnorm = std::sqrt(bn2);
   chns_solve_stats out{};
   out.b_norm = bnorm;
+  out.final_precision = sp->inner_precision;
   if (bnorm == 0.0) {
     CHNS_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
   } else {
     // Jacobi preconditioner from the exact FP64 diagonal
     const double* dinv64 = nullptr;
-    if (sp->pc == CHNS_PC_JACOBI) {
+    // CH pair: 2x2 nodal block Jacobi (the phi and mu unknowns of a node are strongly coupled)
+    const bool block2 = (op == CHNS_OP_CH && sp->pc == CHNS_PC_JACOBI);
+    const int64_t Nn = m->d.n_nodes;
+    if (block2) {
+      double* d4 = ws.coef64 + 11 * Nn;
+      st = block_diag_ch(m, prm, coef, d4, s);
+      if (st != CHNS_OK) return st;
+      note_launch();
+      k_invert_b2<double><<<vgrid(m, Nn), kVecThreads, 0, s>>>(d4, d4, Nn);
+      dinv64 = d4;
+    } else if (sp->pc == CHNS_PC_JACOBI) {
       st = diag_op(m, op, prm, coef, d64, CHNS_FP64, s);
       if (st != CHNS_OK) return st;
       note_launch();
@@ -605,7 +674,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
         st = pcg<double>(c, b, x, dinv64, tol, sp->max_it, sp->check_every, r64, ws.v64[3],
                          ws.v64[4], ws.v64[5], &its, &rn);
       else
-        st = gmres<double>(c, b, x, dinv64, tol, sp->max_it, sp->restart, ws.gm_V, ws.v64[7],
+        st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it, sp->restart, ws.gm_V, ws.v64[7],
                            &its, &rn);
       out.iterations = its;
     } else {
@@ -615,11 +684,14 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
       float* d32 = ws.v32[1];
       float* dinv32 = nullptr;
       if (dinv64) {
-        dinv32 = ws.v32[2];
+        dinv32 = block2 ? static_cast<float*>(ws.coef32) + 6 * Nn : ws.v32[2];
+        const int64_t nd = block2 ? 4 * Nn : n;
         note_launch();
-        k_convert<double, float><<<vgrid(m, n), kVecThreads, 0, s>>>(dinv64, dinv32, n, 1.0);
+        k_convert<double, float><<<vgrid(m, nd), kVecThreads, 0, s>>>(dinv64, dinv32, nd, 1.0);
       }
       int total = 0, refine = 0;
+      double prev_rn = 0.0;
+      chns_precision cur = c.inner;
       for (;;) {
         // r64 = b - A_64 x
         st = apply_op(m, op, prm, coef, x, r64, CHNS_FP64, s);
@@ -644,6 +716,31 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
           st = CHNS_ENOTCONV;
           break;
         }
+        // A cycle that did not halve the FP64 residual means the reduced-precision operator is
+        // too far from the FP64 one: raise the inner precision (BF16 coefficients -> FP32 ->
+        // FP64 Krylov on the remaining correction).
+        if (refine > 0 && rn > 0.5 * prev_rn) {
+          ++out.escalations;
+          if (cur == CHNS_FP32_BF16COEF) {
+            cur = CHNS_FP32;
+            c.inner = cur;
+            st = make_reduced_coef(m, coef, cur, &c.coefR, s);
+            if (st != CHNS_OK) return st;
+          } else {
+            int its = 0;
+            double frn = 0.0;
+            if (sp->ksp == CHNS_KSP_CG)
+              st = pcg<double>(c, b, x, dinv64, tol, sp->max_it - total, sp->check_every, r64,
+                               ws.v64[3], ws.v64[4], ws.v64[5], &its, &frn);
+            else
+              st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it - total, sp->restart, ws.gm_V,
+                                 ws.v64[7], &its, &frn);
+            total += its;
+            cur = CHNS_FP64;
+            break;
+          }
+        }
+        prev_rn = rn;
         const double scale = 1.0 / rn;
         note_launch();
         k_convert<double, float><<<vgrid(m, n), kVecThreads, 0, s>>>(r64, r32, n, scale);
@@ -656,7 +753,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
           ist = pcg<float>(c, r32, d32, dinv32, itol, sp->max_it - total, sp->check_every,
                            ws.v32[3], ws.v32[4], ws.v32[5], ws.v32[6], &its, &irn);
         else
-          ist = gmres<float>(c, r32, d32, dinv32, itol, sp->max_it - total, sp->restart,
+          ist = gmres<float>(c, r32, d32, dinv32, block2, itol, sp->max_it - total, sp->restart,
                              ws.gm_V32, ws.v32[7], &its, &irn);
         if (ist != CHNS_OK && ist != CHNS_ENOTCONV) return ist;
         total += its;
@@ -668,6 +765,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
           break;
         }
       }
+      out.final_precision = cur;
       out.iterations = total;
       out.refinements = refine;
     }

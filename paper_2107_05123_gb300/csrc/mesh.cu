@@ -123,7 +123,7 @@ static chns_status alloc_workspace(chns_mesh* m) {
   CHNS_CUDA(cudaMalloc(&w.counter, 64 * sizeof(unsigned int)));
   CHNS_CUDA(cudaMemset(w.counter, 0, 64 * sizeof(unsigned int)));
   CHNS_CUDA(cudaMallocHost(&w.h_pinned, 1024 * sizeof(double)));
-  CHNS_CUDA(cudaMalloc(&w.coef32, (size_t)8 * N * sizeof(float)));
+  CHNS_CUDA(cudaMalloc(&w.coef32, (size_t)10 * N * sizeof(float)));
   CHNS_CUDA(cudaMalloc(&w.coef16, (size_t)8 * N * sizeof(__nv_bfloat16)));
   CHNS_CUDA(cudaMalloc(&w.coef64, (size_t)16 * N * sizeof(double)));
   return CHNS_OK;

@@ -11,10 +11,22 @@ namespace chns {
 
 template <class C>
 struct CoefArgs {
-  const C* phi;     // phi~
+  const C* phi;     // phi~ (bfloat16 storage holds 1 + phi~, see phi_shift)
   const C* u[3];    // advecting velocity (u_hat or u~)
   const C* mu;      // mu~
+  float phi_shift;  // added to the stored phi values: -1 for bfloat16 storage, else 0
 };
+
+// Gather phi~ of an element. In bfloat16 storage the field is s = 1 + phi~, whose relative
+// precision bounds the relative error of rho(phi) = alpha s + rho_- by 2^-8 even where
+// rho_- << 1 (phi near -1); the shift is removed after interpolation (linear in s).
+template <class T, class C>
+__device__ __forceinline__ void gather_phi(const MeshDev& m, const int idx[8],
+                                           const CoefArgs<C>& cf, T pe[8]) {
+  gather<T, false>(m, idx, cf.phi, pe);
+#pragma unroll
+  for (int a = 0; a < 8; ++a) pe[a] += T(cf.phi_shift);
+}
 
 // ---------------------------------------------------------------- pressure Poisson
 // (grad q, (1/rho(phi~*)) grad p) (Def. weak_VMS_disc_pp_vel, scalar test q).
@@ -57,7 +69,7 @@ struct PoissonK {
   __device__ __forceinline__ void load(const MeshDev& m, const DevParams& p, const CoefArgs<C>& cf,
                                        const int idx[8], const Geo<T>& g) {
     T pe[8];
-    gather<T, false>(m, idx, cf.phi, pe);
+    gather_phi(m, idx, cf, pe);
     poisson_coef(pe, g, p, c);
   }
   __device__ __forceinline__ void apply(const Geo<T>& g, const DevParams&, const T x[NC][8],
@@ -77,7 +89,7 @@ struct MassK {
   __device__ __forceinline__ void load(const MeshDev& m, const DevParams& p, const CoefArgs<C>& cf,
                                        const int idx[8], const Geo<T>& g) {
     T pe[8], pq[8];
-    gather<T, false>(m, idx, cf.phi, pe);
+    gather_phi(m, idx, cf, pe);
     interp3(pe, pq);
 #pragma unroll
     for (int q = 0; q < 8; ++q) c[q] = g.detJ * (T(p.alpha) * clamp1(pq[q]) + T(p.beta));
@@ -109,7 +121,7 @@ struct ChK {
   T ue[3][8];
   __device__ __forceinline__ void load(const MeshDev& m, const DevParams&, const CoefArgs<C>& cf,
                                        const int idx[8], const Geo<T>&) {
-    gather<T, false>(m, idx, cf.phi, pe);
+    gather_phi(m, idx, cf, pe);
 #pragma unroll
     for (int d = 0; d < 3; ++d) gather<T, false>(m, idx, cf.u[d], ue[d]);
   }
@@ -205,7 +217,7 @@ struct MomK {
   T me[8];
   __device__ __forceinline__ void load(const MeshDev& m, const DevParams&, const CoefArgs<C>& cf,
                                        const int idx[8], const Geo<T>&) {
-    gather<T, false>(m, idx, cf.phi, pe);
+    gather_phi(m, idx, cf, pe);
 #pragma unroll
     for (int d = 0; d < 3; ++d) gather<T, false>(m, idx, cf.u[d], ue[d]);
     gather<T, false>(m, idx, cf.mu, me);

@@ -290,6 +290,7 @@ static CoefArgs<double> cargs(const chns_coef* c) {
   a.phi = static_cast<const double*>(c->phi_tilde);
   for (int d = 0; d < 3; ++d) a.u[d] = static_cast<const double*>(c->u_adv[d]);
   a.mu = static_cast<const double*>(c->mu_tilde);
+  a.phi_shift = 0.0f;
   return a;
 }
 

@@ -3,6 +3,7 @@
 // prediction (GMRES), pressure Poisson (CG, mean zero), velocity update (CG). The host only
 // orchestrates; every field operation runs in the library's kernels on the given stream.
 #include <cmath>
+#include <string>
 
 #include "internal.h"
 
@@ -12,6 +13,12 @@ namespace chns {
 static void lin(double a, const double* x, double b, const double* y, double* out, int64_t n,
                 cudaStream_t s) {
   vec_axpby(a, x, b, y, out, n, s);
+}
+
+// Prefix the current error message with the phase of the step that failed.
+static chns_status phase_fail(const char* phase, chns_status rc) {
+  set_error(std::string("chns_step: ") + phase + ": " + chns_last_error());
+  return rc;
 }
 
 struct Timer {
@@ -94,7 +101,7 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
         chns_coef cc{phit, {util[0], util[1], util[2]}, nullptr};
         CHNS_CUDA(cudaMemsetAsync(dx, 0, 2 * N * sizeof(double), s));
         rc = krylov_solve(m, CHNS_OP_CH, prm, &cc, f, dx, &sp->ch, &ks, s);
-        if (rc != CHNS_OK) return rc;
+        if (rc != CHNS_OK) return phase_fail("Cahn-Hilliard Newton step", rc);
         lin(1.0, xch, -1.0, dx, xch, 2 * N, s);
         rc = residual_ch(m, prm, xch, xch + N, phik, muk, ut, f, s);
         if (rc != CHNS_OK) return rc;
@@ -126,7 +133,7 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
       for (int d = 0; d < 3; ++d)
         CHNS_CUDA(cudaMemcpyAsync(v + d * N, uk[d], N * sizeof(double), cudaMemcpyDeviceToDevice, s));
       rc = krylov_solve(m, CHNS_OP_MOMENTUM, prm, &cv, bv, v, &sp->vp, &S.vp[l], s);
-      if (rc != CHNS_OK) return rc;
+      if (rc != CHNS_OK) return phase_fail("velocity prediction", rc);
       S.ms_vp += t.stop();
     }
     // ---- pressure Poisson (warm start from p^k)
@@ -136,7 +143,7 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
       if (rc != CHNS_OK) return rc;
       CHNS_CUDA(cudaMemcpyAsync(pnew, st->p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
       rc = krylov_solve(m, CHNS_OP_POISSON, prm, &cv, bv, pnew, &sp->pp, &S.pp[l], s);
-      if (rc != CHNS_OK) return rc;
+      if (rc != CHNS_OK) return phase_fail("pressure Poisson", rc);
       S.ms_pp += t.stop();
     }
     // ---- velocity update
@@ -146,7 +153,7 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
       if (rc != CHNS_OK) return rc;
       CHNS_CUDA(cudaMemcpyAsync(un, v, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
       rc = krylov_solve(m, CHNS_OP_MASS, prm, &cv, bv, un, &sp->vu, &S.vu[l], s);
-      if (rc != CHNS_OK) return rc;
+      if (rc != CHNS_OK) return phase_fail("velocity update", rc);
       S.ms_vu += t.stop();
     }
     for (int d = 0; d < 3; ++d) ublk[d] = un + d * N;

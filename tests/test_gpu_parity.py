@@ -50,15 +50,20 @@ def test_apply_fp64(name, op):
 @pytest.mark.parametrize("prec", [capi.FP32, capi.FP32_BF16COEF])
 @pytest.mark.parametrize("op", OPS)
 def test_apply_reduced_precision(op, prec):
+    """The oracle sees exactly the rounded inputs the kernel sees. In BF16 coefficient storage the
+    phase field is stored as bfloat16(1 + phi~) (the C ABI's convention)."""
     om, gm = meshes("drop_l3_5")
     f = fields(om.n_nodes, 21 + op)
-    rnd = bf16_round if prec == capi.FP32_BF16COEF else f32_round
-    phi, u, mu = rnd(f["phi"]), rnd(f["u"]), rnd(f["mu"])
     nc = capi.OP_NCOMP[op]
     x = f32_round(f["x"][:nc].ravel())
+    if prec == capi.FP32_BF16COEF:
+        s16 = bf16_round(1.0 + f["phi"])
+        phi, u, mu = s16 - 1.0, bf16_round(f["u"]), bf16_round(f["mu"])
+        cdt, ph = torch.bfloat16, dev(s16).to(torch.bfloat16)
+    else:
+        phi, u, mu = f32_round(f["phi"]), f32_round(f["u"]), f32_round(f["mu"])
+        cdt, ph = torch.float32, dev(phi).to(torch.float32)
     A = oracle_operator(om, op, PRM, phi, u, mu)
-    cdt = torch.bfloat16 if prec == capi.FP32_BF16COEF else torch.float32
-    ph = dev(phi).to(cdt)
     uu = [dev(u[i]).to(cdt) for i in range(3)]
     mm = dev(mu).to(cdt)
     y = torch.zeros(nc * gm.n_nodes, dtype=torch.float32, device="cuda")
