@@ -6,6 +6,7 @@
 // recomputed from the octant level, and scatter-adds the result (hanging corners distributed
 // back to their parents), i.e. y = P^T (sum_e A_e) P x without storing any matrix.
 #include "ops.cuh"
+#include "reduce.cuh"
 
 namespace chns {
 
@@ -28,6 +29,35 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(MeshDev m, DevParams p,
   k.apply(g, p, xin, r);
 #pragma unroll
   for (int c = 0; c < K::NC; ++c) scatter<T, K::DIR>(m, idx, r[c], y + c * m.n_nodes);
+}
+
+// k_apply with the element energy x_e . (A_e x_e) summed in FP64: with y = A x this is x^T A x,
+// the p.Ap of a CG iteration, obtained without reading y back. y must be zero on entry.
+template <class K, class T, class S, class C>
+__global__ void __launch_bounds__(kApplyThreads)
+k_apply_pq(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S* __restrict__ y,
+           double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ pq) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double en[1] = {0.0};
+  if (e < m.n_elem) {
+    int idx[8];
+    load_corners(m, e, idx);
+    const Geo<T> g = geometry<T>(m, e);
+    K k;
+    k.load(m, p, cf, idx, g);
+    T xin[K::NC][8];
+#pragma unroll
+    for (int c = 0; c < K::NC; ++c) gather<T, K::DIR>(m, idx, x + c * m.n_nodes, xin[c]);
+    T r[K::NC][8];
+    k.apply(g, p, xin, r);
+#pragma unroll
+    for (int c = 0; c < K::NC; ++c) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a) en[0] += (double)xin[c][a] * (double)r[c][a];
+      scatter<T, K::DIR>(m, idx, r[c], y + c * m.n_nodes);
+    }
+  }
+  block_reduce_finalize<1, kApplyThreads>(en, part, 0, counter, pq);
 }
 
 // Reference (corner a, slot k) -> node reference with Dirichlet bit and its weight, or -1.
@@ -287,6 +317,41 @@ chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm
       break;
     default:
       set_error("diagonal: bad precision");
+      return CHNS_EINVAL;
+  }
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
+chns_status apply_poisson_pq(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
+                             const void* x, void* y, chns_precision prec, double* pq,
+                             cudaStream_t s) {
+  chns_status st = check_coef(CHNS_OP_POISSON, coef);
+  if (st != CHNS_OK) return st;
+  const DevParams p = make_dev_params(*prm);
+  const unsigned nb = (unsigned)((m->d.n_elem + kApplyThreads - 1) / kApplyThreads);
+  double* part = m->ws.part_big;
+  unsigned* ctr = m->ws.counter + 1;
+  note_launch();
+  switch (prec) {
+    case CHNS_FP64:
+      k_apply_pq<PoissonK<double, double>, double, double, double><<<nb, kApplyThreads, 0, s>>>(
+          m->d, p, coef_args<double>(coef), static_cast<const double*>(x),
+          static_cast<double*>(y), part, ctr, pq);
+      break;
+    case CHNS_FP32:
+      k_apply_pq<PoissonK<float, float>, float, float, float><<<nb, kApplyThreads, 0, s>>>(
+          m->d, p, coef_args<float>(coef), static_cast<const float*>(x), static_cast<float*>(y),
+          part, ctr, pq);
+      break;
+    case CHNS_FP32_BF16COEF:
+      k_apply_pq<PoissonK<float, __nv_bfloat16>, float, float, __nv_bfloat16>
+          <<<nb, kApplyThreads, 0, s>>>(m->d, p, coef_args<__nv_bfloat16>(coef),
+                                        static_cast<const float*>(x), static_cast<float*>(y), part,
+                                        ctr, pq);
+      break;
+    default:
+      set_error("apply: bad precision");
       return CHNS_EINVAL;
   }
   CHNS_CUDA(cudaGetLastError());

@@ -11,6 +11,9 @@ static thread_local std::string g_last_error;
 static std::atomic<unsigned long long> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+void note_launches_undo(unsigned long long k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
+unsigned long long chns_launches_now() { return g_launches.load(); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 

@@ -40,6 +40,7 @@ struct Workspace {
   void* coef32 = nullptr;      // reduced-precision coefficient copies (5 fields, float)
   void* coef16 = nullptr;      // bf16 copies (5 fields)
   double* coef64 = nullptr;    // FP64 step coefficients (phi~, u_hat x3, mu~ + scratch)
+  double* part_big = nullptr;  // per-block partials of element-level reductions (n_elem/64+64)
 };
 
 }  // namespace chns
@@ -57,6 +58,7 @@ struct chns_mesh {
   uint32_t* d_anchor = nullptr;
   int32_t* d_bnd = nullptr;          // boundary node indices (n_boundary)
   chns::Workspace ws;
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture CUDA graphs
   int red_blocks = 0;
   int sm_count = 0;
 };
@@ -64,8 +66,12 @@ struct chns_mesh {
 namespace chns {
 
 void set_error(const std::string& msg);
-// count of kernel launches issued by the library (diagnostic)
+// count of kernel launches issued by the library (diagnostic); graph launches add the number of
+// kernels they contain, and launches recorded during a stream capture are taken back out
 void note_launch();
+void note_launches(unsigned long long k);
+void note_launches_undo(unsigned long long k);
+unsigned long long chns_launches_now();
 chns_status cuda_fail(cudaError_t e, const char* what);
 
 #define CHNS_CUDA(call)                                          \
@@ -94,6 +100,11 @@ constexpr int kScalarBase = 3 * 4096;  // scalars stored after three partial arr
 chns_status apply_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
                      const chns_coef* coef, const void* x, void* y, chns_precision prec,
                      cudaStream_t s);
+// y = A x for the Poisson operator with y already zero, also writing p.Ap (= x^T A x, summed
+// element by element in FP64) to pq_dev; deterministic reduction.
+chns_status apply_poisson_pq(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
+                             const void* x, void* y, chns_precision prec, double* pq_dev,
+                             cudaStream_t s);
 chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
                     const chns_coef* coef, void* d, chns_precision prec, cudaStream_t s);
 // 2x2 nodal blocks of the CH Jacobian, d4 = [d_pp, d_pm, d_mp, d_mm] x n_nodes (FP64)

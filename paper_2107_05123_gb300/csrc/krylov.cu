@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "reduce.cuh"
 
 namespace chns {
 
@@ -24,51 +25,12 @@ constexpr int kMdBlocks = 256;  // blocks per multi-dot row (partials: rows x kM
 enum Slot { S_RZ0 = 0, S_RZ1 = 1, S_PQ = 2, S_RR = 3, S_TMP = 8, S_AUX = 16, S_MD = 64 };
 
 // ------------------------------------------------------------------ device kernels
-// Block reduction of NV sums, partials per block, fixed-order final sum in the last block.
+// Block reduction of NV sums with the fixed-order last-block finalisation of reduce.cuh.
 template <int NV>
 __device__ __forceinline__ void reduce_finalize(double v[NV], double* __restrict__ part,
                                                 unsigned* __restrict__ counter,
                                                 double* __restrict__ out) {
-  __shared__ double sh[NV][kVecThreads];
-  __shared__ bool last;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = v[k];
-  __syncthreads();
-  for (int w = kVecThreads / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) part[k * kRedSlots + blockIdx.x] = sh[k][0];
-    __threadfence();
-    unsigned t = atomicAdd(counter, 1u);
-    last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double s = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += kVecThreads)
-      s += ((volatile double*)part)[k * kRedSlots + b];
-    sh[k][threadIdx.x] = s;
-  }
-  __syncthreads();
-  for (int w = kVecThreads / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) out[k] = sh[k][0];
-    *counter = 0u;
-  }
+  block_reduce_finalize<NV, kVecThreads>(v, part, kRedSlots, counter, out);
 }
 
 #define GRID_LOOP(i, n)                                                     \
@@ -196,13 +158,17 @@ k_cg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __
 }
 
 // beta = rz_new / rz_old; p = z + beta p; rotate rz into the other parity slot; publish r.r.
+// With q != null also clear q for the next apply (its scatter accumulates into zero).
 template <class T>
-__global__ void k_cg_pupdate(T* __restrict__ p, const T* __restrict__ z, int64_t n,
-                             double* __restrict__ S, int parity) {
+__global__ void k_cg_pupdate(T* __restrict__ p, const T* __restrict__ z, T* __restrict__ q,
+                             int64_t n, double* __restrict__ S, int parity) {
   const double rz_old = S[S_RZ0 + parity], rz_new = S[S_TMP];
   const double beta = rz_old != 0.0 ? rz_new / rz_old : 0.0;
   const T b = (T)beta;
-  GRID_LOOP(i, n) p[i] = z[i] + b * p[i];
+  GRID_LOOP(i, n) {
+    p[i] = z[i] + b * p[i];
+    if (q) q[i] = T(0);
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     S[S_RZ0 + (parity ^ 1)] = rz_new;
     S[S_RR] = S[S_TMP + 1];
@@ -398,11 +364,46 @@ chns_status project_mean(const Ctx& c, T* v) {
   return CHNS_OK;
 }
 
+// One CG iteration: q = A p and p.q, then x, r, z and r.z, r.r, then p = z + beta p.
+// Poisson: the apply also returns p.Ap (element energies) and q is cleared by the p update, so an
+// iteration is three kernels. Other operators: apply (clears q itself), dot, update, p update.
+template <class T>
+chns_status cg_iteration(const Ctx& c, cudaStream_t s, T* x, T* r, T* z, T* p, T* q,
+                         const T* dinv, int par) {
+  const int64_t n = c.n;
+  const unsigned rg = red_grid(c.m, n), vg = vgrid(c.m, n);
+  const bool fused = c.op == CHNS_OP_POISSON;
+  chns_status st;
+  if (fused) {
+    if (sizeof(T) == sizeof(double))
+      st = apply_poisson_pq(c.m, c.prm, c.coef64, p, q, CHNS_FP64, c.S + S_PQ, s);
+    else
+      st = apply_poisson_pq(c.m, c.prm, &c.coefR, p, q, c.inner, c.S + S_PQ, s);
+    if (st != CHNS_OK) return st;
+  } else {
+    Ctx cs = c;
+    cs.s = s;
+    st = apply_T<T>(cs, p, q);
+    if (st != CHNS_OK) return st;
+    note_launch();
+    k_dot<T, T><<<rg, kVecThreads, 0, s>>>(p, q, n, c.m->ws.red, c.m->ws.counter, c.S + S_PQ);
+  }
+  note_launch();
+  k_cg_update<T><<<rg, kVecThreads, 0, s>>>(x, r, z, p, q, dinv, n, c.S, par, c.m->ws.red,
+                                            c.m->ws.counter);
+  note_launch();
+  k_cg_pupdate<T><<<vg, kVecThreads, 0, s>>>(p, z, fused ? q : nullptr, n, c.S, par);
+  return CHNS_OK;
+}
+
 // Preconditioned CG on A x = b (type T); x holds the initial guess. Runs until sqrt(r.r) <= tol_abs
-// (checked every check_every iterations) or max_it iterations.
+// or max_it iterations. With chunk >= 2 the iterations run as CUDA graphs of `chunk` iterations
+// (captured once per solve on a private stream); two graph instances write r.r into alternating
+// pinned host slots so the host checks chunk k while chunk k+1 already runs. The solve may do up
+// to two chunks beyond the iteration that reached the tolerance; they only reduce the residual.
 template <class T>
 chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, int max_it,
-                int check_every, T* r, T* z, T* p, T* q, int* iters, double* rnorm) {
+                int chunk, T* r, T* z, T* p, T* q, int* iters, double* rnorm) {
   const int64_t n = c.n;
   const unsigned rg = red_grid(c.m, n), vg = vgrid(c.m, n);
   chns_status st = apply_T<T>(c, x, q);
@@ -413,6 +414,7 @@ chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, i
   note_launch();
   k_mul<T><<<vg, kVecThreads, 0, c.s>>>(dinv, r, z, n);
   CHNS_CUDA(cudaMemcpyAsync(p, z, n * sizeof(T), cudaMemcpyDeviceToDevice, c.s));
+  CHNS_CUDA(cudaMemsetAsync(q, 0, n * sizeof(T), c.s));
   note_launch();
   k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, z, n, c.m->ws.red, c.m->ws.counter, c.S + S_RZ0);
   note_launch();
@@ -420,30 +422,95 @@ chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, i
   CHNS_CUDA(cudaGetLastError());
   int it = 0;
   double rr = 0.0;
-  check_every = std::max(1, check_every);
-  for (;;) {
-    if (it % check_every == 0 || it >= max_it) {
+  st = read_dev(c.m, c.S + S_RR, &rr, 1, c.s);
+  if (st != CHNS_OK) return st;
+  auto bad = [&](double v) {
+    if (std::isfinite(v)) return false;
+    set_error("krylov: NaN/Inf in the residual norm");
+    return true;
+  };
+  if (bad(rr)) {
+    *iters = 0;
+    *rnorm = rr;
+    return CHNS_ENAN;
+  }
+  if (chunk < 2) {
+    while (std::sqrt(rr) > tol_abs && it < max_it) {
+      st = cg_iteration<T>(c, c.s, x, r, z, p, q, dinv, it & 1);
+      if (st != CHNS_OK) return st;
+      ++it;
       st = read_dev(c.m, c.S + S_RR, &rr, 1, c.s);
       if (st != CHNS_OK) return st;
-      if (!std::isfinite(rr)) {
+      if (bad(rr)) {
         *iters = it;
         *rnorm = rr;
-        set_error("krylov: NaN/Inf in the residual norm");
         return CHNS_ENAN;
       }
-      if (std::sqrt(rr) <= tol_abs || it >= max_it) break;
     }
-    const int par = it & 1;
-    st = apply_T<T>(c, p, q);
-    if (st != CHNS_OK) return st;
-    note_launch();
-    k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(p, q, n, c.m->ws.red, c.m->ws.counter, c.S + S_PQ);
-    note_launch();
-    k_cg_update<T><<<rg, kVecThreads, 0, c.s>>>(x, r, z, p, q, dinv, n, c.S, par, c.m->ws.red,
-                                                c.m->ws.counter);
-    note_launch();
-    k_cg_pupdate<T><<<vg, kVecThreads, 0, c.s>>>(p, z, n, c.S, par);
-    ++it;
+  } else if (std::sqrt(rr) > tol_abs && max_it > 0) {
+    chunk += chunk & 1;  // even: every chunk starts at parity 0
+    cudaStream_t cs = c.m->cap_stream;
+    cudaGraphExec_t ge[2] = {nullptr, nullptr};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    volatile double* slot = c.m->ws.h_pinned + 8;
+    unsigned long long per_graph = 0;
+    chns_status rc = CHNS_OK;
+    for (int v = 0; v < 2 && rc == CHNS_OK; ++v) {
+      cudaGraph_t g = nullptr;
+      CHNS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      const unsigned long long l0 = chns_launches_now();
+      for (int i = 0; i < chunk && rc == CHNS_OK; ++i)
+        rc = cg_iteration<T>(c, cs, x, r, z, p, q, dinv, i & 1);
+      cudaMemcpyAsync((void*)(slot + v), c.S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, cs);
+      per_graph = chns_launches_now() - l0;
+      cudaError_t e1 = cudaStreamEndCapture(cs, &g);
+      if (rc != CHNS_OK) {
+        if (g) cudaGraphDestroy(g);
+        break;
+      }
+      if (e1 != cudaSuccess) return cuda_fail(e1, "cudaStreamEndCapture");
+      cudaError_t e2 = cudaGraphInstantiate(&ge[v], g, 0);
+      cudaGraphDestroy(g);
+      if (e2 != cudaSuccess) return cuda_fail(e2, "cudaGraphInstantiate");
+      CHNS_CUDA(cudaEventCreateWithFlags(&ev[v], cudaEventDisableTiming));
+    }
+    note_launches_undo(2 * per_graph);  // captured, not executed
+    if (rc == CHNS_OK) {
+      int k = 0;
+      bool done = false;
+      while (!done) {
+        const int v = k & 1;
+        CHNS_CUDA(cudaGraphLaunch(ge[v], c.s));
+        note_launches(per_graph);
+        CHNS_CUDA(cudaEventRecord(ev[v], c.s));
+        it += chunk;
+        // check the previous chunk while this one runs
+        if (k >= 1) {
+          CHNS_CUDA(cudaEventSynchronize(ev[v ^ 1]));
+          rr = slot[v ^ 1];
+          if (bad(rr) || std::sqrt(rr) <= tol_abs) done = true;
+        }
+        if (done || it >= max_it) {
+          CHNS_CUDA(cudaEventSynchronize(ev[v]));
+          const double last = slot[v];
+          if (!bad(last)) rr = last;
+          else rr = last;
+          done = true;
+        }
+        ++k;
+      }
+    }
+    for (int v = 0; v < 2; ++v) {
+      if (ge[v]) cudaGraphExecDestroy(ge[v]);
+      if (ev[v]) cudaEventDestroy(ev[v]);
+    }
+    if (rc != CHNS_OK) return rc;
+    if (!std::isfinite(rr)) {
+      *iters = it;
+      *rnorm = rr;
+      set_error("krylov: NaN/Inf in the residual norm");
+      return CHNS_ENAN;
+    }
   }
   CHNS_CUDA(cudaGetLastError());
   *iters = it;

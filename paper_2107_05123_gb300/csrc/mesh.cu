@@ -126,6 +126,8 @@ static chns_status alloc_workspace(chns_mesh* m) {
   CHNS_CUDA(cudaMalloc(&w.coef32, (size_t)10 * N * sizeof(float)));
   CHNS_CUDA(cudaMalloc(&w.coef16, (size_t)8 * N * sizeof(__nv_bfloat16)));
   CHNS_CUDA(cudaMalloc(&w.coef64, (size_t)16 * N * sizeof(double)));
+  CHNS_CUDA(cudaMalloc(&w.part_big, (size_t)(m->d.n_elem / 64 + 64) * sizeof(double)));
+  CHNS_CUDA(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
   return CHNS_OK;
 }
 
@@ -151,6 +153,8 @@ static void free_mesh(chns_mesh* m) {
   dfree(w.coef32);
   dfree(w.coef16);
   dfree(w.coef64);
+  dfree(w.part_big);
+  if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
   delete m;
 }
 

@@ -1,0 +1,58 @@
+// Deterministic FP64 block reductions with last-block finalisation: every block writes its
+// partial sums to part[k * pstride + blockIdx.x]; the last block to finish (atomic ticket) sums
+// the partials in a fixed order, writes out[k] and resets the ticket. The result does not depend
+// on block scheduling.
+#pragma once
+
+#include "internal.h"
+
+namespace chns {
+
+template <int NV, int BS>
+__device__ __forceinline__ void block_reduce_finalize(double v[NV], double* __restrict__ part,
+                                                      int64_t pstride,
+                                                      unsigned* __restrict__ counter,
+                                                      double* __restrict__ out) {
+  __shared__ double sh[NV][BS];
+  __shared__ bool last;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = v[k];
+  __syncthreads();
+  for (int w = BS / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) part[k * pstride + blockIdx.x] = sh[k][0];
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += BS)
+      s += ((volatile double*)part)[k * pstride + b];
+    sh[k][threadIdx.x] = s;
+  }
+  __syncthreads();
+  for (int w = BS / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = sh[k][0];
+    *counter = 0u;
+  }
+}
+
+}  // namespace chns

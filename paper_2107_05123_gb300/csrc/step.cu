@@ -96,11 +96,23 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
       fn = f0;
       int its = 0;
       chns_solve_stats ks{};
-      while (fn > std::max(sp->newton_rtol * f0, sp->newton_atol) && its < sp->newton_max_it) {
+      // Inexact Newton: each linear solve only needs the accuracy the nonlinear iteration can
+      // use (Eisenstat-Walker forcing eta_k = 0.9 (|F_k|/|F_k-1|)^2, eta_0 = 1e-3, at most 1e-3),
+      // never tighter than what reaches the Newton target in one step (0.5 target/|F_k|), and
+      // never tighter than the CH solver's rtol.
+      const double target = std::max(sp->newton_rtol * f0, sp->newton_atol);
+      double fprev = f0;
+      while (fn > target && its < sp->newton_max_it) {
+        double eta = 1e-3;
+        if (its > 0) eta = std::min(1e-3, 0.9 * (fn / fprev) * (fn / fprev));
+        eta = std::max(eta, 0.5 * target / fn);
+        chns_solver_params chp = sp->ch;
+        chp.rtol = std::max(eta, sp->ch.rtol);
+        fprev = fn;
         lin(0.5, xch, 0.5, phik, phit, N, s);
         chns_coef cc{phit, {util[0], util[1], util[2]}, nullptr};
         CHNS_CUDA(cudaMemsetAsync(dx, 0, 2 * N * sizeof(double), s));
-        rc = krylov_solve(m, CHNS_OP_CH, prm, &cc, f, dx, &sp->ch, &ks, s);
+        rc = krylov_solve(m, CHNS_OP_CH, prm, &cc, f, dx, &chp, &ks, s);
         if (rc != CHNS_OK) return phase_fail("Cahn-Hilliard Newton step", rc);
         lin(1.0, xch, -1.0, dx, xch, 2 * N, s);
         rc = residual_ch(m, prm, xch, xch + N, phik, muk, ut, f, s);
