@@ -17,7 +17,7 @@ Operators (readings of ambiguous passages are listed by number in the design not
 * velocity update (Def. weak_VMS_disc_vel_update): (w, rho~ u)
 * velocity prediction (Def. weak_VMS_disc): the linear operator in v^{c,k+1} with the RBVMS
   closure rho~ v^f = -tau_m R_m, tau_m with C_I = 6 and G = diag(4/h^2) [readings R1, R3, R4, R5, R8]
-  (R4: tau_m = (4/dt^2 + a.G.a + C_I (eta/(rho Re))^2 G:G)^(-1/2), a = u_hat + J_hat/(rho Pe))
+  (R4: the mixed term u.G.J/(rho Pe) of the printed tau_m is bounded below by -u.G.u)
 * Cahn-Hilliard (Def. weak_VMS_disc_CH): residual and Newton Jacobian in (phi^{k+1}, mu^{k+1})
   [reading R2: the diffusion term enters with a plus sign, as in the strong form]
 
@@ -192,12 +192,12 @@ class VMSState:
         self.uh = np.stack([el.val(u_hat[i]) for i in range(3)], axis=-1)
         self.J = -(co.alpha / co.Cn) * el.grad(mu_t)                   # [R5]
         G = el.gGd[:, None, :]                                          # (E, 1, 3)
-        # advection velocity of the operator: rho u_hat.grad v + (1/Pe) J.grad v = rho a.grad v
-        # with a = u_hat + J/(rho Pe); tau_m uses a.G.a [reading R4: the printed radicand with
-        # u.G.u + u.G.J/(rho Pe) can be negative where J/(rho Pe) >> u]
-        a = self.uh + self.J / (self.rho[..., None] * co.Pe)
-        t = (4.0 / co.dt ** 2
-             + np.sum(a * G * a, axis=-1)
+        # printed tau_m; its mixed term u.G.J/(rho Pe) is bounded below by -u.G.u so that the
+        # radicand stays >= 4/dt^2 + C_I (eta/(rho Re))^2 G:G [reading R4: unbounded, the printed
+        # radicand goes negative where J/(rho Pe) >> u]
+        ugu = np.sum(self.uh * G * self.uh, axis=-1)
+        ugj = (1.0 / (self.rho * co.Pe)) * np.sum(self.uh * G * self.J, axis=-1)
+        t = (4.0 / co.dt ** 2 + ugu + np.maximum(ugj, -ugu)
              + co.C_I * (self.eta / (self.rho * co.Re)) ** 2 * np.sum(G ** 2, axis=-1))
         self.tau = t ** -0.5
         # forcing d_j(d_i phi d_j phi) from the element Hessian (reading R8)

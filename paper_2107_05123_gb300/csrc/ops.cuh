@@ -155,9 +155,9 @@ struct ChK {
 // Per-quadrature-point coefficients of the momentum operator (Def. weak_VMS_disc):
 //   rho~, eta~ from clamp(phi~); grad eta~ = gamma grad phi~ where |phi~| < 1;
 //   J_hat = -(alpha/Cn) grad mu~; G = diag(4/h^2);
-//   tau_m = (4/dt^2 + a.G.a + C_I (eta/(rho Re))^2 G:G)^(-1/2) with a = u + J/(rho Pe), the
-//   advection velocity of the operator (the printed radicand u.G.u + u.G.J/(rho Pe) + ... can be
-//   negative where J/(rho Pe) dominates u; a.G.a keeps it positive).
+//   tau_m = (4/dt^2 + u.G.u + max(u.G.J/(rho Pe), -u.G.u) + C_I (eta/(rho Re))^2 G:G)^(-1/2):
+//   the printed formula with its mixed term bounded below, since unbounded the radicand goes
+//   negative where J/(rho Pe) dominates u.
 // The operator on one velocity component v (the same for each component):
 //   s = rho/dt v + 1/2 rho u.grad v + 1/(2Pe) J.grad v                       (tested with N_a)
 //   R = s - 1/(2Re) grad eta . grad v                                        (R^lin)
@@ -185,19 +185,20 @@ __device__ __forceinline__ VmsQ<T> vms_at(const T pe[8], const T ue[3][8], const
   const T ka = T(-p.alpha / p.Cn);
   const T ir = T(1) / o.rho;
   const T jpe = ir / T(p.Pe);
-  T aga = T(0), gg = T(0);
+  T ugu = T(0), ugj = T(0), gg = T(0);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     o.ge[d] = inside ? T(p.gamma) * o.gphi[d] : T(0);
     o.J[d] = ka * mg[d];
     T Gd = T(4) * g.ih[d] * g.ih[d];
-    const T ad = o.uq[d] + jpe * o.J[d];
-    aga += ad * Gd * ad;
+    ugu += o.uq[d] * Gd * o.uq[d];
+    ugj += o.uq[d] * Gd * o.J[d];
     gg += Gd * Gd;
   }
   const T er = o.eta * ir / T(p.Re);
   const T idt = T(1.0 / p.dt);
-  o.tau = rsqrt(T(4) * idt * idt + aga + T(p.C_I) * er * er * gg);
+  ugj *= jpe;
+  o.tau = rsqrt(T(4) * idt * idt + ugu + (ugj > -ugu ? ugj : -ugu) + T(p.C_I) * er * er * gg);
   o.a0 = o.rho * idt;
   o.e = o.eta * T(0.5 / p.Re);
   const T h2pe = T(0.5 / p.Pe), h2re = T(0.5 / p.Re);

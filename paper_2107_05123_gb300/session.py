@@ -35,7 +35,8 @@ class Mesh:
             pass
 
 
-def default_step_params(rtol=1e-8, inner=capi.FP64, pp_check_every=8, inner_rtol=1e-5):
+def default_step_params(rtol=1e-8, inner=capi.FP64, pp_check_every=8, inner_rtol=1e-5,
+                        newton_rtol=1e-10):
     """Solver settings of a time step: GMRES for CH and velocity prediction, Jacobi-PCG for the
     pressure Poisson and velocity update, all to the relative residual rtol. In the FP32 modes each
     refinement cycle solves its correction to inner_rtol (CG) or 10 x inner_rtol (GMRES)."""
@@ -45,7 +46,7 @@ def default_step_params(rtol=1e-8, inner=capi.FP64, pp_check_every=8, inner_rtol
                           check_every=pp_check_every)
     cgv = capi.make_solver(capi.KSP_CG, capi.PC_JACOBI, rtol, 4000, 30, inner, inner_rtol,
                            check_every=pp_check_every)
-    return capi.chns_step_params(gm, gm, cg, cgv, 1e-10, 1e-14, 10, 2)
+    return capi.chns_step_params(gm, gm, cg, cgv, newton_rtol, 1e-14, 10, 2)
 
 
 class DeviceState:
