@@ -167,9 +167,12 @@ chns_status chns_phi_mass(const chns_mesh* mesh, const double* phi, double* out_
  * inner_precision = CHNS_FP64 runs the whole Krylov iteration in FP64. The FP32 modes run the
  * Krylov iterations with FP32 vectors and applies, FP64 dot products, inside an FP64 iterative
  * refinement loop (r = b - A_64 x in FP64, correction solved to inner_rtol). A refinement cycle
- * that fails to halve the FP64 residual raises the inner precision (BF16 coefficients -> FP32
+ * that fails to reduce the FP64 residual by 4x raises the inner precision (BF16 coefficients -> FP32
  * -> FP64 Krylov for the rest of the solve); stats report how often.
- * coef arrays are FP64; reduced-precision copies are made in the mesh workspace. */
+ * coef arrays are FP64; reduced-precision copies are made in the mesh workspace. In
+ * CHNS_FP32_BF16COEF mode the bfloat16 copies are used by the memory-bound POISSON and MASS
+ * applies; CH and MOMENTUM inner applies use FP32 coefficients. The Jacobi preconditioner is
+ * computed in the precision of the Krylov iteration that uses it. */
 typedef struct {
   int32_t ksp;              /* chns_ksp */
   int32_t pc;               /* chns_pc */

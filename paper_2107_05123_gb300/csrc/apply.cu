@@ -60,6 +60,157 @@ k_apply_pq(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S* _
   block_reduce_finalize<1, kApplyThreads>(en, part, 0, counter, pq);
 }
 
+// Patch apply: one CTA per patch (kPatchElems Morton-consecutive elements, one thread each).
+//  1. the patch's regular slots are gathered once into shared memory (input components and
+//     coefficient fields), Dirichlet nodes as zero for DIR operators;
+//  2. hanging slots are interpolated there from their parent slots (mean of 2 or 4);
+//  3. each thread applies its element operator reading its 8 corners from shared memory and adds
+//     the result into shared accumulators (shared-memory atomics);
+//  4. hanging accumulators are distributed to their parents with the same weights;
+//  5. each regular slot is written once: a plain store when the patch owns the node, a global
+//     atomic add otherwise (nodes on the patch boundary). y must be zero on entry.
+// With PQ the element energies x_e . A_e x_e are summed into pq (x^T A x, deterministic).
+template <class K, class T, class S, class C, bool PQ>
+__global__ void __launch_bounds__(kPatchElems)
+k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S* __restrict__ y,
+              double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ pq) {
+  constexpr int NC = K::NC, NF = K::NF;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw);       // [NC][kPatchSlots]
+  T* ys = xs + NC * kPatchSlots;                // [NC][kPatchSlots]
+  T* fs = ys + NC * kPatchSlots;                // [NF][kPatchSlots]
+  const int pidx = blockIdx.x;
+  const int s0 = m.patch_slot[pidx], ns = m.patch_slot[pidx + 1] - s0, nreg = m.patch_nreg[pidx];
+  const int64_t N = m.n_nodes;
+  const C* fptr[5] = {cf.phi, cf.u[0], cf.u[1], cf.u[2], cf.mu};
+  // 1. regular slots
+  for (int i = threadIdx.x; i < nreg; i += blockDim.x) {
+    const int32_t v = m.slot_node[s0 + i];
+    const int64_t g = v & kNodeMask;
+    const bool dir = K::DIR && (v & kDirBit);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      xs[c * kPatchSlots + i] = dir ? T(0) : (T)x[c * N + g];
+      ys[c * kPatchSlots + i] = T(0);
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T val = ldv<T>(fptr[f], g);
+      if (f == 0) val += T(cf.phi_shift);
+      fs[f * kPatchSlots + i] = val;
+    }
+  }
+  __syncthreads();
+  // 2. hanging slots
+  for (int i = nreg + threadIdx.x; i < ns; i += blockDim.x) {
+    const ushort4 q = m.slot_par[s0 + i];
+    const bool four = q.z != 0xffff;
+    const T w = four ? T(0.25) : T(0.5);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const T* a = xs + c * kPatchSlots;
+      T v = a[q.x] + a[q.y];
+      if (four) v += a[q.z] + a[q.w];
+      xs[c * kPatchSlots + i] = w * v;
+      ys[c * kPatchSlots + i] = T(0);
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const T* a = fs + f * kPatchSlots;
+      T v = a[q.x] + a[q.y];
+      if (four) v += a[q.z] + a[q.w];
+      fs[f * kPatchSlots + i] = w * v;
+    }
+  }
+  __syncthreads();
+  // 3. elements
+  double en[1] = {0.0};
+  const int64_t e = (int64_t)m.patch_elem[pidx] + threadIdx.x;
+  if (e < m.patch_elem[pidx + 1]) {
+    const uint4 lp = __ldg(m.eloc + e);
+    const int sl[8] = {(int)(lp.x & 0xffff), (int)(lp.x >> 16), (int)(lp.y & 0xffff),
+                       (int)(lp.y >> 16),    (int)(lp.z & 0xffff), (int)(lp.z >> 16),
+                       (int)(lp.w & 0xffff), (int)(lp.w >> 16)};
+    const Geo<T> g = geometry<T>(m, e);
+    T fe[NF][8];
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) fe[f][a] = fs[f * kPatchSlots + sl[a]];
+    K k;
+    k.setup(fe, g, p);
+    T xin[NC][8];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) xin[c][a] = xs[c * kPatchSlots + sl[a]];
+    T r[NC][8];
+    k.apply(g, p, xin, r);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        if (PQ) en[0] += (double)xin[c][a] * (double)r[c][a];
+        atomicAdd(ys + c * kPatchSlots + sl[a], r[c][a]);
+      }
+  }
+  __syncthreads();
+  // 4. hanging slots -> parents
+  for (int i = nreg + threadIdx.x; i < ns; i += blockDim.x) {
+    const ushort4 q = m.slot_par[s0 + i];
+    const bool four = q.z != 0xffff;
+    const T w = four ? T(0.25) : T(0.5);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T* a = ys + c * kPatchSlots;
+      const T v = w * a[i];
+      atomicAdd(a + q.x, v);
+      atomicAdd(a + q.y, v);
+      if (four) {
+        atomicAdd(a + q.z, v);
+        atomicAdd(a + q.w, v);
+      }
+    }
+  }
+  __syncthreads();
+  // 5. regular slots -> global
+  for (int i = threadIdx.x; i < nreg; i += blockDim.x) {
+    const int32_t v = m.slot_node[s0 + i];
+    if (K::DIR && (v & kDirBit)) continue;
+    const int64_t g = v & kNodeMask;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const S val = (S)ys[c * kPatchSlots + i];
+      if (v & kOwnBit)
+        y[c * N + g] = val;
+      else
+        atomic_add(y + c * N + g, val);
+    }
+  }
+  if (PQ) block_reduce_finalize<1, kPatchElems>(en, part, 0, counter, pq);
+}
+
+template <class K, class T>
+constexpr size_t patch_smem() {
+  return (size_t)(2 * K::NC + K::NF) * kPatchSlots * sizeof(T);
+}
+
+// Launch the patch apply, raising the dynamic shared-memory limit once per instantiation.
+template <class K, class T, class S, class C, bool PQ>
+static void launch_patch(const chns_mesh* m, const DevParams& p, const CoefArgs<C>& cf,
+                         const S* x, S* y, double* pq, cudaStream_t s) {
+  constexpr size_t smem = patch_smem<K, T>();
+  static bool configured = false;  // per instantiation
+  if (!configured) {
+    cudaFuncSetAttribute(k_apply_patch<K, T, S, C, PQ>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = true;
+  }
+  note_launch();
+  k_apply_patch<K, T, S, C, PQ><<<(unsigned)m->d.n_patch, kPatchElems, smem, s>>>(
+      m->d, p, cf, x, y, m->ws.part_big, m->ws.counter + 1, pq);
+}
+
 // Reference (corner a, slot k) -> node reference with Dirichlet bit and its weight, or -1.
 __device__ __forceinline__ int corner_ref(const MeshDev& m, int v, int k, double& w) {
   int j = v & kIdxMask;
@@ -186,24 +337,18 @@ static chns_status check_coef(chns_operator op, const chns_coef* c) {
 template <class T, class S, class C>
 static void launch_apply(const chns_mesh* m, chns_operator op, const DevParams& p,
                          const CoefArgs<C>& cf, const S* x, S* y, cudaStream_t s) {
-  const int64_t E = m->d.n_elem;
-  const unsigned nb = (unsigned)((E + kApplyThreads - 1) / kApplyThreads);
   switch (op) {
     case CHNS_OP_POISSON:
-      note_launch();
-      k_apply<PoissonK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cf, x, y);
+      launch_patch<PoissonK<T, C>, T, S, C, false>(m, p, cf, x, y, nullptr, s);
       break;
     case CHNS_OP_MASS:
-      note_launch();
-      k_apply<MassK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cf, x, y);
+      launch_patch<MassK<T, C>, T, S, C, false>(m, p, cf, x, y, nullptr, s);
       break;
     case CHNS_OP_CH:
-      note_launch();
-      k_apply<ChK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cf, x, y);
+      launch_patch<ChK<T, C>, T, S, C, false>(m, p, cf, x, y, nullptr, s);
       break;
     case CHNS_OP_MOMENTUM:
-      note_launch();
-      k_apply<MomK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cf, x, y);
+      launch_patch<MomK<T, C>, T, S, C, false>(m, p, cf, x, y, nullptr, s);
       break;
   }
 }
@@ -329,26 +474,21 @@ chns_status apply_poisson_pq(const chns_mesh* m, const chns_params* prm, const c
   chns_status st = check_coef(CHNS_OP_POISSON, coef);
   if (st != CHNS_OK) return st;
   const DevParams p = make_dev_params(*prm);
-  const unsigned nb = (unsigned)((m->d.n_elem + kApplyThreads - 1) / kApplyThreads);
-  double* part = m->ws.part_big;
-  unsigned* ctr = m->ws.counter + 1;
-  note_launch();
   switch (prec) {
     case CHNS_FP64:
-      k_apply_pq<PoissonK<double, double>, double, double, double><<<nb, kApplyThreads, 0, s>>>(
-          m->d, p, coef_args<double>(coef), static_cast<const double*>(x),
-          static_cast<double*>(y), part, ctr, pq);
+      launch_patch<PoissonK<double, double>, double, double, double, true>(
+          m, p, coef_args<double>(coef), static_cast<const double*>(x), static_cast<double*>(y),
+          pq, s);
       break;
     case CHNS_FP32:
-      k_apply_pq<PoissonK<float, float>, float, float, float><<<nb, kApplyThreads, 0, s>>>(
-          m->d, p, coef_args<float>(coef), static_cast<const float*>(x), static_cast<float*>(y),
-          part, ctr, pq);
+      launch_patch<PoissonK<float, float>, float, float, float, true>(
+          m, p, coef_args<float>(coef), static_cast<const float*>(x), static_cast<float*>(y), pq,
+          s);
       break;
     case CHNS_FP32_BF16COEF:
-      k_apply_pq<PoissonK<float, __nv_bfloat16>, float, float, __nv_bfloat16>
-          <<<nb, kApplyThreads, 0, s>>>(m->d, p, coef_args<__nv_bfloat16>(coef),
-                                        static_cast<const float*>(x), static_cast<float*>(y), part,
-                                        ctr, pq);
+      launch_patch<PoissonK<float, __nv_bfloat16>, float, float, __nv_bfloat16, true>(
+          m, p, coef_args<__nv_bfloat16>(coef), static_cast<const float*>(x),
+          static_cast<float*>(y), pq, s);
       break;
     default:
       set_error("apply: bad precision");
@@ -358,17 +498,26 @@ chns_status apply_poisson_pq(const chns_mesh* m, const chns_params* prm, const c
   return CHNS_OK;
 }
 
-// 2x2 nodal blocks of the CH Jacobian (FP64), d4 = [d_pp, d_pm, d_mp, d_mm] x N.
+// 2x2 nodal blocks of the CH Jacobian, d4 = [d_pp, d_pm, d_mp, d_mm] x N, in FP64 or FP32.
 chns_status block_diag_ch(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
-                          double* d4, cudaStream_t s) {
+                          void* d4, chns_precision prec, cudaStream_t s) {
   chns_status st = check_coef(CHNS_OP_CH, coef);
   if (st != CHNS_OK) return st;
   const DevParams p = make_dev_params(*prm);
-  CHNS_CUDA(cudaMemsetAsync(d4, 0, 4 * m->d.n_nodes * sizeof(double), s));
   const unsigned nb = (unsigned)((m->d.n_elem + kApplyThreads - 1) / kApplyThreads);
   note_launch();
-  k_diag<ChK<double, double>, double, double, double, true>
-      <<<nb, kApplyThreads, 0, s>>>(m->d, p, coef_args<double>(coef), d4);
+  if (prec == CHNS_FP64) {
+    CHNS_CUDA(cudaMemsetAsync(d4, 0, 4 * m->d.n_nodes * sizeof(double), s));
+    k_diag<ChK<double, double>, double, double, double, true>
+        <<<nb, kApplyThreads, 0, s>>>(m->d, p, coef_args<double>(coef), static_cast<double*>(d4));
+  } else if (prec == CHNS_FP32) {
+    CHNS_CUDA(cudaMemsetAsync(d4, 0, 4 * m->d.n_nodes * sizeof(float), s));
+    k_diag<ChK<float, float>, float, float, float, true>
+        <<<nb, kApplyThreads, 0, s>>>(m->d, p, coef_args<float>(coef), static_cast<float*>(d4));
+  } else {
+    set_error("block diagonal: bad precision");
+    return CHNS_EINVAL;
+  }
   CHNS_CUDA(cudaGetLastError());
   return CHNS_OK;
 }

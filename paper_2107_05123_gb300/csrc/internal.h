@@ -15,6 +15,13 @@ namespace chns {
 // Element corner indices carry the Dirichlet flag in bit 30; bit 31 is never set.
 constexpr int32_t kDirBit = 1 << 30;
 constexpr int32_t kIdxMask = kDirBit - 1;
+// Patch slot entries: node id (< 2^29) | kOwnBit (only this patch touches the node) | kDirBit.
+constexpr int32_t kOwnBit = 1 << 29;
+constexpr int32_t kNodeMask = kOwnBit - 1;
+// A patch is a run of Morton-consecutive elements processed by one CTA (one thread per element)
+// whose distinct nodes (regular nodes and hanging corners) fit in kPatchSlots shared slots.
+constexpr int kPatchElems = 256;
+constexpr int kPatchSlots = 1024;
 
 // Device view of the mesh tables (passed by value to kernels).
 struct MeshDev {
@@ -26,6 +33,14 @@ struct MeshDev {
   const int4* hang;      // [n_hang] parents (with Dirichlet bit); .z=.w=-1 for edge midpoints
   const uint32_t* anchor;  // [n_elem*3] (only for diagnostics needing positions)
   double ext[3];         // physical extent
+  // patch tables
+  int64_t n_patch;
+  const int32_t* patch_elem;  // [n_patch+1] first element of each patch
+  const int32_t* patch_slot;  // [n_patch+1] first slot of each patch (regular slots, then hanging)
+  const int32_t* patch_nreg;  // [n_patch] regular slots of each patch
+  const int32_t* slot_node;   // [slots] regular slot: node id | kOwnBit | kDirBit
+  const ushort4* slot_par;    // [slots] hanging slot: local parent slots (0xffff = none)
+  const uint4* eloc;          // [n_elem] 8 local slot indices (uint16) per element
 };
 
 struct Workspace {
@@ -57,6 +72,13 @@ struct chns_mesh {
   int4* d_hang = nullptr;
   uint32_t* d_anchor = nullptr;
   int32_t* d_bnd = nullptr;          // boundary node indices (n_boundary)
+  int32_t* d_patch_elem = nullptr;
+  int32_t* d_patch_slot = nullptr;
+  int32_t* d_patch_nreg = nullptr;
+  int32_t* d_slot_node = nullptr;
+  ushort4* d_slot_par = nullptr;
+  uint4* d_eloc = nullptr;
+  int64_t n_slots = 0;
   chns::Workspace ws;
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture CUDA graphs
   int red_blocks = 0;
@@ -107,9 +129,9 @@ chns_status apply_poisson_pq(const chns_mesh* m, const chns_params* prm, const c
                              cudaStream_t s);
 chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
                     const chns_coef* coef, void* d, chns_precision prec, cudaStream_t s);
-// 2x2 nodal blocks of the CH Jacobian, d4 = [d_pp, d_pm, d_mp, d_mm] x n_nodes (FP64)
+// 2x2 nodal blocks of the CH Jacobian, d4 = [d_pp, d_pm, d_mp, d_mm] x n_nodes (FP64 or FP32)
 chns_status block_diag_ch(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
-                          double* d4, cudaStream_t s);
+                          void* d4, chns_precision prec, cudaStream_t s);
 int op_ncomp(chns_operator op);
 bool op_dirichlet(chns_operator op);
 

@@ -87,11 +87,12 @@ __global__ void k_accumulate(double* __restrict__ x, const T* __restrict__ d, do
   GRID_LOOP(i, n) x[i] += scale * (double)d[i];
 }
 
-template <class T>
-__global__ void k_invert(const double* __restrict__ d, T* __restrict__ dinv, int64_t n) {
+// dinv = 1/d (1 where d == 0); d may alias dinv
+template <class TI, class TO>
+__global__ void k_invert(const TI* d, TO* dinv, int64_t n) {
   GRID_LOOP(i, n) {
-    double v = d[i];
-    dinv[i] = (T)(v != 0.0 ? 1.0 / v : 1.0);
+    const double v = (double)d[i];
+    dinv[i] = (TO)(v != 0.0 ? 1.0 / v : 1.0);
   }
 }
 
@@ -103,8 +104,8 @@ __global__ void k_mul(const T* __restrict__ dinv, const T* __restrict__ v, T* __
 }
 
 // Inverse of the 2x2 nodal blocks [a b; c d] (stored as 4 arrays of N), in place into `inv`.
-template <class T>
-__global__ void k_invert_b2(const double* d, T* inv, int64_t N) {  // d may alias inv
+template <class TI, class T>
+__global__ void k_invert_b2(const TI* d, T* inv, int64_t N) {  // d may alias inv
   GRID_LOOP(i, N) {
     const double a = d[i], b = d[N + i], c = d[2 * N + i], e = d[3 * N + i];
     const double det = a * e - b * c;
@@ -714,51 +715,79 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
   if (bnorm == 0.0) {
     CHNS_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
   } else {
-    // Jacobi preconditioner from the exact FP64 diagonal
-    const double* dinv64 = nullptr;
-    // CH pair: 2x2 nodal block Jacobi (the phi and mu unknowns of a node are strongly coupled)
-    const bool block2 = (op == CHNS_OP_CH && sp->pc == CHNS_PC_JACOBI);
+    // Jacobi preconditioner: the operator's exact diagonal (2x2 nodal blocks for the CH pair,
+    // whose phi and mu unknowns are strongly coupled), computed in the precision of the Krylov
+    // iteration that uses it.
+    const bool jac = sp->pc == CHNS_PC_JACOBI;
+    const bool block2 = (op == CHNS_OP_CH && jac);
     const int64_t Nn = m->d.n_nodes;
-    if (block2) {
-      double* d4 = ws.coef64 + 11 * Nn;
-      st = block_diag_ch(m, prm, coef, d4, s);
-      if (st != CHNS_OK) return st;
-      note_launch();
-      k_invert_b2<double><<<vgrid(m, Nn), kVecThreads, 0, s>>>(d4, d4, Nn);
-      dinv64 = d4;
-    } else if (sp->pc == CHNS_PC_JACOBI) {
-      st = diag_op(m, op, prm, coef, d64, CHNS_FP64, s);
-      if (st != CHNS_OK) return st;
-      note_launch();
-      k_invert<double><<<vgrid(m, n), kVecThreads, 0, s>>>(d64, d64, n);
-      dinv64 = d64;
-    }
+    const double* dinv64 = nullptr;
+    auto make_dinv64 = [&]() -> chns_status {
+      if (!jac || dinv64) return CHNS_OK;
+      chns_status r;
+      if (block2) {
+        double* d4 = ws.coef64 + 11 * Nn;
+        r = block_diag_ch(m, prm, coef, d4, CHNS_FP64, s);
+        if (r != CHNS_OK) return r;
+        note_launch();
+        k_invert_b2<double, double><<<vgrid(m, Nn), kVecThreads, 0, s>>>(d4, d4, Nn);
+        dinv64 = d4;
+      } else {
+        r = diag_op(m, op, prm, coef, d64, CHNS_FP64, s);
+        if (r != CHNS_OK) return r;
+        note_launch();
+        k_invert<double, double><<<vgrid(m, n), kVecThreads, 0, s>>>(d64, d64, n);
+        dinv64 = d64;
+      }
+      return CHNS_OK;
+    };
     const double tol = sp->rtol * bnorm;
     if (c.inner == CHNS_FP64) {
+      st = make_dinv64();
+      if (st != CHNS_OK) return st;
       int its = 0;
       double rn = 0.0;
       if (sp->ksp == CHNS_KSP_CG)
         st = pcg<double>(c, b, x, dinv64, tol, sp->max_it, sp->check_every, r64, ws.v64[3],
                          ws.v64[4], ws.v64[5], &its, &rn);
       else
-        st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it, sp->restart, ws.gm_V, ws.v64[7],
-                           &its, &rn);
+        st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it, sp->restart, ws.gm_V,
+                           ws.v64[7], &its, &rn);
       out.iterations = its;
     } else {
-      st = make_reduced_coef(m, coef, c.inner, &c.coefR, s);
+      // FP32 coefficient copies; the preconditioner is computed from them in FP32.
+      chns_coef coef32;
+      st = make_reduced_coef(m, coef, CHNS_FP32, &coef32, s);
       if (st != CHNS_OK) return st;
       float* r32 = ws.v32[0];
       float* d32 = ws.v32[1];
       float* dinv32 = nullptr;
-      if (dinv64) {
-        dinv32 = block2 ? static_cast<float*>(ws.coef32) + 6 * Nn : ws.v32[2];
-        const int64_t nd = block2 ? 4 * Nn : n;
+      if (block2) {
+        dinv32 = static_cast<float*>(ws.coef32) + 6 * Nn;
+        st = block_diag_ch(m, prm, &coef32, dinv32, CHNS_FP32, s);
+        if (st != CHNS_OK) return st;
         note_launch();
-        k_convert<double, float><<<vgrid(m, nd), kVecThreads, 0, s>>>(dinv64, dinv32, nd, 1.0);
+        k_invert_b2<float, float><<<vgrid(m, Nn), kVecThreads, 0, s>>>(dinv32, dinv32, Nn);
+      } else if (jac) {
+        dinv32 = ws.v32[2];
+        st = diag_op(m, op, prm, &coef32, dinv32, CHNS_FP32, s);
+        if (st != CHNS_OK) return st;
+        note_launch();
+        k_invert<float, float><<<vgrid(m, n), kVecThreads, 0, s>>>(dinv32, dinv32, n);
+      }
+      // bfloat16 coefficient storage only where the apply is memory bound (Poisson, mass); the
+      // CH and momentum applies are arithmetic bound and use mu~ through its gradient.
+      if (c.inner == CHNS_FP32_BF16COEF && (op == CHNS_OP_POISSON || op == CHNS_OP_MASS)) {
+        st = make_reduced_coef(m, coef, CHNS_FP32_BF16COEF, &c.coefR, s);
+        if (st != CHNS_OK) return st;
+      } else {
+        c.inner = CHNS_FP32;
+        c.coefR = coef32;
       }
       int total = 0, refine = 0;
       double prev_rn = 0.0;
       chns_precision cur = c.inner;
+      (void)d32;
       for (;;) {
         // r64 = b - A_64 x
         st = apply_op(m, op, prm, coef, x, r64, CHNS_FP64, s);
@@ -786,14 +815,15 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
         // A cycle that did not halve the FP64 residual means the reduced-precision operator is
         // too far from the FP64 one: raise the inner precision (BF16 coefficients -> FP32 ->
         // FP64 Krylov on the remaining correction).
-        if (refine > 0 && rn > 0.5 * prev_rn) {
+        if (refine > 0 && rn > 0.25 * prev_rn) {
           ++out.escalations;
           if (cur == CHNS_FP32_BF16COEF) {
             cur = CHNS_FP32;
             c.inner = cur;
-            st = make_reduced_coef(m, coef, cur, &c.coefR, s);
-            if (st != CHNS_OK) return st;
+            c.coefR = coef32;
           } else {
+            st = make_dinv64();
+            if (st != CHNS_OK) return st;
             int its = 0;
             double frn = 0.0;
             if (sp->ksp == CHNS_KSP_CG)

@@ -10,6 +10,7 @@
 // interpolation from the immediate parent of Fig. "traversal". Under the full 2:1 balance the
 // parents of a hanging node are never hanging themselves; this is checked.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cstring>
 #include <numeric>
@@ -142,6 +143,12 @@ static void free_mesh(chns_mesh* m) {
   dfree(m->d_hang);
   dfree(m->d_anchor);
   dfree(m->d_bnd);
+  dfree(m->d_patch_elem);
+  dfree(m->d_patch_slot);
+  dfree(m->d_patch_nreg);
+  dfree(m->d_slot_node);
+  dfree(m->d_slot_par);
+  dfree(m->d_eloc);
   Workspace& w = m->ws;
   for (auto p : w.v64) dfree(p);
   for (auto p : w.v32) dfree(p);
@@ -156,6 +163,119 @@ static void free_mesh(chns_mesh* m) {
   dfree(w.part_big);
   if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
   delete m;
+}
+
+// Greedy partition of the Morton-ordered elements into patches (see kPatchElems/kPatchSlots):
+// regular slots = distinct nodes used as corners or as parents of hanging corners, hanging slots
+// = distinct hanging corners; a node is owned by a patch when no other patch has it as a slot.
+struct PatchTables {
+  std::vector<int32_t> elem, slot, nreg, node;
+  std::vector<ushort4> par;
+  std::vector<uint4> eloc;
+};
+
+static void build_patches(int64_t n, int64_t N, const std::vector<int32_t>& enode,
+                          const std::vector<int4>& hang, PatchTables& P) {
+  std::vector<int32_t> stamp_n(N, -1), slot_n(N, 0), stamp_h(hang.size(), -1), slot_h(hang.size(), 0);
+  std::vector<int32_t> count(N, 0);
+  std::vector<int32_t> reg, hg;                    // current patch: node ids, hanging ids
+  std::vector<std::array<int32_t, 8>> ecorner;     // provisional: >= 0 regular slot, < 0 ~hslot
+  int32_t pid = 0;
+  int64_t e0 = 0;
+  P.eloc.resize(n);
+  auto close = [&](int64_t e_end) {
+    const int32_t nr = (int32_t)reg.size();
+    P.elem.push_back((int32_t)e0);
+    P.slot.push_back((int32_t)P.node.size());
+    P.nreg.push_back(nr);
+    for (int32_t id : reg) {
+      P.node.push_back(id);
+      P.par.push_back(make_ushort4(0xffff, 0xffff, 0xffff, 0xffff));
+      ++count[id & kIdxMask & ~kDirBit];
+    }
+    for (int32_t h : hg) {
+      const int4 q = hang[h];
+      const int32_t ps[4] = {q.x, q.y, q.z, q.w};
+      unsigned short loc[4] = {0xffff, 0xffff, 0xffff, 0xffff};
+      for (int k = 0; k < 4; ++k)
+        if (ps[k] >= 0) loc[k] = (unsigned short)slot_n[ps[k] & kIdxMask];
+      P.node.push_back(-1);
+      P.par.push_back(make_ushort4(loc[0], loc[1], loc[2], loc[3]));
+    }
+    for (int64_t e = e0; e < e_end; ++e) {
+      unsigned short l[8];
+      for (int c = 0; c < 8; ++c) {
+        int32_t v = ecorner[e - e0][c];
+        l[c] = (unsigned short)(v >= 0 ? v : nr + ~v);
+      }
+      P.eloc[e] = make_uint4(l[0] | (l[1] << 16), l[2] | (l[3] << 16), l[4] | (l[5] << 16),
+                             l[6] | (l[7] << 16));
+    }
+    reg.clear();
+    hg.clear();
+    ecorner.clear();
+    ++pid;
+    e0 = e_end;
+  };
+  for (int64_t e = 0; e < n; ++e) {
+    // distinct new references of this element
+    int32_t newn[40], newh[8];
+    int nn = 0, nh = 0;
+    auto add_node = [&](int32_t id) {
+      const int32_t j = id & kIdxMask;
+      if (stamp_n[j] == pid) return;
+      for (int k = 0; k < nn; ++k)
+        if ((newn[k] & kIdxMask) == j) return;
+      newn[nn++] = id;
+    };
+    for (int c = 0; c < 8; ++c) {
+      const int32_t v = enode[8 * e + c];
+      const int32_t j = v & kIdxMask;
+      if (j < N) {
+        add_node(v);
+      } else {
+        const int32_t h = j - (int32_t)N;
+        bool seen = stamp_h[h] == pid;
+        for (int k = 0; k < nh && !seen; ++k) seen = newh[k] == h;
+        if (!seen) newh[nh++] = h;
+        const int4 q = hang[h];
+        add_node(q.x);
+        add_node(q.y);
+        if (q.z >= 0) {
+          add_node(q.z);
+          add_node(q.w);
+        }
+      }
+    }
+    const int64_t slots = (int64_t)reg.size() + hg.size() + nn + nh;
+    if (e > e0 && (e - e0 >= kPatchElems || slots > kPatchSlots)) {
+      close(e);
+      --e;  // re-examine this element in the new patch
+      continue;
+    }
+    for (int k = 0; k < nn; ++k) {
+      const int32_t j = newn[k] & kIdxMask;
+      stamp_n[j] = pid;
+      slot_n[j] = (int32_t)reg.size();
+      reg.push_back(newn[k]);
+    }
+    for (int k = 0; k < nh; ++k) {
+      stamp_h[newh[k]] = pid;
+      slot_h[newh[k]] = (int32_t)hg.size();
+      hg.push_back(newh[k]);
+    }
+    std::array<int32_t, 8> ec;
+    for (int c = 0; c < 8; ++c) {
+      const int32_t j = enode[8 * e + c] & kIdxMask;
+      ec[c] = j < N ? slot_n[j] : ~slot_h[j - (int32_t)N];
+    }
+    ecorner.push_back(ec);
+  }
+  close(n);
+  P.elem.push_back((int32_t)n);
+  P.slot.push_back((int32_t)P.node.size());
+  for (auto& id : P.node)
+    if (id >= 0 && count[id & kIdxMask & ~kDirBit] == 1) id |= kOwnBit;
 }
 
 static chns_status build(const uint32_t* anchors, const uint8_t* levels, int64_t n,
@@ -321,6 +441,10 @@ static chns_status build(const uint32_t* anchors, const uint8_t* levels, int64_t
       }
   });
 
+  // ---- patches (CTA-level gather / scatter)
+  PatchTables P;
+  build_patches(n, N, enode, hang, P);
+
   // ---- upload
   m->d.n_elem = n;
   m->d.n_nodes = N;
@@ -350,6 +474,29 @@ static chns_status build(const uint32_t* anchors, const uint8_t* levels, int64_t
       CHNS_CUDA(cudaMemcpyAsync(m->d_bnd, bl.data(), bl.size() * sizeof(int32_t),
                                 cudaMemcpyHostToDevice, stream));
     CHNS_CUDA(cudaStreamSynchronize(stream));
+  }
+  {
+    const int64_t np = (int64_t)P.nreg.size();
+    m->d.n_patch = np;
+    m->n_slots = (int64_t)P.node.size();
+    CHNS_CUDA(cudaMalloc(&m->d_patch_elem, (np + 1) * sizeof(int32_t)));
+    CHNS_CUDA(cudaMalloc(&m->d_patch_slot, (np + 1) * sizeof(int32_t)));
+    CHNS_CUDA(cudaMalloc(&m->d_patch_nreg, np * sizeof(int32_t)));
+    CHNS_CUDA(cudaMalloc(&m->d_slot_node, P.node.size() * sizeof(int32_t)));
+    CHNS_CUDA(cudaMalloc(&m->d_slot_par, P.par.size() * sizeof(ushort4)));
+    CHNS_CUDA(cudaMalloc(&m->d_eloc, (size_t)n * sizeof(uint4)));
+    CHNS_CUDA(cudaMemcpy(m->d_patch_elem, P.elem.data(), (np + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CHNS_CUDA(cudaMemcpy(m->d_patch_slot, P.slot.data(), (np + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CHNS_CUDA(cudaMemcpy(m->d_patch_nreg, P.nreg.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CHNS_CUDA(cudaMemcpy(m->d_slot_node, P.node.data(), P.node.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CHNS_CUDA(cudaMemcpy(m->d_slot_par, P.par.data(), P.par.size() * sizeof(ushort4), cudaMemcpyHostToDevice));
+    CHNS_CUDA(cudaMemcpy(m->d_eloc, P.eloc.data(), (size_t)n * sizeof(uint4), cudaMemcpyHostToDevice));
+    m->d.patch_elem = m->d_patch_elem;
+    m->d.patch_slot = m->d_patch_slot;
+    m->d.patch_nreg = m->d_patch_nreg;
+    m->d.slot_node = m->d_slot_node;
+    m->d.slot_par = m->d_slot_par;
+    m->d.eloc = m->d_eloc;
   }
   m->d.enode = m->d_enode;
   m->d.level = m->d_level;

@@ -65,12 +65,16 @@ struct PoissonK {
   static constexpr int NC = 1;
   static constexpr bool DIR = false;
   static constexpr bool DIAG_PER_COMP = false;
+  static constexpr int NF = 1;  // coefficient fields: phi~
   T c[8];
+  __device__ __forceinline__ void setup(const T f[NF][8], const Geo<T>& g, const DevParams& p) {
+    poisson_coef(f[0], g, p, c);
+  }
   __device__ __forceinline__ void load(const MeshDev& m, const DevParams& p, const CoefArgs<C>& cf,
                                        const int idx[8], const Geo<T>& g) {
-    T pe[8];
-    gather_phi(m, idx, cf, pe);
-    poisson_coef(pe, g, p, c);
+    T f[NF][8];
+    gather_phi(m, idx, cf, f[0]);
+    setup(f, g, p);
   }
   __device__ __forceinline__ void apply(const Geo<T>& g, const DevParams&, const T x[NC][8],
                                         T r[NC][8]) const {
@@ -85,14 +89,19 @@ struct MassK {
   static constexpr int NC = 3;
   static constexpr bool DIR = true;
   static constexpr bool DIAG_PER_COMP = false;
+  static constexpr int NF = 1;  // phi~
   T c[8];
-  __device__ __forceinline__ void load(const MeshDev& m, const DevParams& p, const CoefArgs<C>& cf,
-                                       const int idx[8], const Geo<T>& g) {
-    T pe[8], pq[8];
-    gather_phi(m, idx, cf, pe);
-    interp3(pe, pq);
+  __device__ __forceinline__ void setup(const T f[NF][8], const Geo<T>& g, const DevParams& p) {
+    T pq[8];
+    interp3(f[0], pq);
 #pragma unroll
     for (int q = 0; q < 8; ++q) c[q] = g.detJ * (T(p.alpha) * clamp1(pq[q]) + T(p.beta));
+  }
+  __device__ __forceinline__ void load(const MeshDev& m, const DevParams& p, const CoefArgs<C>& cf,
+                                       const int idx[8], const Geo<T>& g) {
+    T f[NF][8];
+    gather_phi(m, idx, cf, f[0]);
+    setup(f, g, p);
   }
   __device__ __forceinline__ void apply(const Geo<T>&, const DevParams&, const T x[NC][8],
                                         T r[NC][8]) const {
@@ -117,8 +126,18 @@ struct ChK {
   static constexpr int NC = 2;
   static constexpr bool DIR = false;
   static constexpr bool DIAG_PER_COMP = true;
+  static constexpr int NF = 4;  // phi~, u~ (3)
   T pe[8];
   T ue[3][8];
+  __device__ __forceinline__ void setup(const T f[NF][8], const Geo<T>&, const DevParams&) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      pe[a] = f[0][a];
+      ue[0][a] = f[1][a];
+      ue[1][a] = f[2][a];
+      ue[2][a] = f[3][a];
+    }
+  }
   __device__ __forceinline__ void load(const MeshDev& m, const DevParams&, const CoefArgs<C>& cf,
                                        const int idx[8], const Geo<T>&) {
     gather_phi(m, idx, cf, pe);
@@ -216,9 +235,20 @@ struct MomK {
   static constexpr int NC = 3;
   static constexpr bool DIR = true;
   static constexpr bool DIAG_PER_COMP = false;
+  static constexpr int NF = 5;  // phi~, u_hat (3), mu~
   T pe[8];
   T ue[3][8];
   T me[8];
+  __device__ __forceinline__ void setup(const T f[NF][8], const Geo<T>&, const DevParams&) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      pe[a] = f[0][a];
+      ue[0][a] = f[1][a];
+      ue[1][a] = f[2][a];
+      ue[2][a] = f[3][a];
+      me[a] = f[4][a];
+    }
+  }
   __device__ __forceinline__ void load(const MeshDev& m, const DevParams&, const CoefArgs<C>& cf,
                                        const int idx[8], const Geo<T>&) {
     gather_phi(m, idx, cf, pe);
