@@ -286,9 +286,14 @@ def chns_krylov_solve(mesh, op, prm, coef, b, x, solver, stream=None, check=True
 
 
 def chns_step(mesh, state: chns_state, prm, step_params, stream=None) -> chns_step_stats:
+    """On failure the raised ChnsError carries the partial statistics as .stats."""
     st = chns_step_stats()
-    _check(LIB.chns_step(mesh, C.byref(state), C.byref(prm), C.byref(step_params), C.byref(st),
-                         _stream(stream)), "chns_step")
+    rc = LIB.chns_step(mesh, C.byref(state), C.byref(prm), C.byref(step_params), C.byref(st),
+                       _stream(stream))
+    if rc != OK:
+        err = ChnsError(rc, "chns_step", LIB.chns_last_error().decode())
+        err.stats = st
+        raise err
     return st
 
 

@@ -845,13 +845,18 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
         int its = 0;
         double irn = 0.0;
         const double itol = std::max(sp->inner_rtol, 0.5 * tol / rn);
+        // Each cycle gets a bounded number of iterations: an FP32 iteration that stagnates above
+        // its tolerance then falls through to the FP64 residual check (and escalation) instead
+        // of spending the whole budget.
+        const int cap = sp->ksp == CHNS_KSP_GMRES ? 4 * sp->restart : std::max(1000, sp->max_it / 4);
+        const int budget = std::min(sp->max_it - total, cap);
         chns_status ist;
         if (sp->ksp == CHNS_KSP_CG)
-          ist = pcg<float>(c, r32, d32, dinv32, itol, sp->max_it - total, sp->check_every,
-                           ws.v32[3], ws.v32[4], ws.v32[5], ws.v32[6], &its, &irn);
+          ist = pcg<float>(c, r32, d32, dinv32, itol, budget, sp->check_every, ws.v32[3],
+                           ws.v32[4], ws.v32[5], ws.v32[6], &its, &irn);
         else
-          ist = gmres<float>(c, r32, d32, dinv32, block2, itol, sp->max_it - total, sp->restart,
-                             ws.gm_V32, ws.v32[7], &its, &irn);
+          ist = gmres<float>(c, r32, d32, dinv32, block2, itol, budget, sp->restart, ws.gm_V32,
+                             ws.v32[7], &its, &irn);
         if (ist != CHNS_OK && ist != CHNS_ENOTCONV) return ist;
         total += its;
         ++refine;

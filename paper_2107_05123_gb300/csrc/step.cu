@@ -20,6 +20,11 @@ static chns_status phase_fail(const char* phase, chns_status rc) {
   set_error(std::string("chns_step: ") + phase + ": " + chns_last_error());
   return rc;
 }
+#define STEP_FAIL(phase, rc)              \
+  do {                                    \
+    if (stats) *stats = S;                \
+    return phase_fail(phase, rc);         \
+  } while (0)
 
 struct Timer {
   cudaEvent_t a, b;
@@ -113,7 +118,8 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
         chns_coef cc{phit, {util[0], util[1], util[2]}, nullptr};
         CHNS_CUDA(cudaMemsetAsync(dx, 0, 2 * N * sizeof(double), s));
         rc = krylov_solve(m, CHNS_OP_CH, prm, &cc, f, dx, &chp, &ks, s);
-        if (rc != CHNS_OK) return phase_fail("Cahn-Hilliard Newton step", rc);
+        S.ch[l] = ks;
+        if (rc != CHNS_OK) STEP_FAIL("Cahn-Hilliard Newton step", rc);
         lin(1.0, xch, -1.0, dx, xch, 2 * N, s);
         rc = residual_ch(m, prm, xch, xch + N, phik, muk, ut, f, s);
         if (rc != CHNS_OK) return rc;
@@ -145,7 +151,7 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
       for (int d = 0; d < 3; ++d)
         CHNS_CUDA(cudaMemcpyAsync(v + d * N, uk[d], N * sizeof(double), cudaMemcpyDeviceToDevice, s));
       rc = krylov_solve(m, CHNS_OP_MOMENTUM, prm, &cv, bv, v, &sp->vp, &S.vp[l], s);
-      if (rc != CHNS_OK) return phase_fail("velocity prediction", rc);
+      if (rc != CHNS_OK) STEP_FAIL("velocity prediction", rc);
       S.ms_vp += t.stop();
     }
     // ---- pressure Poisson (warm start from p^k)
@@ -155,7 +161,7 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
       if (rc != CHNS_OK) return rc;
       CHNS_CUDA(cudaMemcpyAsync(pnew, st->p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
       rc = krylov_solve(m, CHNS_OP_POISSON, prm, &cv, bv, pnew, &sp->pp, &S.pp[l], s);
-      if (rc != CHNS_OK) return phase_fail("pressure Poisson", rc);
+      if (rc != CHNS_OK) STEP_FAIL("pressure Poisson", rc);
       S.ms_pp += t.stop();
     }
     // ---- velocity update
@@ -165,7 +171,7 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
       if (rc != CHNS_OK) return rc;
       CHNS_CUDA(cudaMemcpyAsync(un, v, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
       rc = krylov_solve(m, CHNS_OP_MASS, prm, &cv, bv, un, &sp->vu, &S.vu[l], s);
-      if (rc != CHNS_OK) return phase_fail("velocity update", rc);
+      if (rc != CHNS_OK) STEP_FAIL("velocity update", rc);
       S.ms_vu += t.stop();
     }
     for (int d = 0; d < 3; ++d) ublk[d] = un + d * N;
