@@ -3,10 +3,13 @@
 Inputs only: these functions describe initial phase fields, chemical potentials and velocities
 of the synthetic workloads. They hold none of the discretisation.
 
-The interface profile is the paper's printed form tanh(sqrt(2) d / Cn) (Sec. 6.4), with the
-signed distance d > 0 in the phase phi = +1 (the continuous, heavier fluid) and d < 0 inside
-drops (phi = -1). The initial chemical potential is the pointwise closed form of the
-continuous definition mu = psi'(phi) - Cn^2 lap(phi) (Sec. 3), evaluated analytically.
+The interface profile is tanh(d / (sqrt(2) Cn)), the planar equilibrium of the chemical
+potential mu = psi'(phi) - Cn^2 lap(phi) of Sec. 3 (psi' = phi^3 - phi), with the signed distance
+d > 0 in the phase phi = +1 (the continuous, heavier fluid) and d < 0 inside drops (phi = -1).
+(The 3D Rayleigh-Taylor setup of Sec. 6.4 prints tanh(sqrt(2) d / Cn), twice as steep; started
+from it, a drop at density ratio 1000 releases the non-equilibrium capillary force in its first
+steps.) The initial chemical potential is the pointwise closed form of mu, evaluated
+analytically; for the equilibrium profile only the curvature part remains.
 """
 from __future__ import annotations
 
@@ -14,8 +17,8 @@ import numpy as np
 
 
 def _tanh_profile(d, grad_d_sq, lap_d, Cn):
-    """phi = tanh(k d) with k = sqrt(2)/Cn; returns phi and its Laplacian."""
-    k = np.sqrt(2.0) / Cn
+    """phi = tanh(k d) with k = 1/(sqrt(2) Cn); returns phi and its Laplacian."""
+    k = 1.0 / (np.sqrt(2.0) * Cn)
     t = np.tanh(k * d)
     s2 = 1.0 - t * t
     lap = k * s2 * lap_d - 2.0 * k * k * t * s2 * grad_d_sq
@@ -61,7 +64,7 @@ def fourier_curl_velocity(x, seed: int, kmax: int = 2):
 
 # ---------------------------------------------------------------- drops and interfaces
 def drops_phi(x, centres, radii, Cn):
-    """phi = min_i tanh(sqrt(2)(|x-c_i| - R_i)/Cn) (phi = -1 inside drops) and its Laplacian
+    """phi = min_i tanh((|x-c_i| - R_i)/(sqrt(2) Cn)) (phi = -1 inside drops) and its Laplacian
     taken from the drop that attains the minimum."""
     best_phi = None
     best_lap = None
