@@ -160,6 +160,22 @@ chns_status chns_rhs_velocity_update(const chns_mesh* mesh, const chns_params* p
 /* Integral of phi (1^T M phi) by the same quadrature, FP64 (Prop. mass_conservation). */
 chns_status chns_phi_mass(const chns_mesh* mesh, const double* phi, double* out_host, void* stream);
 
+/* The same phi integral for callers that cannot allocate memory while they run: code inside a
+ * CUDA stream capture (where allocation calls are not allowed), or an application whose memory
+ * is all reserved up front by its own pool so that a library may not take any more. The paper
+ * has no counterpart; this is a property of the library only.
+ * Nothing is allocated during the call: the block partial sums and the finishing ticket live in
+ * a fixed scratch array inside the library (65,536 partial sums, ~0.5 MB, which every GPU that
+ * loads the library keeps until the process exits), and the result is written to `out`, a
+ * device double owned by the caller. The call is asynchronous on `stream`.
+ * Limits and rules: meshes of more than 8,388,608 elements are rejected with CHNS_EINVAL. The
+ * first call on a device looks up the scratch array's device address on the current device;
+ * make that first call before any stream capture. Every call shares the one scratch array, so
+ * calls that overlap on the GPU (other streams, other threads) race and give wrong results:
+ * serialise them. */
+chns_status chns_phi_mass_noalloc(const chns_mesh* mesh, const double* phi, double* out,
+                                  void* stream);
+
 /* ---------------------------------------------------------------- Krylov solves
  * Solve A x = b for an operator, b and x FP64 device arrays of the operator's component count;
  * x holds the initial guess on entry. Stops at ||b - A x||_2 <= rtol ||b||_2 (FP64 residual).

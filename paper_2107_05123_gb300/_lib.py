@@ -104,6 +104,7 @@ _SIGS = {
     "chns_rhs_poisson": ([_P, C.POINTER(chns_params), C.POINTER(chns_coef), _PP3, _PP3, _P, _P, _P], C.c_int),
     "chns_rhs_velocity_update": ([_P, C.POINTER(chns_params), C.POINTER(chns_coef), _PP3, _PP3, _P, _P, _P, _P], C.c_int),
     "chns_phi_mass": ([_P, _P, C.POINTER(C.c_double), _P], C.c_int),
+    "chns_phi_mass_noalloc": ([_P, _P, _P, _P], C.c_int),
     "chns_krylov_solve": ([_P, C.c_int, C.POINTER(chns_params), C.POINTER(chns_coef), _P, _P,
                            C.POINTER(chns_solver_params), C.POINTER(chns_solve_stats), _P], C.c_int),
     "chns_step": ([_P, C.POINTER(chns_state), C.POINTER(chns_params), C.POINTER(chns_step_params),
@@ -274,6 +275,12 @@ def chns_phi_mass(mesh, phi, stream=None) -> float:
     out = C.c_double()
     _check(LIB.chns_phi_mass(mesh, _ptr(phi), C.byref(out), _stream(stream)), "chns_phi_mass")
     return out.value
+
+
+def chns_phi_mass_noalloc(mesh, phi, out, stream=None):
+    """Writes the integral to the device double `out`; allocates nothing (see include/chns.h)."""
+    _check(LIB.chns_phi_mass_noalloc(mesh, _ptr(phi), _ptr(out), _stream(stream)),
+           "chns_phi_mass_noalloc")
 
 
 def chns_krylov_solve(mesh, op, prm, coef, b, x, solver, stream=None, check=True):
