@@ -341,6 +341,37 @@ def run_reference(args):
     }))
 
 
+def run_apply_only(args):
+    """Profiling aid: the roofline kernel alone (Poisson apply, BF16 coefficients, FP32 vectors)
+    on the bench mesh, a few launches, with one timing line."""
+    import torch
+
+    from chns_workloads import configs
+    from paper_2107_05123_gb300 import capi
+    from paper_2107_05123_gb300.session import Mesh
+
+    w = configs.rising_drop(5, 8)
+    mesh = Mesh(w.anchors, w.levels, w.extent)
+    f0 = w.init(mesh.node_xyz)
+    prm = capi.make_params(w.params.as_dict())
+    coef = capi.make_coef((torch.as_tensor(f0["phi"], device="cuda") + 1.0).to(torch.bfloat16))
+    x = torch.randn(mesh.n_nodes, device="cuda")
+    y = torch.empty_like(x)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    ts = []
+    for i in range(args.steps + args.warmup):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        capi.chns_apply_poisson(mesh.handle, prm, coef, x, y, capi.FP32_BF16COEF)
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ts.append(e0.elapsed_time(e1))
+    print(json.dumps({"mode": "apply", "n_elem": mesh.n_elem, "n_nodes": mesh.n_nodes,
+                      "ms": statistics.mean(ts)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,8 +384,12 @@ def main():
                     help="time only one path and print a detail line (profiling runs)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the roofline kernel from an ncu capture")
+    ap.add_argument("--mode", choices=["bench", "apply"], default="bench",
+                    help="apply: time only the roofline kernel (profiling aid)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.mode == "apply":
+        run_apply_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

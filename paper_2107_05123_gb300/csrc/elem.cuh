@@ -16,26 +16,64 @@ namespace chns {
 constexpr double kW0 = 0.78867513459481288225;  // (1 + 1/sqrt(3)) / 2
 constexpr double kW1 = 0.21132486540518711775;  // (1 - 1/sqrt(3)) / 2
 
-// Physical parameters in device form (Sec. 3 maps rho(phi), eta(phi)).
-struct DevParams {
-  double alpha, beta, gamma, xi;
-  double dt, Re, We, Cn, Pe, Fr, C_I;
+// Physical parameters in device form (Sec. 3: rho(phi) = alpha phi + beta, eta = gamma phi + xi)
+// with every quotient the kernels need precomputed on the host, in the kernel's own precision:
+// the device code multiplies only (on GB300 an FP64 division inside an FP32 kernel costs more
+// than the whole FP32 element computation around it).
+template <class T>
+struct PrmT {
+  T alpha, beta, gamma, xi, C_I;
+  T dt, idt, four_idt2, k2dt, half_dt;  // dt, 1/dt, 4/dt^2, 2/dt, dt/2
+  T inv_re, h2re, inv_pe, h2pe;         // 1/Re, 1/(2Re), 1/Pe, 1/(2Pe)
+  T inv_pecn, kmu, kphi, cn2;           // 1/(Pe Cn), 1/(2 Pe Cn), Cn^2/2, Cn^2
+  T ka, cw, inv_fr;                     // -alpha/Cn, Cn/We, 1/Fr
 };
+
+struct DevParams {
+  PrmT<double> d;
+  PrmT<float> f;
+  template <class T>
+  __host__ __device__ __forceinline__ const PrmT<T>& get() const;
+};
+template <>
+__host__ __device__ __forceinline__ const PrmT<double>& DevParams::get<double>() const { return d; }
+template <>
+__host__ __device__ __forceinline__ const PrmT<float>& DevParams::get<float>() const { return f; }
+
+template <class T>
+inline PrmT<T> make_prm(const chns_params& p) {
+  const double rp = 1.0, rm = 1.0 / p.rho_ratio, ep = 1.0, em = 1.0 / p.eta_ratio;
+  const double alpha = (rp - rm) / (2 * rp), beta = (rp + rm) / (2 * rp);
+  const double gamma = (ep - em) / (2 * ep), xi = (ep + em) / (2 * ep);
+  PrmT<T> q;
+  q.alpha = (T)alpha;
+  q.beta = (T)beta;
+  q.gamma = (T)gamma;
+  q.xi = (T)xi;
+  q.C_I = (T)p.C_I;
+  q.dt = (T)p.dt;
+  q.idt = (T)(1.0 / p.dt);
+  q.four_idt2 = (T)(4.0 / (p.dt * p.dt));
+  q.k2dt = (T)(2.0 / p.dt);
+  q.half_dt = (T)(0.5 * p.dt);
+  q.inv_re = (T)(1.0 / p.Re);
+  q.h2re = (T)(0.5 / p.Re);
+  q.inv_pe = (T)(1.0 / p.Pe);
+  q.h2pe = (T)(0.5 / p.Pe);
+  q.inv_pecn = (T)(1.0 / (p.Pe * p.Cn));
+  q.kmu = (T)(0.5 / (p.Pe * p.Cn));
+  q.kphi = (T)(0.5 * p.Cn * p.Cn);
+  q.cn2 = (T)(p.Cn * p.Cn);
+  q.ka = (T)(-alpha / p.Cn);
+  q.cw = (T)(p.Cn / p.We);
+  q.inv_fr = (T)(1.0 / p.Fr);
+  return q;
+}
 
 inline DevParams make_dev_params(const chns_params& p) {
   DevParams d;
-  double rp = 1.0, rm = 1.0 / p.rho_ratio, ep = 1.0, em = 1.0 / p.eta_ratio;
-  d.alpha = (rp - rm) / (2 * rp);
-  d.beta = (rp + rm) / (2 * rp);
-  d.gamma = (ep - em) / (2 * ep);
-  d.xi = (ep + em) / (2 * ep);
-  d.dt = p.dt;
-  d.Re = p.Re;
-  d.We = p.We;
-  d.Cn = p.Cn;
-  d.Pe = p.Pe;
-  d.Fr = p.Fr;
-  d.C_I = p.C_I;
+  d.d = make_prm<double>(p);
+  d.f = make_prm<float>(p);
   return d;
 }
 
@@ -64,15 +102,23 @@ struct Geo {
 
 template <class T>
 __device__ __forceinline__ Geo<T> geometry(const MeshDev& m, int64_t e) {
+  const LevelGeo& L = m.geo[m.level[e]];
   Geo<T> g;
-  int l = m.level[e];
-  double s = ldexp(1.0, -l);
+  if constexpr (sizeof(T) == sizeof(double)) {
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    g.h[d] = (T)(m.ext[d] * s);
-    g.ih[d] = (T)(1.0 / (m.ext[d] * s));
+    for (int d = 0; d < 3; ++d) {
+      g.h[d] = L.h[d];
+      g.ih[d] = L.ih[d];
+    }
+    g.detJ = L.detJ;
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      g.h[d] = L.hf[d];
+      g.ih[d] = L.ihf[d];
+    }
+    g.detJ = L.detJf;
   }
-  g.detJ = (T)(m.ext[0] * m.ext[1] * m.ext[2] * s * s * s * 0.125);
   return g;
 }
 

@@ -23,6 +23,13 @@ constexpr int32_t kNodeMask = kOwnBit - 1;
 constexpr int kPatchElems = 256;
 constexpr int kPatchSlots = 1024;
 
+// Element geometry of one octant level on the box [0,L]^3 scaled per axis: h_d = L_d 2^-level,
+// 1/h_d and det J = h_x h_y h_z / 8, in FP64 and FP32 (looked up, never recomputed per element).
+struct LevelGeo {
+  double h[3], ih[3], detJ;
+  float hf[3], ihf[3], detJf;
+};
+
 // Device view of the mesh tables (passed by value to kernels).
 struct MeshDev {
   int64_t n_elem;
@@ -41,6 +48,7 @@ struct MeshDev {
   const int32_t* slot_node;   // [slots] regular slot: node id | kOwnBit | kDirBit
   const ushort4* slot_par;    // [slots] hanging slot: local parent slots (0xffff = none)
   const uint4* eloc;          // [n_elem] 8 local slot indices (uint16) per element
+  const LevelGeo* geo;        // [CHNS_MAXD] per-level geometry
 };
 
 struct Workspace {
@@ -78,6 +86,7 @@ struct chns_mesh {
   int32_t* d_slot_node = nullptr;
   ushort4* d_slot_par = nullptr;
   uint4* d_eloc = nullptr;
+  chns::LevelGeo* d_geo = nullptr;
   int64_t n_slots = 0;
   chns::Workspace ws;
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture CUDA graphs

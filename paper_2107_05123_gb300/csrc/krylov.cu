@@ -20,6 +20,7 @@ namespace chns {
 
 constexpr int kVecThreads = 256;
 constexpr int kMdBlocks = 256;  // blocks per multi-dot row (partials: rows x kMdBlocks)
+constexpr int kMd2Blocks = 256;  // blocks of the one-pass multi-dot (partials: rows x blocks)
 
 // device scalar slots (offsets from ws.red + kScalarBase)
 enum Slot { S_RZ0 = 0, S_RZ1 = 1, S_PQ = 2, S_RR = 3, S_TMP = 8, S_AUX = 16, S_MD = 64 };
@@ -41,8 +42,9 @@ template <class A, class B>
 __global__ void __launch_bounds__(kVecThreads)
 k_dot(const A* __restrict__ a, const B* __restrict__ b, int64_t n, double* part, unsigned* counter,
       double* out) {
-  double v[1] = {0.0};
-  GRID_LOOP(i, n) v[0] += (double)a[i] * (double)b[i];
+  A t = A(0);  // per-thread partial sum in the vector type, FP64 across threads
+  GRID_LOOP(i, n) t += a[i] * (A)b[i];
+  double v[1] = {(double)t};
   reduce_finalize<1>(v, part, counter, out);
 }
 
@@ -142,19 +144,25 @@ __global__ void __launch_bounds__(kVecThreads)
 k_cg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __restrict__ p,
             const T* __restrict__ q, const T* __restrict__ dinv, int64_t n, double* __restrict__ S,
             int parity, double* part, unsigned* counter) {
-  const double rz = S[S_RZ0 + parity], pq = S[S_PQ];
-  const double alpha = (pq > 0.0 && isfinite(pq)) ? rz / pq : 0.0;
-  const T a = (T)alpha;
-  double v[2] = {0.0, 0.0};
+  // one division per block (FP64 division is slow on this part), shared with the block
+  __shared__ T s_alpha;
+  if (threadIdx.x == 0) {
+    const double rz = S[S_RZ0 + parity], pq = S[S_PQ];
+    s_alpha = (T)((pq > 0.0 && isfinite(pq)) ? rz / pq : 0.0);
+  }
+  __syncthreads();
+  const T a = s_alpha;
+  T v0 = T(0), v1 = T(0);  // per-thread partial sums in T (a few terms), then FP64 across threads
   GRID_LOOP(i, n) {
     x[i] += a * p[i];
     const T ri = r[i] - a * q[i];
     r[i] = ri;
     const T zi = dinv ? dinv[i] * ri : ri;
     z[i] = zi;
-    v[0] += (double)ri * (double)zi;
-    v[1] += (double)ri * (double)ri;
+    v0 += ri * zi;
+    v1 += ri * ri;
   }
+  double v[2] = {(double)v0, (double)v1};
   reduce_finalize<2>(v, part, counter, S + S_TMP);
 }
 
@@ -163,15 +171,19 @@ k_cg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __
 template <class T>
 __global__ void k_cg_pupdate(T* __restrict__ p, const T* __restrict__ z, T* __restrict__ q,
                              int64_t n, double* __restrict__ S, int parity) {
-  const double rz_old = S[S_RZ0 + parity], rz_new = S[S_TMP];
-  const double beta = rz_old != 0.0 ? rz_new / rz_old : 0.0;
-  const T b = (T)beta;
+  __shared__ T s_beta;
+  if (threadIdx.x == 0) {
+    const double rz_old = S[S_RZ0 + parity], rz_new = S[S_TMP];
+    s_beta = (T)(rz_old != 0.0 ? rz_new / rz_old : 0.0);
+  }
+  __syncthreads();
+  const T b = s_beta;
   GRID_LOOP(i, n) {
     p[i] = z[i] + b * p[i];
     if (q) q[i] = T(0);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    S[S_RZ0 + (parity ^ 1)] = rz_new;
+    S[S_RZ0 + (parity ^ 1)] = S[S_TMP];
     S[S_RR] = S[S_TMP + 1];
   }
 }
@@ -233,6 +245,75 @@ __global__ void k_gmres_update_b2(const T* __restrict__ V, int64_t ld, int nk,
     const double z1 = (double)inv[2 * N + i] * a0 + (double)inv[3 * N + i] * a1;
     x[i] = (T)((double)x[i] + z0);
     x[N + i] = (T)((double)x[N + i] + z1);
+  }
+}
+
+// Multi-dot of rows V_0..V_{nk-1} with w, plus w.w as row nk. Each block stages a slice of w in
+// shared memory once and sweeps all rows over it (the rows are read once, w once); per-warp sums
+// accumulate in shared memory across the block's slices; partials land in part[k][blockIdx.x].
+constexpr int kMd2Threads = 256, kMd2Slice = 2048, kMd2MaxRows = CHNS_GMRES_MAX_RESTART + 2;
+template <class T>
+__global__ void __launch_bounds__(kMd2Threads)
+k_multidot2(const T* __restrict__ V, int64_t ld, int nk, const T* __restrict__ w, int64_t n,
+            double* __restrict__ part) {
+  __shared__ T wsl[kMd2Slice];
+  __shared__ double acc[kMd2MaxRows][kMd2Threads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = threadIdx.x; k < (nk + 1) * (kMd2Threads / 32); k += kMd2Threads)
+    acc[k / (kMd2Threads / 32)][k % (kMd2Threads / 32)] = 0.0;
+  const int64_t nsl = (n + kMd2Slice - 1) / kMd2Slice;
+  for (int64_t sl = blockIdx.x; sl < nsl; sl += gridDim.x) {
+    const int64_t i0 = sl * kMd2Slice;
+    __syncthreads();
+    for (int t = threadIdx.x; t < kMd2Slice; t += kMd2Threads)
+      wsl[t] = (i0 + t < n) ? w[i0 + t] : T(0);
+    __syncthreads();
+    for (int k = 0; k <= nk; ++k) {
+      T sum = T(0);
+      if (k < nk) {
+        const T* vk = V + (int64_t)k * ld + i0;
+        for (int t = threadIdx.x; t < kMd2Slice; t += kMd2Threads)
+          if (i0 + t < n) sum += vk[t] * wsl[t];
+      } else {
+        for (int t = threadIdx.x; t < kMd2Slice; t += kMd2Threads) sum += wsl[t] * wsl[t];
+      }
+      double d = (double)sum;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+      if (lane == 0) acc[k][warp] += d;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k <= nk; k += kMd2Threads) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kMd2Threads / 32; ++q) t += acc[k][q];
+    part[(int64_t)k * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// w = (w - sum_k h_k V_k) * scale, with scale = 1/sqrt(h[nk] - sum_k h_k^2) when NORMALISE
+// (h[nk] = w.w from the same multi-dot: Pythagoras for the classical Gram-Schmidt step).
+template <class T, bool NORMALISE>
+__global__ void k_orth_update_scale(const T* __restrict__ V, int64_t ld, int nk,
+                                    const double* __restrict__ h, T* __restrict__ w, int64_t n) {
+  __shared__ double s_scale;
+  if (threadIdx.x == 0) {
+    double sc = 1.0;
+    if (NORMALISE) {
+      double hh = 0.0;
+      for (int k = 0; k < nk; ++k) hh += h[k] * h[k];
+      const double r = h[nk] - hh;
+      sc = r > 0.0 ? rsqrt(r) : 1.0;
+    }
+    s_scale = sc;
+  }
+  __syncthreads();
+  const double sc = s_scale;
+  GRID_LOOP(i, n) {
+    double acc = (double)w[i];
+    for (int k = 0; k < nk; ++k) acc -= h[k] * (double)V[(int64_t)k * ld + i];
+    w[i] = (T)(acc * sc);
   }
 }
 
@@ -565,27 +646,44 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, do
         k_mul<T><<<vg, kVecThreads, 0, c.s>>>(dinv, vj, z, n);
       st = apply_T<T>(c, z, w);
       if (st != CHNS_OK) return st;
-      for (int i = 0; i <= j; ++i) Hij(i, j) = 0.0;
-      double ww = 0.0;
-      for (int pass = 0; pass < 2; ++pass) {
-        const int nk = pass == 0 ? j + 1 : j + 2;  // second pass also computes w.w
+      // classical Gram-Schmidt: h = V^T w and w.w in one pass; a second pass only when the
+      // new vector lost more than half its norm to the projection (cancellation)
+      const unsigned md2 = (unsigned)std::max<int64_t>(
+          1, std::min<int64_t>((n + kMd2Slice - 1) / kMd2Slice, kMd2Blocks));
+      int nk = j + 1;
+      note_launch();
+      k_multidot2<T><<<md2, kMd2Threads, 0, c.s>>>(V, ld, nk, w, n, c.m->ws.red);
+      note_launch();
+      k_multidot_final<<<nk + 1, kVecThreads, 0, c.s>>>(c.m->ws.red, (int)md2, hdev);
+      CHNS_CUDA(cudaGetLastError());
+      st = read_dev(c.m, hdev, h.data(), nk + 1, c.s);
+      if (st != CHNS_OK) return st;
+      double hh = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        Hij(i, j) = h[i];
+        hh += h[i] * h[i];
+      }
+      double ww = h[nk];
+      double hn2 = ww - hh;
+      if (!(hn2 > 0.5 * ww)) {
+        // re-orthogonalise: w -= V h, then a second multi-dot on the updated vector
         note_launch();
-        k_multidot<T><<<dim3(mdb, nk), kVecThreads, 0, c.s>>>(V, ld, w, n, c.m->ws.red);
+        k_orth_update_scale<T, false><<<vg, kVecThreads, 0, c.s>>>(V, ld, nk, hdev, w, n);
         note_launch();
-        k_multidot_final<<<nk, kVecThreads, 0, c.s>>>(c.m->ws.red, (int)mdb, hdev);
+        k_multidot2<T><<<md2, kMd2Threads, 0, c.s>>>(V, ld, nk, w, n, c.m->ws.red);
         note_launch();
-        k_orth_update<T><<<vg, kVecThreads, 0, c.s>>>(V, ld, j + 1, hdev, w, n);
+        k_multidot_final<<<nk + 1, kVecThreads, 0, c.s>>>(c.m->ws.red, (int)md2, hdev);
         CHNS_CUDA(cudaGetLastError());
-        st = read_dev(c.m, hdev, h.data(), nk, c.s);
+        st = read_dev(c.m, hdev, h.data(), nk + 1, c.s);
         if (st != CHNS_OK) return st;
-        double hh = 0.0;
+        double h2 = 0.0;
         for (int i = 0; i <= j; ++i) {
           Hij(i, j) += h[i];
-          hh += h[i] * h[i];
+          h2 += h[i] * h[i];
         }
-        if (pass == 1) ww = std::max(0.0, h[j + 1] - hh);
+        hn2 = h[nk] - h2;
       }
-      const double hn = std::sqrt(ww);
+      const double hn = std::sqrt(std::max(0.0, hn2));
       Hij(j + 1, j) = hn;
       if (!std::isfinite(hn)) {
         set_error("krylov: NaN/Inf in GMRES");
@@ -593,7 +691,10 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, do
         *rnorm = hn;
         return CHNS_ENAN;
       }
-      if (hn > 0.0) note_launch(), k_scale<T><<<vg, kVecThreads, 0, c.s>>>(w, 1.0 / hn, n);
+      if (hn > 0.0) {
+        note_launch();
+        k_orth_update_scale<T, true><<<vg, kVecThreads, 0, c.s>>>(V, ld, nk, hdev, w, n);
+      }
       // Givens rotations
       for (int i = 0; i < j; ++i) {
         double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <array>
 #include <atomic>
+#include <cmath>
 #include <cstring>
 #include <numeric>
 #include <thread>
@@ -149,6 +150,7 @@ static void free_mesh(chns_mesh* m) {
   dfree(m->d_slot_node);
   dfree(m->d_slot_par);
   dfree(m->d_eloc);
+  dfree(m->d_geo);
   Workspace& w = m->ws;
   for (auto p : w.v64) dfree(p);
   for (auto p : w.v32) dfree(p);
@@ -497,6 +499,24 @@ static chns_status build(const uint32_t* anchors, const uint8_t* levels, int64_t
     m->d.slot_node = m->d_slot_node;
     m->d.slot_par = m->d_slot_par;
     m->d.eloc = m->d_eloc;
+  }
+  {
+    std::vector<LevelGeo> geo(CHNS_MAXD);
+    for (int l = 0; l < CHNS_MAXD; ++l) {
+      const double sc = std::ldexp(1.0, -l);
+      LevelGeo& G = geo[l];
+      for (int d = 0; d < 3; ++d) {
+        G.h[d] = extent[d] * sc;
+        G.ih[d] = 1.0 / G.h[d];
+        G.hf[d] = (float)G.h[d];
+        G.ihf[d] = (float)G.ih[d];
+      }
+      G.detJ = G.h[0] * G.h[1] * G.h[2] * 0.125;
+      G.detJf = (float)G.detJ;
+    }
+    CHNS_CUDA(cudaMalloc(&m->d_geo, CHNS_MAXD * sizeof(LevelGeo)));
+    CHNS_CUDA(cudaMemcpy(m->d_geo, geo.data(), CHNS_MAXD * sizeof(LevelGeo), cudaMemcpyHostToDevice));
+    m->d.geo = m->d_geo;
   }
   m->d.enode = m->d_enode;
   m->d.level = m->d_level;

@@ -36,7 +36,9 @@ __device__ __forceinline__ void poisson_coef(const T pe[8], const Geo<T>& g, con
   T pq[8];
   interp3(pe, pq);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) c[q] = g.detJ / (T(p.alpha) * clamp1(pq[q]) + T(p.beta));
+  const PrmT<T>& k = p.get<T>();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) c[q] = g.detJ / (k.alpha * clamp1(pq[q]) + k.beta);
 }
 
 // Sum-factorised local stiffness apply with a per-quadrature-point coefficient c[q]:
@@ -95,7 +97,10 @@ struct MassK {
     T pq[8];
     interp3(f[0], pq);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) c[q] = g.detJ * (T(p.alpha) * clamp1(pq[q]) + T(p.beta));
+    for (int q = 0; q < 8; ++q) {
+      const PrmT<T>& k = p.get<T>();
+      c[q] = g.detJ * (k.alpha * clamp1(pq[q]) + k.beta);
+    }
   }
   __device__ __forceinline__ void load(const MeshDev& m, const DevParams& p, const CoefArgs<C>& cf,
                                        const int idx[8], const Geo<T>& g) {
@@ -148,7 +153,8 @@ struct ChK {
                                         T r[NC][8]) const {
 #pragma unroll
     for (int a = 0; a < 8; ++a) r[0][a] = r[1][a] = T(0);
-    const T idt = T(1.0 / p.dt), kmu = T(0.5 / (p.Pe * p.Cn)), kphi = T(0.5 * p.Cn * p.Cn);
+    const PrmT<T>& pk = p.get<T>();
+    const T idt = pk.idt, kmu = pk.kmu, kphi = pk.kphi;
     const T J = g.detJ;
     for_qp([&](auto QC) {
       constexpr int Q = decltype(QC)::value;
@@ -197,30 +203,30 @@ __device__ __forceinline__ VmsQ<T> vms_at(const T pe[8], const T ue[3][8], const
   (void)mv;
 #pragma unroll
   for (int d = 0; d < 3; ++d) o.uq[d] = val_at<Q>(ue[d]);
+  const PrmT<T>& k = p.get<T>();
   T pc = clamp1(pv);
-  o.rho = T(p.alpha) * pc + T(p.beta);
-  o.eta = T(p.gamma) * pc + T(p.xi);
+  o.rho = k.alpha * pc + k.beta;
+  o.eta = k.gamma * pc + k.xi;
   const bool inside = pv < T(1) && pv > T(-1);
-  const T ka = T(-p.alpha / p.Cn);
+  const T ka = k.ka;
   const T ir = T(1) / o.rho;
-  const T jpe = ir / T(p.Pe);
+  const T jpe = ir * k.inv_pe;
   T ugu = T(0), ugj = T(0), gg = T(0);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    o.ge[d] = inside ? T(p.gamma) * o.gphi[d] : T(0);
+    o.ge[d] = inside ? k.gamma * o.gphi[d] : T(0);
     o.J[d] = ka * mg[d];
     T Gd = T(4) * g.ih[d] * g.ih[d];
     ugu += o.uq[d] * Gd * o.uq[d];
     ugj += o.uq[d] * Gd * o.J[d];
     gg += Gd * Gd;
   }
-  const T er = o.eta * ir / T(p.Re);
-  const T idt = T(1.0 / p.dt);
+  const T er = o.eta * ir * k.inv_re;
   ugj *= jpe;
-  o.tau = rsqrt(T(4) * idt * idt + ugu + (ugj > -ugu ? ugj : -ugu) + T(p.C_I) * er * er * gg);
-  o.a0 = o.rho * idt;
-  o.e = o.eta * T(0.5 / p.Re);
-  const T h2pe = T(0.5 / p.Pe), h2re = T(0.5 / p.Re);
+  o.tau = rsqrt(k.four_idt2 + ugu + (ugj > -ugu ? ugj : -ugu) + k.C_I * er * er * gg);
+  o.a0 = o.rho * k.idt;
+  o.e = o.eta * k.h2re;
+  const T h2pe = k.h2pe, h2re = k.h2re;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     o.b[d] = T(0.5) * o.rho * o.uq[d] + h2pe * o.J[d];

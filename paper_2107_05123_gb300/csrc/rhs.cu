@@ -33,7 +33,7 @@ k_residual_ch(MeshDev m, DevParams p, const double* __restrict__ phi, const doub
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     pt[i] = 0.5 * (a[i] + b[i]);
-    dp[i] = (a[i] - b[i]) / p.dt;
+    dp[i] = (a[i] - b[i]) * p.d.idt;
   }
   gather<double, false>(m, idx, mu, a);
   gather<double, false>(m, idx, muk, b);
@@ -42,7 +42,7 @@ k_residual_ch(MeshDev m, DevParams p, const double* __restrict__ phi, const doub
 #pragma unroll
   for (int d = 0; d < 3; ++d) gather<double, false>(m, idx, u.c[d], ue[d]);
   double r0[8] = {0}, r1[8] = {0};
-  const double J = g.detJ, kmu = 1.0 / (p.Pe * p.Cn), c2 = p.Cn * p.Cn;
+  const double J = g.detJ, kmu = p.d.inv_pecn, c2 = p.d.cn2;
   for_qp([&](auto QC) {
     constexpr int Q = decltype(QC)::value;
     double pv, pg[3], mv, mg[3];
@@ -92,7 +92,7 @@ k_rhs_momentum(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 uk,
   for (int d = 0; d < 3; ++d) gather<double, false>(m, idx, cf.u[d], ue[d]);
   gather<double, false>(m, idx, cf.mu, me);
   gather<double, false>(m, idx, pk, pp);
-  const double J = g.detJ, cw = p.Cn / p.We;
+  const double J = g.detJ, cw = p.d.cw;
   for (int i = 0; i < 3; ++i) {
     double ui[8], r[8] = {0};
     gather<double, false>(m, idx, uk.c[i], ui);
@@ -104,7 +104,7 @@ k_rhs_momentum(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 uk,
       double pv, pg[3], v, vg[3];
       vg_at<Q>(pp, g, pv, pg);
       vg_at<Q>(ui, g, v, vg);
-      const double grav = c.rho * ghat(i) / p.Fr;
+      const double grav = c.rho * ghat(i) * p.d.inv_fr;
       double bdot = c.b[0] * vg[0] + c.b[1] * vg[1] + c.b[2] * vg[2];
       double bpdot = c.bp[0] * vg[0] + c.bp[1] * vg[1] + c.bp[2] * vg[2];
       double r0 = -c.a0 * v + bpdot + cw * F[i] + pg[i] - grav;
@@ -137,8 +137,8 @@ __device__ __forceinline__ void rm_at(const VmsQ<double>& c, const DevParams& p,
     double adv = c.uq[0] * tg[0] + c.uq[1] * tg[1] + c.uq[2] * tg[2];
     double jdv = c.J[0] * tg[0] + c.J[1] * tg[1] + c.J[2] * tg[2];
     double edv = c.ge[0] * tg[0] + c.ge[1] * tg[1] + c.ge[2] * tg[2];
-    R[i] = c.rho * (vv - uv) / p.dt + c.rho * adv + jdv / p.Pe + (p.Cn / p.We) * F[i] + pg[i] -
-           edv / p.Re - c.rho * ghat(i) / p.Fr;
+    R[i] = c.rho * (vv - uv) * p.d.idt + c.rho * adv + jdv * p.d.inv_pe + p.d.cw * F[i] + pg[i] -
+           edv * p.d.inv_re - c.rho * ghat(i) * p.d.inv_fr;
   }
 }
 
@@ -163,7 +163,7 @@ k_rhs_poisson(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 v, Ptr3 uk,
   gather<double, false>(m, idx, cf.mu, me);
   gather<double, false>(m, idx, pk, pp);
   double r[8] = {0};
-  const double J = g.detJ, k2 = 2.0 / p.dt;
+  const double J = g.detJ, k2 = p.d.k2dt;
   for_qp([&](auto QC) {
     constexpr int Q = decltype(QC)::value;
     VmsQ<double> c = vms_at<Q>(pe, ue, me, g, p);
@@ -214,7 +214,7 @@ k_rhs_vu(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 v, Ptr3 uk,
     vg_at<Q>(dpe, g, dv, dg);
     const double V0[3] = {0.0, 0.0, 0.0};
     for (int i = 0; i < 3; ++i)
-      add_test<Q>(r[i], J * (c.rho * vq[i] - c.tau * R[i] - 0.5 * p.dt * dg[i]), V0, g);
+      add_test<Q>(r[i], J * (c.rho * vq[i] - c.tau * R[i] - p.d.half_dt * dg[i]), V0, g);
   });
   for (int i = 0; i < 3; ++i) scatter<double, true>(m, idx, r[i], b + i * m.n_nodes);
 }
