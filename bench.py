@@ -7,8 +7,9 @@ dt 5e-4), seeded synthetic fields. One bench step = one chns_step (two blocks of
 velocity prediction, pressure Poisson, velocity update) to relative residual 1e-8.
 
 value       = n_nodes x (Poisson solves in the timed steps) / (their device time), for the headline
-              path: FP32 Krylov iterations with BF16 coefficient storage inside FP64 refinement;
+              path: FP32 Krylov iterations and applies inside FP64 refinement (FP64 dot products);
 plain_fp64  = the same numbers for the all-FP64 path on the same GPU;
+bf16_coefficients = the headline path with bfloat16 coefficient storage for Poisson / mass;
 e2e         = one Poisson solve through the C ABI from pinned host buffers (copies timed);
 roofline    = the dominant apply kernel timed alone from a cold L2 (algorithmic bytes / time);
 cpu_baseline= the FP64 CPU oracle (assembled matrix + Jacobi-PCG) on a bounded sample.
@@ -174,11 +175,13 @@ def run_ours(args):
                     pp_refinements=last.pp[1].refinements)
 
     with ClockSampler(local) as clk:
-        headline = plain = None
+        headline = plain = bf16 = None
         if args.paths in ("both", "headline"):
-            headline = run_path(capi.FP32_BF16COEF, "fp32_bf16coef_fp64refine")
+            headline = run_path(capi.FP32, "fp32_fp64refine")
         if args.paths in ("both", "plain"):
             plain = run_path(capi.FP64, "fp64")
+        if args.paths == "both":
+            bf16 = run_path(capi.FP32_BF16COEF, "fp32_bf16coef_fp64refine")
     clocks = clk.summary()
     if args.paths != "both":
         if rank == 0:
@@ -189,25 +192,24 @@ def run_ours(args):
     # timed alone from a cold L2 on the launching stream.
     stream = torch.cuda.current_stream()
     phit = torch.as_tensor(f0["phi"], device="cuda")
-    coef16 = (phit + 1.0).to(torch.bfloat16)  # BF16 storage holds 1 + phi~
     x32 = torch.randn(N, device="cuda", dtype=torch.float32)
     y32 = torch.empty_like(x32)
-    c16 = capi.make_coef(coef16)
+    c32 = capi.make_coef(phit.float())
     times = []
     for i in range(13):
         flush_l2()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        capi.chns_apply_poisson(mesh.handle, prm, c16, x32, y32, capi.FP32_BF16COEF, stream)
+        capi.chns_apply_poisson(mesh.handle, prm, c32, x32, y32, capi.FP32, stream)
         e1.record(stream)
         torch.cuda.synchronize()
         if i >= 3:
             times.append(e0.elapsed_time(e1))
     t_apply = statistics.mean(times) * 1e-3
     E, H = mesh.n_elem, mesh.n_hanging
-    # algorithmic bytes: x read + y written (4 B each per node), phi~ (2 B per node), the
-    # element table (8 x int32 + level byte per element), the hanging table (16 B per entry)
-    alg_bytes = N * (4 + 4 + 2) + E * 33 + H * 16
+    # algorithmic bytes: x read + y written + phi~ read (4 B each per node), the element table
+    # (8 x int32 + level byte per element), the hanging table (16 B per entry)
+    alg_bytes = N * (4 + 4 + 4) + E * 33 + H * 16
     peak, peak_kind = _peaks()
     achieved = alg_bytes / t_apply / 1e9
     traffic = args.traffic  # dram bytes per launch from an ncu capture, when supplied
@@ -222,8 +224,8 @@ def run_ours(args):
     phi_h = phit.cpu().pin_memory()
     x_h = torch.zeros(N, dtype=torch.float64).pin_memory()
     bd, xd, pd = torch.empty_like(b_dev), torch.empty_like(b_dev), torch.empty_like(b_dev)
-    solver = capi.make_solver(capi.KSP_CG, capi.PC_JACOBI, 1e-8, 20000, 30, capi.FP32_BF16COEF,
-                              1e-3, 30, check_every=8)
+    solver = capi.make_solver(capi.KSP_CG, capi.PC_JACOBI, 1e-8, 20000, 30, capi.FP32,
+                              1e-6, 30, check_every=8)
     e2e_ms = []
     for i in range(args.warmup + args.steps):
         barrier()
@@ -245,7 +247,7 @@ def run_ours(args):
             "metric": METRIC, "value": headline["value"], "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": headline["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16coef/f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_elem": int(E), "n_nodes": int(N),
                        "n_hanging": int(H), "rtol": 1e-8, "l2": "flushed before every step",
@@ -255,11 +257,14 @@ def run_ours(args):
                            "pp_iters_per_solve": plain["pp_iters_per_solve"],
                            "phases_ms": plain["phases_ms"]},
             "headline_detail": headline,
+            "bf16_coefficients": {"value": bf16["value"], "ms_per_step": bf16["ms_per_step"],
+                                  "pp_ms_per_solve": bf16["pp_ms_per_solve"],
+                                  "pp_iters_per_solve": bf16["pp_iters_per_solve"]},
             "speedup_vs_plain_fp64": {"pp": headline["value"] / plain["value"],
                                       "step": plain["ms_per_step"] / headline["ms_per_step"]},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(2 * N * 8),
                     "d2h_bytes_per_step": int(N * 8)},
-            "roofline": {"kernel": "k_apply<PoissonK<float,bf16>>", "bound": "hbm",
+            "roofline": {"kernel": "k_apply_patch<PoissonK<float,float>>", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "alg_bytes": int(alg_bytes), "ms": t_apply * 1e3},
@@ -372,6 +377,43 @@ def run_apply_only(args):
                       "ms": statistics.mean(ts)}))
 
 
+def run_pp_only(args):
+    """Profiling aid: pressure-Poisson solves alone (headline precision) on the bench mesh, with
+    the right-hand side of the initial state, inside an NVTX range "pp_solve"."""
+    import torch
+
+    from chns_workloads import configs
+    from paper_2107_05123_gb300 import capi
+    from paper_2107_05123_gb300.session import Mesh
+
+    w = configs.rising_drop(5, 8)
+    mesh = Mesh(w.anchors, w.levels, w.extent)
+    N = mesh.n_nodes
+    f0 = w.init(mesh.node_xyz)
+    prm = capi.make_params(w.params.as_dict())
+    phit = torch.as_tensor(f0["phi"], device="cuda")
+    zero3 = [torch.zeros(N, dtype=torch.float64, device="cuda") for _ in range(3)]
+    b = torch.zeros(N, dtype=torch.float64, device="cuda")
+    capi.chns_rhs_poisson(mesh.handle, prm,
+                          capi.make_coef(phit, zero3, torch.as_tensor(f0["mu"], device="cuda")),
+                          zero3, zero3, torch.zeros_like(b), b)
+    solver = capi.make_solver(capi.KSP_CG, capi.PC_JACOBI, 1e-8, 20000, 30, capi.FP32, 1e-6, 30,
+                              check_every=8)
+    x = torch.zeros_like(b)
+    res = []
+    for i in range(args.steps + args.warmup):
+        x.zero_()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            torch.cuda.nvtx.range_push("pp_solve")
+        st = capi.chns_krylov_solve(mesh.handle, capi.OP_POISSON, prm, capi.make_coef(phit), b, x,
+                                    solver)
+        if i >= args.warmup:
+            torch.cuda.nvtx.range_pop()
+            res.append((st.ms, st.iterations, st.refinements, st.rel_residual))
+    print(json.dumps({"mode": "pp", "n_nodes": N, "solves": res}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,11 +426,13 @@ def main():
                     help="time only one path and print a detail line (profiling runs)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the roofline kernel from an ncu capture")
-    ap.add_argument("--mode", choices=["bench", "apply"], default="bench",
-                    help="apply: time only the roofline kernel (profiling aid)")
+    ap.add_argument("--mode", choices=["bench", "apply", "pp"], default="bench",
+                    help="apply / pp: time only the roofline kernel / the Poisson solve (profiling)")
     args = ap.parse_args()
     if args.mode == "apply":
         run_apply_only(args)
+    elif args.mode == "pp":
+        run_pp_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -83,6 +83,16 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
   const int s0 = m.patch_slot[pidx], ns = m.patch_slot[pidx + 1] - s0, nreg = m.patch_nreg[pidx];
   const int64_t N = m.n_nodes;
   const C* fptr[5] = {cf.phi, cf.u[0], cf.u[1], cf.u[2], cf.mu};
+  // the element's local corner slots and level are loaded first, so that their latency overlaps
+  // the gather of the patch's nodes
+  const int64_t e = (int64_t)m.patch_elem[pidx] + threadIdx.x;
+  const bool has_elem = e < m.patch_elem[pidx + 1];
+  uint4 lp = make_uint4(0, 0, 0, 0);
+  int lev = 0;
+  if (has_elem) {
+    lp = __ldg(m.eloc + e);
+    lev = __ldg(m.level + e);
+  }
   // 1. regular slots
   for (int i = threadIdx.x; i < nreg; i += blockDim.x) {
     const int32_t v = m.slot_node[s0 + i];
@@ -125,13 +135,11 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
   __syncthreads();
   // 3. elements
   double en[1] = {0.0};
-  const int64_t e = (int64_t)m.patch_elem[pidx] + threadIdx.x;
-  if (e < m.patch_elem[pidx + 1]) {
-    const uint4 lp = __ldg(m.eloc + e);
+  if (has_elem) {
     const int sl[8] = {(int)(lp.x & 0xffff), (int)(lp.x >> 16), (int)(lp.y & 0xffff),
                        (int)(lp.y >> 16),    (int)(lp.z & 0xffff), (int)(lp.z >> 16),
                        (int)(lp.w & 0xffff), (int)(lp.w >> 16)};
-    const Geo<T> g = geometry<T>(m, e);
+    const Geo<T> g = level_geometry<T>(m, lev);
     T fe[NF][8];
 #pragma unroll
     for (int f = 0; f < NF; ++f)

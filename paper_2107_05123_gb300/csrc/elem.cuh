@@ -101,8 +101,8 @@ struct Geo {
 };
 
 template <class T>
-__device__ __forceinline__ Geo<T> geometry(const MeshDev& m, int64_t e) {
-  const LevelGeo& L = m.geo[m.level[e]];
+__device__ __forceinline__ Geo<T> level_geometry(const MeshDev& m, int level) {
+  const LevelGeo& L = m.geo[level];
   Geo<T> g;
   if constexpr (sizeof(T) == sizeof(double)) {
 #pragma unroll
@@ -120,6 +120,11 @@ __device__ __forceinline__ Geo<T> geometry(const MeshDev& m, int64_t e) {
     g.detJ = L.detJf;
   }
   return g;
+}
+
+template <class T>
+__device__ __forceinline__ Geo<T> geometry(const MeshDev& m, int64_t e) {
+  return level_geometry<T>(m, m.level[e]);
 }
 
 __device__ __forceinline__ void load_corners(const MeshDev& m, int64_t e, int idx[8]) {

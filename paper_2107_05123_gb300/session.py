@@ -35,13 +35,13 @@ class Mesh:
             pass
 
 
-def default_step_params(rtol=1e-8, inner=capi.FP64, pp_check_every=8, inner_rtol=1e-5,
+def default_step_params(rtol=1e-8, inner=capi.FP64, pp_check_every=8, inner_rtol=1e-6,
                         newton_rtol=1e-10):
     """Solver settings of a time step: GMRES for CH and velocity prediction, Jacobi-PCG for the
     pressure Poisson and velocity update, all to the relative residual rtol. In the FP32 modes each
-    refinement cycle solves its correction to inner_rtol (CG) or 10 x inner_rtol (GMRES)."""
+    refinement cycle solves its correction to inner_rtol (CG) or 100 x inner_rtol (GMRES)."""
     gm = capi.make_solver(capi.KSP_GMRES, capi.PC_JACOBI, rtol, 4000, 30, inner,
-                          10 * inner_rtol)
+                          100 * inner_rtol)
     cg = capi.make_solver(capi.KSP_CG, capi.PC_JACOBI, rtol, 20000, 30, inner, inner_rtol,
                           check_every=pp_check_every)
     cgv = capi.make_solver(capi.KSP_CG, capi.PC_JACOBI, rtol, 4000, 30, inner, inner_rtol,
