@@ -69,7 +69,8 @@ k_apply_pq(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S* _
 //  4. hanging accumulators are distributed to their parents with the same weights;
 //  5. each regular slot is written once: a plain store when the patch owns the node, a global
 //     atomic add otherwise (nodes on the patch boundary). y must be zero on entry.
-// With PQ the element energies x_e . A_e x_e are summed into pq (x^T A x, deterministic).
+// With PQ the block sums of the element energies x_e . A_e x_e (summing to x^T A x) are written
+// to part[blockIdx.x]; the consumer kernel adds them in a fixed order.
 template <class K, class T, class S, class C, bool PQ>
 __global__ void __launch_bounds__(kPatchElems)
 k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S* __restrict__ y,
@@ -195,7 +196,7 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
         atomic_add(y + c * N + g, val);
     }
   }
-  if (PQ) block_reduce_finalize<1, kPatchElems>(en, part, 0, counter, pq);
+  if (PQ) block_write_partials<1, kPatchElems>(en, part, 0);
 }
 
 template <class K, class T>

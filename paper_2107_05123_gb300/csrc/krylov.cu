@@ -137,21 +137,20 @@ __global__ void k_mul_b2(const T* __restrict__ inv, const T* __restrict__ v, T* 
   }
 }
 
-// ---- CG: q = A p given. alpha = rz/pq; x += alpha p; r -= alpha q; z = dinv r;
-// partial sums of r.z and r.r land in S_TMP, S_TMP+1.
+// ---- CG. Scalars pass between kernels as per-block partial sums that the consuming kernel adds
+// in a fixed order (the launch boundary is the only global barrier; no fences or tickets).
+// k_cg_update: pq = sum of the np_pq partials of p.Ap; alpha = rz/pq; x += alpha p;
+// r -= alpha q; z = dinv r; writes its block partials of r.z and r.r to part2[0/1][block].
 template <class T>
 __global__ void __launch_bounds__(kVecThreads)
 k_cg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __restrict__ p,
-            const T* __restrict__ q, const T* __restrict__ dinv, int64_t n, double* __restrict__ S,
-            int parity, double* part, unsigned* counter) {
-  // one division per block (FP64 division is slow on this part), shared with the block
-  __shared__ T s_alpha;
-  if (threadIdx.x == 0) {
-    const double rz = S[S_RZ0 + parity], pq = S[S_PQ];
-    s_alpha = (T)((pq > 0.0 && isfinite(pq)) ? rz / pq : 0.0);
-  }
-  __syncthreads();
-  const T a = s_alpha;
+            const T* __restrict__ q, const T* __restrict__ dinv, int64_t n,
+            double* __restrict__ S, int parity, const double* __restrict__ pq_part, int np_pq,
+            double* __restrict__ part2) {
+  double pqv[1];
+  block_sum_partials<1, kVecThreads>(pq_part, 0, np_pq, pqv);
+  const double rz = S[S_RZ0 + parity];
+  const T a = (T)((pqv[0] > 0.0 && isfinite(pqv[0])) ? rz / pqv[0] : 0.0);
   T v0 = T(0), v1 = T(0);  // per-thread partial sums in T (a few terms), then FP64 across threads
   GRID_LOOP(i, n) {
     x[i] += a * p[i];
@@ -163,29 +162,38 @@ k_cg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __
     v1 += ri * ri;
   }
   double v[2] = {(double)v0, (double)v1};
-  reduce_finalize<2>(v, part, counter, S + S_TMP);
+  block_write_partials<2, kVecThreads>(v, part2, kRedSlots);
 }
 
-// beta = rz_new / rz_old; p = z + beta p; rotate rz into the other parity slot; publish r.r.
-// With q != null also clear q for the next apply (its scatter accumulates into zero).
+// k_cg_pupdate: rz_new, rr = sums of the np2 partials; beta = rz_new/rz_old; p = z + beta p
+// (q cleared for the next apply when given); block 0 publishes rz_new (next parity) and r.r.
 template <class T>
-__global__ void k_cg_pupdate(T* __restrict__ p, const T* __restrict__ z, T* __restrict__ q,
-                             int64_t n, double* __restrict__ S, int parity) {
-  __shared__ T s_beta;
-  if (threadIdx.x == 0) {
-    const double rz_old = S[S_RZ0 + parity], rz_new = S[S_TMP];
-    s_beta = (T)(rz_old != 0.0 ? rz_new / rz_old : 0.0);
-  }
-  __syncthreads();
-  const T b = s_beta;
+__global__ void __launch_bounds__(kVecThreads)
+k_cg_pupdate(T* __restrict__ p, const T* __restrict__ z, T* __restrict__ q, int64_t n,
+             double* __restrict__ S, int parity, const double* __restrict__ part2, int np2) {
+  double v[2];
+  block_sum_partials<2, kVecThreads>(part2, kRedSlots, np2, v);
+  const double rz_old = S[S_RZ0 + parity];
+  const T b = (T)(rz_old != 0.0 ? v[0] / rz_old : 0.0);
   GRID_LOOP(i, n) {
     p[i] = z[i] + b * p[i];
     if (q) q[i] = T(0);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    S[S_RZ0 + (parity ^ 1)] = S[S_TMP];
-    S[S_RR] = S[S_TMP + 1];
+    S[S_RZ0 + (parity ^ 1)] = v[0];
+    S[S_RR] = v[1];
   }
+}
+
+// p.q partials for the operators whose apply does not return them (no fence, no ticket)
+template <class T>
+__global__ void __launch_bounds__(kVecThreads)
+k_dot_partials(const T* __restrict__ a, const T* __restrict__ b, int64_t n,
+               double* __restrict__ part) {
+  T t = T(0);
+  GRID_LOOP(i, n) t += a[i] * b[i];
+  double v[1] = {(double)t};
+  block_write_partials<1, kVecThreads>(v, part, 0);
 }
 
 // ---- GMRES: multi-dot of rows V_0..V_{nk-1} with w; partials [nk][gridDim.x]
@@ -455,26 +463,32 @@ chns_status cg_iteration(const Ctx& c, cudaStream_t s, T* x, T* r, T* z, T* p, T
   const int64_t n = c.n;
   const unsigned rg = red_grid(c.m, n), vg = vgrid(c.m, n);
   const bool fused = c.op == CHNS_OP_POISSON;
+  // p.Ap partials: from the Poisson apply itself (one per patch), else from k_dot_partials
+  double* pq_part = c.m->ws.part_big;
+  int np_pq;
   chns_status st;
   if (fused) {
     if (sizeof(T) == sizeof(double))
-      st = apply_poisson_pq(c.m, c.prm, c.coef64, p, q, CHNS_FP64, c.S + S_PQ, s);
+      st = apply_poisson_pq(c.m, c.prm, c.coef64, p, q, CHNS_FP64, pq_part, s);
     else
-      st = apply_poisson_pq(c.m, c.prm, &c.coefR, p, q, c.inner, c.S + S_PQ, s);
+      st = apply_poisson_pq(c.m, c.prm, &c.coefR, p, q, c.inner, pq_part, s);
     if (st != CHNS_OK) return st;
+    np_pq = (int)c.m->d.n_patch;
   } else {
     Ctx cs = c;
     cs.s = s;
     st = apply_T<T>(cs, p, q);
     if (st != CHNS_OK) return st;
     note_launch();
-    k_dot<T, T><<<rg, kVecThreads, 0, s>>>(p, q, n, c.m->ws.red, c.m->ws.counter, c.S + S_PQ);
+    k_dot_partials<T><<<rg, kVecThreads, 0, s>>>(p, q, n, pq_part);
+    np_pq = (int)rg;
   }
   note_launch();
-  k_cg_update<T><<<rg, kVecThreads, 0, s>>>(x, r, z, p, q, dinv, n, c.S, par, c.m->ws.red,
-                                            c.m->ws.counter);
+  k_cg_update<T><<<rg, kVecThreads, 0, s>>>(x, r, z, p, q, dinv, n, c.S, par, pq_part, np_pq,
+                                            c.m->ws.red);
   note_launch();
-  k_cg_pupdate<T><<<vg, kVecThreads, 0, s>>>(p, z, fused ? q : nullptr, n, c.S, par);
+  k_cg_pupdate<T><<<vg, kVecThreads, 0, s>>>(p, z, fused ? q : nullptr, n, c.S, par, c.m->ws.red,
+                                             (int)rg);
   return CHNS_OK;
 }
 

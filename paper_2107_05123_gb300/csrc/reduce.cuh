@@ -55,4 +55,48 @@ __device__ __forceinline__ void block_reduce_finalize(double v[NV], double* __re
   }
 }
 
+// Write this block's NV sums to part[k * pstride + blockIdx.x] (no fence, no ticket): a later
+// kernel, after the launch boundary, adds the partials with block_sum_partials.
+template <int NV, int BS>
+__device__ __forceinline__ void block_write_partials(double v[NV], double* __restrict__ part,
+                                                     int64_t pstride) {
+  __shared__ double sh[NV][BS];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = v[k];
+  __syncthreads();
+  for (int w = BS / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) part[k * pstride + blockIdx.x] = sh[k][0];
+}
+
+// Sum np partials part[k * pstride + b] (b < np) in a fixed order; every thread of the block
+// receives the totals in out[k]. The summation order depends only on np and BS.
+template <int NV, int BS>
+__device__ __forceinline__ void block_sum_partials(const double* __restrict__ part, int64_t pstride,
+                                                   int np, double out[NV]) {
+  __shared__ double sh[NV][BS];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < np; b += BS) t += part[k * pstride + b];
+    sh[k][threadIdx.x] = t;
+  }
+  __syncthreads();
+  for (int w = BS / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = sh[k][0];
+  __syncthreads();
+}
+
 }  // namespace chns
