@@ -71,10 +71,11 @@ k_apply_pq(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S* _
 //     atomic add otherwise (nodes on the patch boundary). y must be zero on entry.
 // With PQ the block sums of the element energies x_e . A_e x_e (summing to x^T A x) are written
 // to part[blockIdx.x]; the consumer kernel adds them in a fixed order.
-template <class K, class T, class S, class C, bool PQ>
+template <class K, class T, class S, class C, bool PQ, bool CGP>
 __global__ void __launch_bounds__(kPatchElems)
 k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S* __restrict__ y,
-              double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ pq) {
+              double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ S_cg,
+              const S* __restrict__ zcg, S* __restrict__ pout) {
   constexpr int NC = K::NC, NF = K::NF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* xs = reinterpret_cast<T*>(smem_raw);       // [NC][kPatchSlots]
@@ -84,6 +85,19 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
   const int s0 = m.patch_slot[pidx], ns = m.patch_slot[pidx + 1] - s0, nreg = m.patch_nreg[pidx];
   const int64_t N = m.n_nodes;
   const C* fptr[5] = {cf.phi, cf.u[0], cf.u[1], cf.u[2], cf.mu};
+  // With PQ the last thread publishes the block's partial of p.Ap: it stores nothing to global
+  // memory before that, so that its fence is cheap.
+  constexpr int kPub = kPatchElems - 1;
+  const int gstride = PQ ? kPatchElems - 1 : kPatchElems;
+  const bool gworker = !PQ || (int)threadIdx.x != kPub;
+  // CG direction update fused into the gather (CGP): p_new = z + beta p_old with
+  // beta = rz_cur / rz_prev; x holds p_old and p_new goes to pout (separate buffers, so that a
+  // patch never reads a p value another patch has already updated)
+  __shared__ T s_beta;
+  if (CGP && threadIdx.x == 0) {
+    const double rzc = S_cg[kCgRzCur], rzp = S_cg[kCgRzPrev];
+    s_beta = (T)(rzp != 0.0 ? rzc / rzp : 0.0);
+  }
   // the element's local corner slots and level are loaded first, so that their latency overlaps
   // the gather of the patch's nodes
   const int64_t e = (int64_t)m.patch_elem[pidx] + threadIdx.x;
@@ -94,21 +108,32 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
     lp = __ldg(m.eloc + e);
     lev = __ldg(m.level + e);
   }
+  if (CGP) __syncthreads();
   // 1. regular slots
-  for (int i = threadIdx.x; i < nreg; i += blockDim.x) {
-    const int32_t v = m.slot_node[s0 + i];
-    const int64_t g = v & kNodeMask;
-    const bool dir = K::DIR && (v & kDirBit);
+  if (gworker) {
+    for (int i = threadIdx.x; i < nreg; i += gstride) {
+      const int32_t v = m.slot_node[s0 + i];
+      const int64_t g = v & kNodeMask;
+      const bool dir = K::DIR && (v & kDirBit);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      xs[c * kPatchSlots + i] = dir ? T(0) : (T)x[c * N + g];
-      ys[c * kPatchSlots + i] = T(0);
-    }
+      for (int c = 0; c < NC; ++c) {
+        T xv;
+        if (CGP) {
+          const S pv = zcg[c * N + g] + (S)s_beta * x[c * N + g];
+          pout[c * N + g] = pv;  // patches sharing the node store the same value
+          xv = (T)pv;
+        } else {
+          xv = (T)x[c * N + g];
+        }
+        xs[c * kPatchSlots + i] = dir ? T(0) : xv;
+        ys[c * kPatchSlots + i] = T(0);
+      }
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      T val = ldv<T>(fptr[f], g);
-      if (f == 0) val += T(cf.phi_shift);
-      fs[f * kPatchSlots + i] = val;
+      for (int f = 0; f < NF; ++f) {
+        T val = ldv<T>(fptr[f], g);
+        if (f == 0) val += T(cf.phi_shift);
+        fs[f * kPatchSlots + i] = val;
+      }
     }
   }
   __syncthreads();
@@ -155,13 +180,21 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
       for (int a = 0; a < 8; ++a) xin[c][a] = xs[c * kPatchSlots + sl[a]];
     T r[NC][8];
     k.apply(g, p, xin, r);
+    T ent = T(0);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
-        if (PQ) en[0] += (double)xin[c][a] * (double)r[c][a];
+        if (PQ) ent += xin[c][a] * r[c][a];
         atomicAdd(ys + c * kPatchSlots + sl[a], r[c][a]);
       }
+    en[0] = (double)ent;
+  }
+  // p.Ap: published before any global store of this block's results
+  if (PQ) {
+    __shared__ double tot[1];
+    if (block_reduce_ticket<1, kPatchElems>(en, part, 0, counter, kPub, tot) && threadIdx.x == 0)
+      S_cg[kCgPq] = tot[0];
   }
   __syncthreads();
   // 4. hanging slots -> parents
@@ -196,7 +229,6 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
         atomic_add(y + c * N + g, val);
     }
   }
-  if (PQ) block_write_partials<1, kPatchElems>(en, part, 0);
 }
 
 template <class K, class T>
@@ -205,19 +237,20 @@ constexpr size_t patch_smem() {
 }
 
 // Launch the patch apply, raising the dynamic shared-memory limit once per instantiation.
-template <class K, class T, class S, class C, bool PQ>
+template <class K, class T, class S, class C, bool PQ, bool CGP = false>
 static void launch_patch(const chns_mesh* m, const DevParams& p, const CoefArgs<C>& cf,
-                         const S* x, S* y, double* pq, cudaStream_t s) {
+                         const S* x, S* y, double* S_cg, cudaStream_t s, const S* z = nullptr,
+                         S* pout = nullptr) {
   constexpr size_t smem = patch_smem<K, T>();
   static bool configured = false;  // per instantiation
   if (!configured) {
-    cudaFuncSetAttribute(k_apply_patch<K, T, S, C, PQ>,
+    cudaFuncSetAttribute(k_apply_patch<K, T, S, C, PQ, CGP>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = true;
   }
   note_launch();
-  k_apply_patch<K, T, S, C, PQ><<<(unsigned)m->d.n_patch, kPatchElems, smem, s>>>(
-      m->d, p, cf, x, y, m->ws.part_big, m->ws.counter + 1, pq);
+  k_apply_patch<K, T, S, C, PQ, CGP><<<(unsigned)m->d.n_patch, kPatchElems, smem, s>>>(
+      m->d, p, cf, x, y, m->ws.part_big, m->ws.counter + 1, S_cg, z, pout);
 }
 
 // Reference (corner a, slot k) -> node reference with Dirichlet bit and its weight, or -1.
@@ -477,27 +510,28 @@ chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm
   return CHNS_OK;
 }
 
-chns_status apply_poisson_pq(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
-                             const void* x, void* y, chns_precision prec, double* pq,
-                             cudaStream_t s) {
+chns_status apply_poisson_cg(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
+                             const void* z, const void* p_old, void* p_new, void* y,
+                             chns_precision prec, double* S_cg, cudaStream_t s) {
   chns_status st = check_coef(CHNS_OP_POISSON, coef);
   if (st != CHNS_OK) return st;
   const DevParams p = make_dev_params(*prm);
   switch (prec) {
     case CHNS_FP64:
-      launch_patch<PoissonK<double, double>, double, double, double, true>(
-          m, p, coef_args<double>(coef), static_cast<const double*>(x), static_cast<double*>(y),
-          pq, s);
+      launch_patch<PoissonK<double, double>, double, double, double, true, true>(
+          m, p, coef_args<double>(coef), static_cast<const double*>(p_old),
+          static_cast<double*>(y), S_cg, s, static_cast<const double*>(z),
+          static_cast<double*>(p_new));
       break;
     case CHNS_FP32:
-      launch_patch<PoissonK<float, float>, float, float, float, true>(
-          m, p, coef_args<float>(coef), static_cast<const float*>(x), static_cast<float*>(y), pq,
-          s);
+      launch_patch<PoissonK<float, float>, float, float, float, true, true>(
+          m, p, coef_args<float>(coef), static_cast<const float*>(p_old), static_cast<float*>(y),
+          S_cg, s, static_cast<const float*>(z), static_cast<float*>(p_new));
       break;
     case CHNS_FP32_BF16COEF:
-      launch_patch<PoissonK<float, __nv_bfloat16>, float, float, __nv_bfloat16, true>(
-          m, p, coef_args<__nv_bfloat16>(coef), static_cast<const float*>(x),
-          static_cast<float*>(y), pq, s);
+      launch_patch<PoissonK<float, __nv_bfloat16>, float, float, __nv_bfloat16, true, true>(
+          m, p, coef_args<__nv_bfloat16>(coef), static_cast<const float*>(p_old),
+          static_cast<float*>(y), S_cg, s, static_cast<const float*>(z), static_cast<float*>(p_new));
       break;
     default:
       set_error("apply: bad precision");

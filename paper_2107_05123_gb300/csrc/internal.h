@@ -131,11 +131,14 @@ constexpr int kScalarBase = 3 * 4096;  // scalars stored after three partial arr
 chns_status apply_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
                      const chns_coef* coef, const void* x, void* y, chns_precision prec,
                      cudaStream_t s);
-// y = A x for the Poisson operator with y already zero, also writing p.Ap (= x^T A x, summed
-// element by element in FP64) to pq_dev; deterministic reduction.
-chns_status apply_poisson_pq(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
-                             const void* x, void* y, chns_precision prec, double* pq_dev,
-                             cudaStream_t s);
+// Slots of the CG scalars (offsets from the scalar area of ws.red).
+constexpr int kCgRzCur = 0, kCgRzPrev = 1, kCgPq = 2, kCgRr = 3;
+// One fused CG step of the Poisson operator: p_new = z + beta p_old (beta = S[rz_cur]/S[rz_prev])
+// during the gather, y = A p_new (y zero on entry), and S[pq] = p_new.A p_new (deterministic
+// last-block sum).
+chns_status apply_poisson_cg(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
+                             const void* z, const void* p_old, void* p_new, void* y,
+                             chns_precision prec, double* S_cg, cudaStream_t s);
 chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
                     const chns_coef* coef, void* d, chns_precision prec, cudaStream_t s);
 // 2x2 nodal blocks of the CH Jacobian, d4 = [d_pp, d_pm, d_mp, d_mm] x n_nodes (FP64 or FP32)

@@ -137,63 +137,60 @@ __global__ void k_mul_b2(const T* __restrict__ inv, const T* __restrict__ v, T* 
   }
 }
 
-// ---- CG. Scalars pass between kernels as per-block partial sums that the consuming kernel adds
-// in a fixed order (the launch boundary is the only global barrier; no fences or tickets).
-// k_cg_update: pq = sum of the np_pq partials of p.Ap; alpha = rz/pq; x += alpha p;
-// r -= alpha q; z = dinv r; writes its block partials of r.z and r.r to part2[0/1][block].
+// ---- CG kernels. Scalars live in device memory: S[kCgRzCur], S[kCgRzPrev], S[kCgPq], S[kCgRr].
+// k_cg_update: alpha = rz_cur / pq (one division per block); x += alpha p; r -= alpha q;
+// z = dinv r (q cleared when zero_q); r.z and r.r are reduced with the last thread of each block as
+// publisher (it stores nothing else, so its fence is cheap); the last block rotates
+// rz_prev <- rz_cur <- r.z and stores r.r.
 template <class T>
 __global__ void __launch_bounds__(kVecThreads)
 k_cg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __restrict__ p,
-            const T* __restrict__ q, const T* __restrict__ dinv, int64_t n,
-            double* __restrict__ S, int parity, const double* __restrict__ pq_part, int np_pq,
-            double* __restrict__ part2) {
-  double pqv[1];
-  block_sum_partials<1, kVecThreads>(pq_part, 0, np_pq, pqv);
-  const double rz = S[S_RZ0 + parity];
-  const T a = (T)((pqv[0] > 0.0 && isfinite(pqv[0])) ? rz / pqv[0] : 0.0);
+            T* __restrict__ q, const T* __restrict__ dinv, int64_t n, double* __restrict__ S,
+            bool zero_q, double* __restrict__ part, unsigned* __restrict__ counter) {
+  constexpr int kPub = kVecThreads - 1;
+  __shared__ T s_alpha;
+  if (threadIdx.x == 0) {
+    const double rz = S[kCgRzCur], pq = S[kCgPq];
+    s_alpha = (T)((pq > 0.0 && isfinite(pq)) ? rz / pq : 0.0);
+  }
+  __syncthreads();
+  const T a = s_alpha;
   T v0 = T(0), v1 = T(0);  // per-thread partial sums in T (a few terms), then FP64 across threads
-  GRID_LOOP(i, n) {
-    x[i] += a * p[i];
-    const T ri = r[i] - a * q[i];
-    r[i] = ri;
-    const T zi = dinv ? dinv[i] * ri : ri;
-    z[i] = zi;
-    v0 += ri * zi;
-    v1 += ri * ri;
+  if ((int)threadIdx.x != kPub) {
+    const int64_t stride = (int64_t)gridDim.x * (kVecThreads - 1);
+    for (int64_t i = blockIdx.x * (int64_t)(kVecThreads - 1) + threadIdx.x; i < n; i += stride) {
+      x[i] += a * p[i];
+      const T ri = r[i] - a * q[i];
+      if (zero_q) q[i] = T(0);
+      r[i] = ri;
+      const T zi = dinv ? dinv[i] * ri : ri;
+      z[i] = zi;
+      v0 += ri * zi;
+      v1 += ri * ri;
+    }
   }
   double v[2] = {(double)v0, (double)v1};
-  block_write_partials<2, kVecThreads>(v, part2, kRedSlots);
-}
-
-// k_cg_pupdate: rz_new, rr = sums of the np2 partials; beta = rz_new/rz_old; p = z + beta p
-// (q cleared for the next apply when given); block 0 publishes rz_new (next parity) and r.r.
-template <class T>
-__global__ void __launch_bounds__(kVecThreads)
-k_cg_pupdate(T* __restrict__ p, const T* __restrict__ z, T* __restrict__ q, int64_t n,
-             double* __restrict__ S, int parity, const double* __restrict__ part2, int np2) {
-  double v[2];
-  block_sum_partials<2, kVecThreads>(part2, kRedSlots, np2, v);
-  const double rz_old = S[S_RZ0 + parity];
-  const T b = (T)(rz_old != 0.0 ? v[0] / rz_old : 0.0);
-  GRID_LOOP(i, n) {
-    p[i] = z[i] + b * p[i];
-    if (q) q[i] = T(0);
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    S[S_RZ0 + (parity ^ 1)] = v[0];
-    S[S_RR] = v[1];
+  __shared__ double tot[2];
+  if (block_reduce_ticket<2, kVecThreads>(v, part, kRedSlots, counter, kPub, tot) &&
+      threadIdx.x == 0) {
+    S[kCgRzPrev] = S[kCgRzCur];
+    S[kCgRzCur] = tot[0];
+    S[kCgRr] = tot[1];
   }
 }
 
-// p.q partials for the operators whose apply does not return them (no fence, no ticket)
+// p_new = z + beta p_old with beta = rz_cur / rz_prev (operators whose apply does not fuse it)
 template <class T>
-__global__ void __launch_bounds__(kVecThreads)
-k_dot_partials(const T* __restrict__ a, const T* __restrict__ b, int64_t n,
-               double* __restrict__ part) {
-  T t = T(0);
-  GRID_LOOP(i, n) t += a[i] * b[i];
-  double v[1] = {(double)t};
-  block_write_partials<1, kVecThreads>(v, part, 0);
+__global__ void k_cg_pupdate(const T* __restrict__ z, const T* __restrict__ p_old,
+                             T* __restrict__ p_new, int64_t n, const double* __restrict__ S) {
+  __shared__ T s_beta;
+  if (threadIdx.x == 0) {
+    const double rzc = S[kCgRzCur], rzp = S[kCgRzPrev];
+    s_beta = (T)(rzp != 0.0 ? rzc / rzp : 0.0);
+  }
+  __syncthreads();
+  const T b = s_beta;
+  GRID_LOOP(i, n) p_new[i] = z[i] + b * p_old[i];
 }
 
 // ---- GMRES: multi-dot of rows V_0..V_{nk-1} with w; partials [nk][gridDim.x]
@@ -454,41 +451,36 @@ chns_status project_mean(const Ctx& c, T* v) {
   return CHNS_OK;
 }
 
-// One CG iteration: q = A p and p.q, then x, r, z and r.z, r.r, then p = z + beta p.
-// Poisson: the apply also returns p.Ap (element energies) and q is cleared by the p update, so an
-// iteration is three kernels. Other operators: apply (clears q itself), dot, update, p update.
+// One CG iteration with direction buffers p_old -> p_new. Poisson: two kernels (the apply fuses
+// p_new = z + beta p_old into its gather and returns p.Ap; the update clears q for the next
+// apply). Other operators: p update, apply, dot, update.
 template <class T>
-chns_status cg_iteration(const Ctx& c, cudaStream_t s, T* x, T* r, T* z, T* p, T* q,
-                         const T* dinv, int par) {
+chns_status cg_iteration(const Ctx& c, cudaStream_t s, T* x, T* r, T* z, const T* p_old,
+                         T* p_new, T* q, const T* dinv) {
   const int64_t n = c.n;
   const unsigned rg = red_grid(c.m, n), vg = vgrid(c.m, n);
   const bool fused = c.op == CHNS_OP_POISSON;
-  // p.Ap partials: from the Poisson apply itself (one per patch), else from k_dot_partials
-  double* pq_part = c.m->ws.part_big;
-  int np_pq;
   chns_status st;
   if (fused) {
     if (sizeof(T) == sizeof(double))
-      st = apply_poisson_pq(c.m, c.prm, c.coef64, p, q, CHNS_FP64, pq_part, s);
+      st = apply_poisson_cg(c.m, c.prm, c.coef64, z, p_old, p_new, q, CHNS_FP64, c.S, s);
     else
-      st = apply_poisson_pq(c.m, c.prm, &c.coefR, p, q, c.inner, pq_part, s);
+      st = apply_poisson_cg(c.m, c.prm, &c.coefR, z, p_old, p_new, q, c.inner, c.S, s);
     if (st != CHNS_OK) return st;
-    np_pq = (int)c.m->d.n_patch;
   } else {
+    note_launch();
+    k_cg_pupdate<T><<<vg, kVecThreads, 0, s>>>(z, p_old, p_new, n, c.S);
     Ctx cs = c;
     cs.s = s;
-    st = apply_T<T>(cs, p, q);
+    st = apply_T<T>(cs, p_new, q);
     if (st != CHNS_OK) return st;
     note_launch();
-    k_dot_partials<T><<<rg, kVecThreads, 0, s>>>(p, q, n, pq_part);
-    np_pq = (int)rg;
+    k_dot<T, T><<<rg, kVecThreads, 0, s>>>(p_new, q, n, c.m->ws.red, c.m->ws.counter,
+                                            c.S + kCgPq);
   }
   note_launch();
-  k_cg_update<T><<<rg, kVecThreads, 0, s>>>(x, r, z, p, q, dinv, n, c.S, par, pq_part, np_pq,
-                                            c.m->ws.red);
-  note_launch();
-  k_cg_pupdate<T><<<vg, kVecThreads, 0, s>>>(p, z, fused ? q : nullptr, n, c.S, par, c.m->ws.red,
-                                             (int)rg);
+  k_cg_update<T><<<rg, kVecThreads, 0, s>>>(x, r, z, p_new, q, dinv, n, c.S, fused, c.m->ws.red,
+                                            c.m->ws.counter);
   return CHNS_OK;
 }
 
@@ -499,7 +491,8 @@ chns_status cg_iteration(const Ctx& c, cudaStream_t s, T* x, T* r, T* z, T* p, T
 // to two chunks beyond the iteration that reached the tolerance; they only reduce the residual.
 template <class T>
 chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, int max_it,
-                int chunk, T* r, T* z, T* p, T* q, int* iters, double* rnorm) {
+                int chunk, T* r, T* z, T* p, T* q, T* p2, int* iters, double* rnorm) {
+  T* pb[2] = {p, p2};  // direction buffers: iteration k reads pb[k & 1], writes pb[(k & 1) ^ 1]
   const int64_t n = c.n;
   const unsigned rg = red_grid(c.m, n), vg = vgrid(c.m, n);
   chns_status st = apply_T<T>(c, x, q);
@@ -509,16 +502,20 @@ chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, i
   if (c.op == CHNS_OP_POISSON) project_mean<T>(c, r);
   note_launch();
   k_mul<T><<<vg, kVecThreads, 0, c.s>>>(dinv, r, z, n);
-  CHNS_CUDA(cudaMemcpyAsync(p, z, n * sizeof(T), cudaMemcpyDeviceToDevice, c.s));
+  // p_old = 0 and rz_prev = rz_cur make the first direction p = z
+  CHNS_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), c.s));
   CHNS_CUDA(cudaMemsetAsync(q, 0, n * sizeof(T), c.s));
   note_launch();
-  k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, z, n, c.m->ws.red, c.m->ws.counter, c.S + S_RZ0);
+  k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, z, n, c.m->ws.red, c.m->ws.counter,
+                                          c.S + kCgRzCur);
+  CHNS_CUDA(cudaMemcpyAsync(c.S + kCgRzPrev, c.S + kCgRzCur, sizeof(double),
+                            cudaMemcpyDeviceToDevice, c.s));
   note_launch();
-  k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, r, n, c.m->ws.red, c.m->ws.counter, c.S + S_RR);
+  k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, r, n, c.m->ws.red, c.m->ws.counter, c.S + kCgRr);
   CHNS_CUDA(cudaGetLastError());
   int it = 0;
   double rr = 0.0;
-  st = read_dev(c.m, c.S + S_RR, &rr, 1, c.s);
+  st = read_dev(c.m, c.S + kCgRr, &rr, 1, c.s);
   if (st != CHNS_OK) return st;
   auto bad = [&](double v) {
     if (std::isfinite(v)) return false;
@@ -532,10 +529,10 @@ chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, i
   }
   if (chunk < 2) {
     while (std::sqrt(rr) > tol_abs && it < max_it) {
-      st = cg_iteration<T>(c, c.s, x, r, z, p, q, dinv, it & 1);
+      st = cg_iteration<T>(c, c.s, x, r, z, pb[it & 1], pb[(it & 1) ^ 1], q, dinv);
       if (st != CHNS_OK) return st;
       ++it;
-      st = read_dev(c.m, c.S + S_RR, &rr, 1, c.s);
+      st = read_dev(c.m, c.S + kCgRr, &rr, 1, c.s);
       if (st != CHNS_OK) return st;
       if (bad(rr)) {
         *iters = it;
@@ -556,8 +553,8 @@ chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, i
       CHNS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
       const unsigned long long l0 = chns_launches_now();
       for (int i = 0; i < chunk && rc == CHNS_OK; ++i)
-        rc = cg_iteration<T>(c, cs, x, r, z, p, q, dinv, i & 1);
-      cudaMemcpyAsync((void*)(slot + v), c.S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, cs);
+        rc = cg_iteration<T>(c, cs, x, r, z, pb[i & 1], pb[(i & 1) ^ 1], q, dinv);
+      cudaMemcpyAsync((void*)(slot + v), c.S + kCgRr, sizeof(double), cudaMemcpyDeviceToHost, cs);
       per_graph = chns_launches_now() - l0;
       cudaError_t e1 = cudaStreamEndCapture(cs, &g);
       if (rc != CHNS_OK) {
@@ -864,7 +861,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
       double rn = 0.0;
       if (sp->ksp == CHNS_KSP_CG)
         st = pcg<double>(c, b, x, dinv64, tol, sp->max_it, sp->check_every, r64, ws.v64[3],
-                         ws.v64[4], ws.v64[5], &its, &rn);
+                         ws.v64[4], ws.v64[5], ws.v64[6], &its, &rn);
       else
         st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it, sp->restart, ws.gm_V,
                            ws.v64[7], &its, &rn);
@@ -943,7 +940,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
             double frn = 0.0;
             if (sp->ksp == CHNS_KSP_CG)
               st = pcg<double>(c, b, x, dinv64, tol, sp->max_it - total, sp->check_every, r64,
-                               ws.v64[3], ws.v64[4], ws.v64[5], &its, &frn);
+                               ws.v64[3], ws.v64[4], ws.v64[5], ws.v64[6], &its, &frn);
             else
               st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it - total, sp->restart, ws.gm_V,
                                  ws.v64[7], &its, &frn);
@@ -968,7 +965,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
         chns_status ist;
         if (sp->ksp == CHNS_KSP_CG)
           ist = pcg<float>(c, r32, d32, dinv32, itol, budget, sp->check_every, ws.v32[3],
-                           ws.v32[4], ws.v32[5], ws.v32[6], &its, &irn);
+                           ws.v32[4], ws.v32[5], ws.v32[6], ws.v32[8], &its, &irn);
         else
           ist = gmres<float>(c, r32, d32, dinv32, block2, itol, budget, sp->restart, ws.gm_V32,
                              ws.v32[7], &its, &irn);
