@@ -31,35 +31,6 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(MeshDev m, DevParams p,
   for (int c = 0; c < K::NC; ++c) scatter<T, K::DIR>(m, idx, r[c], y + c * m.n_nodes);
 }
 
-// k_apply with the element energy x_e . (A_e x_e) summed in FP64: with y = A x this is x^T A x,
-// the p.Ap of a CG iteration, obtained without reading y back. y must be zero on entry.
-template <class K, class T, class S, class C>
-__global__ void __launch_bounds__(kApplyThreads)
-k_apply_pq(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S* __restrict__ y,
-           double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ pq) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double en[1] = {0.0};
-  if (e < m.n_elem) {
-    int idx[8];
-    load_corners(m, e, idx);
-    const Geo<T> g = geometry<T>(m, e);
-    K k;
-    k.load(m, p, cf, idx, g);
-    T xin[K::NC][8];
-#pragma unroll
-    for (int c = 0; c < K::NC; ++c) gather<T, K::DIR>(m, idx, x + c * m.n_nodes, xin[c]);
-    T r[K::NC][8];
-    k.apply(g, p, xin, r);
-#pragma unroll
-    for (int c = 0; c < K::NC; ++c) {
-#pragma unroll
-      for (int a = 0; a < 8; ++a) en[0] += (double)xin[c][a] * (double)r[c][a];
-      scatter<T, K::DIR>(m, idx, r[c], y + c * m.n_nodes);
-    }
-  }
-  block_reduce_finalize<1, kApplyThreads>(en, part, 0, counter, pq);
-}
-
 // Patch apply: one CTA per patch (kPatchElems Morton-consecutive elements, one thread each).
 //  1. the patch's regular slots are gathered once into shared memory (input components and
 //     coefficient fields), Dirichlet nodes as zero for DIR operators;
@@ -160,7 +131,7 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
   }
   __syncthreads();
   // 3. elements
-  double en[1] = {0.0};
+  typename Acc<T>::type en[1] = {Acc<T>::zero()};
   if (has_elem) {
     const int sl[8] = {(int)(lp.x & 0xffff), (int)(lp.x >> 16), (int)(lp.y & 0xffff),
                        (int)(lp.y >> 16),    (int)(lp.z & 0xffff), (int)(lp.z >> 16),
@@ -180,15 +151,13 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
       for (int a = 0; a < 8; ++a) xin[c][a] = xs[c * kPatchSlots + sl[a]];
     T r[NC][8];
     k.apply(g, p, xin, r);
-    T ent = T(0);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
-        if (PQ) ent += xin[c][a] * r[c][a];
+        if (PQ) Acc<T>::fma(en[0], xin[c][a], r[c][a]);
         atomicAdd(ys + c * kPatchSlots + sl[a], r[c][a]);
       }
-    en[0] = (double)ent;
   }
   // p.Ap: published before any global store of this block's results
   if (PQ) {

@@ -27,8 +27,8 @@ enum Slot { S_RZ0 = 0, S_RZ1 = 1, S_PQ = 2, S_RR = 3, S_TMP = 8, S_AUX = 16, S_M
 
 // ------------------------------------------------------------------ device kernels
 // Block reduction of NV sums with the fixed-order last-block finalisation of reduce.cuh.
-template <int NV>
-__device__ __forceinline__ void reduce_finalize(double v[NV], double* __restrict__ part,
+template <int NV, class A>
+__device__ __forceinline__ void reduce_finalize(A (&v)[NV], double* __restrict__ part,
                                                 unsigned* __restrict__ counter,
                                                 double* __restrict__ out) {
   block_reduce_finalize<NV, kVecThreads>(v, part, kRedSlots, counter, out);
@@ -42,17 +42,18 @@ template <class A, class B>
 __global__ void __launch_bounds__(kVecThreads)
 k_dot(const A* __restrict__ a, const B* __restrict__ b, int64_t n, double* part, unsigned* counter,
       double* out) {
-  A t = A(0);  // per-thread partial sum in the vector type, FP64 across threads
-  GRID_LOOP(i, n) t += a[i] * (A)b[i];
-  double v[1] = {(double)t};
+  typename Acc<A>::type t = Acc<A>::zero();  // double-float for FP32 vectors, FP64 for FP64
+  GRID_LOOP(i, n) Acc<A>::fma(t, a[i], (A)b[i]);
+  typename Acc<A>::type v[1] = {t};
   reduce_finalize<1>(v, part, counter, out);
 }
 
 template <class A>
 __global__ void __launch_bounds__(kVecThreads)
 k_sum(const A* __restrict__ a, int64_t n, double* part, unsigned* counter, double* out) {
-  double v[1] = {0.0};
-  GRID_LOOP(i, n) v[0] += (double)a[i];
+  typename Acc<A>::type t = Acc<A>::zero();
+  GRID_LOOP(i, n) Acc<A>::add(t, a[i]);
+  typename Acc<A>::type v[1] = {t};
   reduce_finalize<1>(v, part, counter, out);
 }
 
@@ -155,7 +156,7 @@ k_cg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __
   }
   __syncthreads();
   const T a = s_alpha;
-  T v0 = T(0), v1 = T(0);  // per-thread partial sums in T (a few terms), then FP64 across threads
+  typename Acc<T>::type v0 = Acc<T>::zero(), v1 = Acc<T>::zero();
   if ((int)threadIdx.x != kPub) {
     const int64_t stride = (int64_t)gridDim.x * (kVecThreads - 1);
     for (int64_t i = blockIdx.x * (int64_t)(kVecThreads - 1) + threadIdx.x; i < n; i += stride) {
@@ -165,11 +166,11 @@ k_cg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __
       r[i] = ri;
       const T zi = dinv ? dinv[i] * ri : ri;
       z[i] = zi;
-      v0 += ri * zi;
-      v1 += ri * ri;
+      Acc<T>::fma(v0, ri, zi);
+      Acc<T>::fma(v1, ri, ri);
     }
   }
-  double v[2] = {(double)v0, (double)v1};
+  typename Acc<T>::type v[2] = {v0, v1};
   __shared__ double tot[2];
   if (block_reduce_ticket<2, kVecThreads>(v, part, kRedSlots, counter, kPub, tot) &&
       threadIdx.x == 0) {
@@ -193,35 +194,14 @@ __global__ void k_cg_pupdate(const T* __restrict__ z, const T* __restrict__ p_ol
   GRID_LOOP(i, n) p_new[i] = z[i] + b * p_old[i];
 }
 
-// ---- GMRES: multi-dot of rows V_0..V_{nk-1} with w; partials [nk][gridDim.x]
-template <class T>
+// ---- GMRES
 __global__ void __launch_bounds__(kVecThreads)
-k_multidot(const T* __restrict__ V, int64_t ld, const T* __restrict__ w, int64_t n,
-           double* __restrict__ part) {
-  __shared__ double sh[kVecThreads];
-  const T* vk = V + (int64_t)blockIdx.y * ld;
-  double s = 0.0;
-  GRID_LOOP(i, n) s += (double)vk[i] * (double)w[i];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int q = kVecThreads / 2; q > 0; q >>= 1) {
-    if ((int)threadIdx.x < q) sh[threadIdx.x] += sh[threadIdx.x + q];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = sh[0];
-}
-
-__global__ void k_multidot_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
-  __shared__ double sh[kVecThreads];
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += kVecThreads) s += part[(int64_t)blockIdx.x * nb + b];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int q = kVecThreads / 2; q > 0; q >>= 1) {
-    if ((int)threadIdx.x < q) sh[threadIdx.x] += sh[threadIdx.x + q];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+k_multidot_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  double s[1] = {0.0};
+  for (int b = threadIdx.x; b < nb; b += kVecThreads) s[0] += part[(int64_t)blockIdx.x * nb + b];
+  double t[1];
+  block_sum<1, kVecThreads>(s, t);
+  if (threadIdx.x == 0) out[blockIdx.x] = t[0];
 }
 
 // w -= sum_k h_k V_k
@@ -274,18 +254,16 @@ k_multidot2(const T* __restrict__ V, int64_t ld, int nk, const T* __restrict__ w
       wsl[t] = (i0 + t < n) ? w[i0 + t] : T(0);
     __syncthreads();
     for (int k = 0; k <= nk; ++k) {
-      T sum = T(0);
+      typename Acc<T>::type sum = Acc<T>::zero();
       if (k < nk) {
         const T* vk = V + (int64_t)k * ld + i0;
         for (int t = threadIdx.x; t < kMd2Slice; t += kMd2Threads)
-          if (i0 + t < n) sum += vk[t] * wsl[t];
+          if (i0 + t < n) Acc<T>::fma(sum, vk[t], wsl[t]);
       } else {
-        for (int t = threadIdx.x; t < kMd2Slice; t += kMd2Threads) sum += wsl[t] * wsl[t];
+        for (int t = threadIdx.x; t < kMd2Slice; t += kMd2Threads) Acc<T>::fma(sum, wsl[t], wsl[t]);
       }
-      double d = (double)sum;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-      if (lane == 0) acc[k][warp] += d;
+      const auto d = warp_sum(sum);
+      if (lane == 0) acc[k][warp] += acc_value(d);
     }
   }
   __syncthreads();

@@ -1,82 +1,124 @@
-// Deterministic FP64 block reductions with last-block finalisation: every block writes its
-// partial sums to part[k * pstride + blockIdx.x]; the last block to finish (atomic ticket) sums
-// the partials in a fixed order, writes out[k] and resets the ticket. The result does not depend
-// on block scheduling.
+// Reductions for the Krylov scalars.
+//
+// FP64 arithmetic has long latency on this part (a block-wide FP64 shared-memory tree costs more
+// than the vector update it reduces), so the per-thread and per-warp stages of the dot products
+// of FP32 vectors use double-float (float-pair) arithmetic: products are split exactly with an FMA
+// (p = a*b, e = fma(a, b, -p)) and sums use Knuth's TwoSum, so a warp's sum carries ~48 bits of
+// significand, as an FP64 sum would. Only the 8 warp sums of a block and the block partials are
+// added in FP64. FP64 vectors use FP64 throughout (warp shuffles, no shared-memory tree).
+//
+// Block partials are combined by the last block to finish (atomic ticket) in a fixed order, so
+// results do not depend on scheduling.
 #pragma once
 
 #include "internal.h"
 
 namespace chns {
 
-template <int NV, int BS>
-__device__ __forceinline__ void block_reduce_finalize(double v[NV], double* __restrict__ part,
-                                                      int64_t pstride,
-                                                      unsigned* __restrict__ counter,
-                                                      double* __restrict__ out) {
-  __shared__ double sh[NV][BS];
-  __shared__ bool last;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = v[k];
-  __syncthreads();
-  for (int w = BS / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) part[k * pstride + blockIdx.x] = sh[k][0];
-    __threadfence();
-    unsigned t = atomicAdd(counter, 1u);
-    last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double s = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += BS)
-      s += ((volatile double*)part)[k * pstride + b];
-    sh[k][threadIdx.x] = s;
-  }
-  __syncthreads();
-  for (int w = BS / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) out[k] = sh[k][0];
-    *counter = 0u;
-  }
+// ---- double-float accumulator
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_zero() { return DF{0.f, 0.f}; }
+
+// a + b with the rounding error of the high parts kept (TwoSum)
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float bp = s - a.hi;
+  const float err = (a.hi - (s - bp)) + (b.hi - bp);
+  const float lo = a.lo + b.lo + err;
+  const float hi = s + lo;
+  return DF{hi, lo - (hi - s)};
 }
 
-// Like block_reduce_finalize, but (1) the partial is published by thread `pub`, which the caller
-// keeps free of global stores so that its fence only waits for the partial itself, and (2) no
-// thread returns early: every thread gets `last` (this block finished last) and, in the last
-// block, the totals in out_sh[k] (shared; valid after the call).
-template <int NV, int BS>
-__device__ __forceinline__ bool block_reduce_ticket(double v[NV], double* __restrict__ part,
+// acc += a * b with the product split exactly (TwoProduct via FMA)
+__device__ __forceinline__ void df_fma(DF& acc, float a, float b) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  acc = df_add(acc, DF{p, e});
+}
+
+__device__ __forceinline__ void df_addf(DF& acc, float a) { acc = df_add(acc, DF{a, 0.f}); }
+
+__device__ __forceinline__ double df_value(DF a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ DF warp_sum(DF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF w{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+    v = df_add(v, w);
+  }
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double acc_value(DF a) { return df_value(a); }
+__device__ __forceinline__ double acc_value(double a) { return a; }
+
+// Per-thread accumulators matching the vector type: DF for float, double for double.
+template <class T>
+struct Acc;
+template <>
+struct Acc<float> {
+  using type = DF;
+  __device__ static DF zero() { return df_zero(); }
+  __device__ static void fma(DF& a, float x, float y) { df_fma(a, x, y); }
+  __device__ static void add(DF& a, float x) { df_addf(a, x); }
+};
+template <>
+struct Acc<double> {
+  using type = double;
+  __device__ static double zero() { return 0.0; }
+  __device__ static void fma(double& a, double x, double y) { a = ::fma(x, y, a); }
+  __device__ static void add(double& a, double x) { a += x; }
+};
+
+// Block sums of NV accumulators; the totals (double) are valid in thread 0.
+template <int NV, int BS, class A>
+__device__ __forceinline__ void block_sum(A (&v)[NV], double (&tot)[NV]) {
+  __shared__ double ws[NV][BS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const A s = warp_sum(v[k]);
+    if (lane == 0) ws[k][warp] = acc_value(s);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < BS / 32; ++w) t += ws[k][w];
+      tot[k] = t;
+    }
+}
+
+// Sum of the block accumulators over the grid: thread `pub` publishes the block's partials to
+// part[k * pstride + blockIdx.x] (the caller keeps `pub` free of other global stores so that its
+// fence is cheap), takes a ticket, and the last block adds all partials in a fixed order. No
+// thread returns early; returns true in the last block, where out_sh[k] (shared) holds the totals.
+template <int NV, int BS, class A>
+__device__ __forceinline__ bool block_reduce_ticket(A (&v)[NV], double* __restrict__ part,
                                                     int64_t pstride, unsigned* __restrict__ counter,
                                                     int pub, double (&out_sh)[NV]) {
-  __shared__ double sh[NV][BS];
+  __shared__ double tot[NV];
   __shared__ bool last;
+  double t0[NV];
+  block_sum<NV, BS>(v, t0);
+  if (threadIdx.x == 0)
 #pragma unroll
-  for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = v[k];
+    for (int k = 0; k < NV; ++k) tot[k] = t0[k];
   __syncthreads();
-  for (int w = BS / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-    __syncthreads();
-  }
   if ((int)threadIdx.x == pub) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) part[k * pstride + blockIdx.x] = sh[k][0];
+    for (int k = 0; k < NV; ++k) part[k * pstride + blockIdx.x] = tot[k];
     __threadfence();
     const unsigned t = atomicAdd(counter, 1u);
     last = (t == gridDim.x - 1);
@@ -85,23 +127,18 @@ __device__ __forceinline__ bool block_reduce_ticket(double v[NV], double* __rest
   const bool is_last = last;
   if (is_last) {
     __threadfence();
+    double s[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double s = 0.0;
+      s[k] = 0.0;
       for (unsigned b = threadIdx.x; b < gridDim.x; b += BS)
-        s += ((volatile double*)part)[k * pstride + b];
-      sh[k][threadIdx.x] = s;
+        s[k] += ((volatile double*)part)[k * pstride + b];
     }
-    __syncthreads();
-    for (int w = BS / 2; w > 0; w >>= 1) {
-      if ((int)threadIdx.x < w)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-      __syncthreads();
-    }
+    double fin[NV];
+    block_sum<NV, BS>(s, fin);
     if (threadIdx.x == 0) {
 #pragma unroll
-      for (int k = 0; k < NV; ++k) out_sh[k] = sh[k][0];
+      for (int k = 0; k < NV; ++k) out_sh[k] = fin[k];
       *counter = 0u;
     }
     __syncthreads();
@@ -109,48 +146,16 @@ __device__ __forceinline__ bool block_reduce_ticket(double v[NV], double* __rest
   return is_last;
 }
 
-// Write this block's NV sums to part[k * pstride + blockIdx.x] (no fence, no ticket): a later
-// kernel, after the launch boundary, adds the partials with block_sum_partials.
-template <int NV, int BS>
-__device__ __forceinline__ void block_write_partials(double v[NV], double* __restrict__ part,
-                                                     int64_t pstride) {
-  __shared__ double sh[NV][BS];
+// Classic form: thread 0 publishes and the last block writes the totals to out[k] (global).
+template <int NV, int BS, class A>
+__device__ __forceinline__ void block_reduce_finalize(A (&v)[NV], double* __restrict__ part,
+                                                      int64_t pstride,
+                                                      unsigned* __restrict__ counter,
+                                                      double* __restrict__ out) {
+  __shared__ double tot[NV];
+  if (block_reduce_ticket<NV, BS>(v, part, pstride, counter, 0, tot) && threadIdx.x == 0)
 #pragma unroll
-  for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = v[k];
-  __syncthreads();
-  for (int w = BS / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) part[k * pstride + blockIdx.x] = sh[k][0];
-}
-
-// Sum np partials part[k * pstride + b] (b < np) in a fixed order; every thread of the block
-// receives the totals in out[k]. The summation order depends only on np and BS.
-template <int NV, int BS>
-__device__ __forceinline__ void block_sum_partials(const double* __restrict__ part, int64_t pstride,
-                                                   int np, double out[NV]) {
-  __shared__ double sh[NV][BS];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double t = 0.0;
-    for (int b = threadIdx.x; b < np; b += BS) t += part[k * pstride + b];
-    sh[k][threadIdx.x] = t;
-  }
-  __syncthreads();
-  for (int w = BS / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-    __syncthreads();
-  }
-#pragma unroll
-  for (int k = 0; k < NV; ++k) out[k] = sh[k][0];
-  __syncthreads();
+    for (int k = 0; k < NV; ++k) out[k] = tot[k];
 }
 
 }  // namespace chns
