@@ -70,12 +70,16 @@ typedef enum {
   CHNS_OP_MOMENTUM = 3    /* velocity-prediction operator, 3 components, Dirichlet identity */
 } chns_operator;
 
-typedef enum { CHNS_KSP_CG = 0, CHNS_KSP_GMRES = 1 } chns_ksp;
+/* FCG: flexible CG (Polak-Ribiere beta = z_new.(r_new - r_old) / r_old.z_old), for a
+ * preconditioner that changes from one application to the next; POISSON only. */
+typedef enum { CHNS_KSP_CG = 0, CHNS_KSP_GMRES = 1, CHNS_KSP_FCG = 2 } chns_ksp;
 /* JACOBI: inverse of the exact diagonal; for CHNS_OP_CH the inverse of the exact 2x2 nodal
- * (phi, mu) blocks. */
-typedef enum { CHNS_PC_NONE = 0, CHNS_PC_JACOBI = 1 } chns_pc;
+ * (phi, mu) blocks. LEARNED (with CHNS_KSP_FCG on POISSON): z = D^-1 r + c(r), the Jacobi
+ * smoother plus the coarse correction c(r) of a trained network (see chns_learned below). */
+typedef enum { CHNS_PC_NONE = 0, CHNS_PC_JACOBI = 1, CHNS_PC_LEARNED = 2 } chns_pc;
 
 typedef struct chns_mesh chns_mesh;   /* opaque; owns device tables and workspace */
+typedef struct chns_learned chns_learned;  /* opaque; learned coarse correction (below) */
 
 typedef struct {
   int64_t n_elem;
@@ -198,7 +202,8 @@ typedef struct {
   int32_t inner_precision;  /* chns_precision */
   double inner_rtol;        /* FP32 modes: relative tolerance of each correction solve */
   int32_t max_refine;       /* FP32 modes: maximum refinement cycles */
-  int32_t check_every;      /* CG: iterations between host convergence checks (>= 1) */
+  int32_t check_every;      /* CG/FCG: iterations between host convergence checks (>= 1) */
+  chns_learned* learned;    /* CHNS_PC_LEARNED: the network (not owned); else ignored */
 } chns_solver_params;
 
 typedef struct {
@@ -235,6 +240,14 @@ typedef struct {
   double newton_atol;
   int32_t newton_max_it;
   int32_t blocks;           /* block iterations per step (2 in the paper) */
+  /* Training-pair collection (learned preconditioner): when `collect` is set, the right-hand
+   * side of every pressure-Poisson solve of the step is also solved by FP64 Jacobi-PCG from
+   * zero to relative residual 1e-10, and the errors x* - x_k of the iterates k = collect_every,
+   * 2 collect_every, ... (at most collect_max per solve) are added to its replay buffer (see
+   * chns_learned_add_sample). The step's own solution is not affected. */
+  chns_learned* collect;
+  int32_t collect_every;
+  int32_t collect_max;
 } chns_step_params;
 
 typedef struct {
@@ -246,6 +259,73 @@ typedef struct {
 
 chns_status chns_step(const chns_mesh* mesh, chns_state* state, const chns_params* prm,
                       const chns_step_params* sp, chns_step_stats* stats, void* stream);
+
+/* ---------------------------------------------------------------- learned preconditioner
+ * Not in the paper: a coarse correction for the pressure-Poisson solve, computed by a small
+ * 3D convolutional network on a uniform D^3 grid of cells over the domain and applied inside
+ * flexible CG together with the Jacobi smoother (CHNS_KSP_FCG + CHNS_PC_LEARNED):
+ *     z = D^-1 r + s(r) out_scale P_g net(x(r)).
+ * Grid transfer: P_g (n_nodes x D^3) interpolates cell-centred values trilinearly at the
+ *   nodes; cell (i, j, k) has its centre at ((i + 1/2)/D, (j + 1/2)/D, (k + 1/2)/D) of the box,
+ *   values beyond the outermost centres are extrapolated as constants. R = P_g^T restricts.
+ * Input x(r), 2 channels: R r / s(r) with s(r) = sqrt(r.r / D^3); and the cell mean
+ *   (P_g^T f) / (P_g^T 1) of f = log(1/rho(clamp(phi~, -1, 1))) (0 in cells no node reaches).
+ * Network (16 channels, 4 levels): enc0 = relu(conv3(x)) at D; enc_l = relu(conv3(pool(
+ *   enc_{l-1}))) at D/2^l for l = 1..3; dec_l = relu(conv3(up(dec_{l+1}) + enc_l)) for
+ *   l = 2, 1, 0 with dec_3 = enc_3; out = conv1(dec_0), one channel, linear. conv3: 3x3x3 taps,
+ *   zero padding, bias; pool: mean of 2x2x2 cells; up: copy to the 8 children. Activations and
+ *   conv weights are bfloat16 with FP32 accumulation (tensor cores); master weights, gradients
+ *   and the Adam state are FP32.
+ * Parameters: one FP32 vector, for each layer enc0, enc1, enc2, enc3, dec2, dec1, dec0 the
+ *   weights W[27][16][cin] (tap t = 9 (dz+1) + 3 (dy+1) + (dx+1), the tap reads the input at
+ *   offset (dx, dy, dz); output channel; input channel; cin = 2 for enc0, else 16) then its
+ *   bias[16]; then out.W[16] and out.b[1].
+ * Training: pairs (x(A e), cell_mean(e) / s(A e)) of error samples e; loss = mean over cells
+ *   of (out - target / out_scale)^2 / 2; Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * Grid arrays are FP32 device arrays indexed (channel, z, y, x), x fastest. The object owns its
+ * device memory (activations, gradients, replay buffer of `capacity` pairs) and may be used
+ * with any mesh. Calls are asynchronous on `stream` except those returning host values. */
+chns_status chns_learned_create(int32_t D, int32_t capacity, uint64_t seed, void* stream,
+                                chns_learned** out);  /* D: power of two, 8..256 */
+void chns_learned_destroy(chns_learned* net);
+int64_t chns_learned_num_params(const chns_learned* net);
+/* host FP32 vectors of chns_learned_num_params values; set also clears the Adam state */
+chns_status chns_learned_get_params(const chns_learned* net, float* params);
+chns_status chns_learned_set_params(chns_learned* net, const float* params);
+chns_status chns_learned_set_output_scale(chns_learned* net, double out_scale);  /* > 0 */
+double chns_learned_output_scale(const chns_learned* net);
+/* out (D^3, device) = net(x) for x (2 D^3, device); keeps the activations for backward */
+chns_status chns_learned_forward(chns_learned* net, const float* x, float* out, void* stream);
+/* grad (num_params, device FP32) of a loss whose derivative with respect to the output of the
+ * last forward is gout (D^3, device) */
+chns_status chns_learned_backward(chns_learned* net, const float* gout, float* grad,
+                                  void* stream);
+/* one Adam step with the gradient grad (device) and learning rate lr */
+chns_status chns_learned_adam(chns_learned* net, const float* grad, double lr, void* stream);
+/* x (2 D^3, device) = x(r) for a nodal residual r (FP64 device); s_host = s(r) */
+chns_status chns_learned_inputs(chns_learned* net, const chns_mesh* mesh, const chns_params* prm,
+                                const chns_coef* coef, const double* r, float* x,
+                                double* s_host, void* stream);
+/* y (n_nodes, FP64 device) = P_g grid for grid (D^3, device) */
+chns_status chns_learned_prolong(chns_learned* net, const chns_mesh* mesh, const float* grid,
+                                 double* y, void* stream);
+/* Add the training pair of the error sample e (FP64 device, n_nodes) of the Poisson operator
+ * with coefficients coef: r = A e, input x(r), target cell_mean(e) / s(r). The replay buffer is
+ * a ring: beyond `capacity` pairs the oldest is replaced. e = 0 adds nothing. */
+chns_status chns_learned_add_sample(chns_learned* net, const chns_mesh* mesh,
+                                    const chns_params* prm, const chns_coef* coef,
+                                    const double* e, void* stream);
+/* Solve A x = b by FP64 Jacobi-PCG from zero to relative residual 1e-10 and add the pairs of
+ * the iterate errors x* - x_k, k = every, 2 every, ... (at most max_samples); *added = count. */
+chns_status chns_learned_collect(chns_learned* net, const chns_mesh* mesh, const chns_params* prm,
+                                 const chns_coef* coef, const double* b, int32_t every,
+                                 int32_t max_samples, int32_t* added, void* stream);
+int32_t chns_learned_num_samples(const chns_learned* net);
+/* `iterations` Adam steps on pairs drawn from the replay buffer (sample k of step i chosen by a
+ * hash of (seed, i)); loss_host (optional, `iterations` floats) receives each step's loss. If
+ * the output scale was never set, it is first set to the RMS of the stored targets. */
+chns_status chns_learned_train(chns_learned* net, int32_t iterations, double lr, uint64_t seed,
+                               float* loss_host, void* stream);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* chns_last_error(void);

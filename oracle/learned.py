@@ -56,13 +56,52 @@ def grid_prolongation(node_int: np.ndarray, extent, D: int) -> sp.csr_matrix:
                          shape=(n, D ** 3))
 
 
-def restrict_inputs(Pg: sp.csr_matrix, r: np.ndarray, logrho_nodes: np.ndarray, D: int):
-    """The two input channels (2, D, D, D): R r and the weighted mean of log(1/rho)."""
-    rr = Pg.T @ r
+def cell_mean(Pg: sp.csr_matrix, f: np.ndarray, D: int) -> np.ndarray:
+    """P_g-weighted mean (P_g^T f) / (P_g^T 1) per cell, 0 in cells no node reaches; (D, D, D)."""
     wsum = Pg.T @ np.ones(Pg.shape[0])
-    lr = (Pg.T @ logrho_nodes) / np.maximum(wsum, 1e-300)
-    lr[wsum == 0] = 0.0
-    return np.stack([rr, lr]).reshape(2, D, D, D)
+    num = Pg.T @ f
+    out = np.zeros_like(num)
+    nz = wsum > 0
+    out[nz] = num[nz] / wsum[nz]
+    return out.reshape(D, D, D)
+
+
+def log_inv_rho(co, phi_t: np.ndarray) -> np.ndarray:
+    """log(1/rho(phi*)) at the nodes, phi* = clamp(phi~, -1, 1) (co: oracle.fem.Coeffs)."""
+    return -np.log(co.rho(phi_t))
+
+
+def input_scale(r: np.ndarray, D: int) -> float:
+    """s(r) = sqrt(r.r / D^3): the residual channel is fed as R r / s and the network's output is
+    scaled back by s, which makes the correction positively homogeneous in r."""
+    return float(np.sqrt(np.dot(r, r) / D ** 3))
+
+
+def restrict_inputs(Pg: sp.csr_matrix, r: np.ndarray, lr_cell: np.ndarray, D: int):
+    """The two input channels (2, D, D, D): R r / s(r) and the cell mean of log(1/rho); and s."""
+    s = input_scale(r, D)
+    rr = (Pg.T @ r).reshape(D, D, D)
+    return np.stack([rr / s if s > 0 else 0.0 * rr, lr_cell]), s
+
+
+def training_target(Pg: sp.csr_matrix, e: np.ndarray, s: float, D: int) -> np.ndarray:
+    """Grid target of an error sample e (residual r = A e): the cell mean of e divided by s(r)."""
+    return cell_mean(Pg, e, D) / s
+
+
+def coarse_correction(P, Pg, r, lr_cell, D, out_scale, round_act=None):
+    """c(r) = s(r) out_scale P_g net(R r / s(r), lr); zero for r = 0."""
+    x, s = restrict_inputs(Pg, r, lr_cell, D)
+    if s == 0.0:
+        return np.zeros(Pg.shape[0])
+    out, _ = forward(P, x, round_act)
+    return s * out_scale * (Pg @ out.ravel())
+
+
+def precondition(P, Pg, r, lr_cell, D, out_scale, dinv, round_act=None):
+    """Additive two-level preconditioner z = D^-1 r + c(r) (Jacobi smoother + learned coarse
+    correction), used inside flexible CG."""
+    return dinv * r + coarse_correction(P, Pg, r, lr_cell, D, out_scale, round_act)
 
 
 # ------------------------------------------------------------------ layers (arrays: (C, D, D, D) with index [c, z, y, x])
@@ -154,8 +193,11 @@ def forward(P, x, round_act=None):
     return out, cache
 
 
-def backward(P, cache, gout):
-    """Gradients of all parameters given dL/d(out) (D,D,D)."""
+def backward(P, cache, gout, round_grad=None):
+    """Gradients of all parameters given dL/d(out) (D,D,D). round_grad (optional) rounds the
+    gradient at each conv output after the ReLU mask, where a reduced-precision implementation
+    stores it as the operand of its transposed convolution and weight-gradient contraction."""
+    rg = round_grad or (lambda a: a)
     G = {}
     d0 = cache["dec0.out"]
     G["out.W"] = np.tensordot(gout[None], d0, axes=([1, 2, 3], [1, 2, 3]))
@@ -163,7 +205,7 @@ def backward(P, cache, gout):
     gd = P["out.W"][0][:, None, None, None] * gout[None]
     genc = {l: np.zeros_like(cache[f"enc{l}.out"]) for l in range(4)}
     for l in (0, 1, 2):
-        gz = gd * (cache[f"dec{l}.out"] > 0)
+        gz = rg(gd * (cache[f"dec{l}.out"] > 0))
         gin, G[f"dec{l}.W"], G[f"dec{l}.b"] = conv3_backward(cache[f"dec{l}.in"], P[f"dec{l}.W"], gz)
         genc[l] += gin                      # skip connection
         gd = up_backward(gin)               # to dec_{l+1} (= enc3 for l = 2)
@@ -171,10 +213,39 @@ def backward(P, cache, gout):
     ga = None
     for l in (3, 2, 1, 0):
         g = genc[l] + (ga if ga is not None else 0.0)
-        gz = g * (cache[f"enc{l}.out"] > 0)
+        gz = rg(g * (cache[f"enc{l}.out"] > 0))
         gin, G[f"enc{l}.W"], G[f"enc{l}.b"] = conv3_backward(cache[f"enc{l}.in"], P[f"enc{l}.W"], gz)
         ga = pool_backward(gin) if l > 0 else None
     return G
+
+
+def flatten(P) -> np.ndarray:
+    """Parameters (or gradients) as one vector: per layer of LAYERS its W then b, then out.W, out.b."""
+    keys = [k for name in LAYERS for k in (name + ".W", name + ".b")] + ["out.W", "out.b"]
+    return np.concatenate([np.asarray(P[k], dtype=np.float64).ravel() for k in keys])
+
+
+def unflatten(v: np.ndarray, C: int = 16, cin: int = 2):
+    P, o = {}, 0
+    shapes = []
+    for name in LAYERS:
+        ci = cin if name == "enc0" else C
+        shapes += [(name + ".W", (27, C, ci)), (name + ".b", (C,))]
+    shapes += [("out.W", (1, C)), ("out.b", (1,))]
+    for k, shp in shapes:
+        n = int(np.prod(shp))
+        P[k] = np.asarray(v[o:o + n], dtype=np.float64).reshape(shp).copy()
+        o += n
+    assert o == len(v)
+    return P
+
+
+def bf16_round(a) -> np.ndarray:
+    """Round to bfloat16 (nearest, ties to even), returned as float64."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 def loss_and_grad(out, target):

@@ -28,8 +28,8 @@ FP64, FP32, FP32_BF16COEF = 0, 1, 2
 OP_POISSON, OP_MASS, OP_CH, OP_MOMENTUM = 0, 1, 2, 3
 OP_NCOMP = {OP_POISSON: 1, OP_MASS: 3, OP_CH: 2, OP_MOMENTUM: 3}
 # chns_ksp / chns_pc
-KSP_CG, KSP_GMRES = 0, 1
-PC_NONE, PC_JACOBI = 0, 1
+KSP_CG, KSP_GMRES, KSP_FCG = 0, 1, 2
+PC_NONE, PC_JACOBI, PC_LEARNED = 0, 1, 2
 
 
 class ChnsError(RuntimeError):
@@ -57,7 +57,7 @@ class chns_solver_params(C.Structure):
     _fields_ = [("ksp", C.c_int32), ("pc", C.c_int32), ("rtol", C.c_double),
                 ("max_it", C.c_int32), ("restart", C.c_int32), ("inner_precision", C.c_int32),
                 ("inner_rtol", C.c_double), ("max_refine", C.c_int32),
-                ("check_every", C.c_int32)]
+                ("check_every", C.c_int32), ("learned", C.c_void_p)]
 
 
 class chns_solve_stats(C.Structure):
@@ -75,7 +75,9 @@ class chns_step_params(C.Structure):
     _fields_ = [("ch", chns_solver_params), ("vp", chns_solver_params),
                 ("pp", chns_solver_params), ("vu", chns_solver_params),
                 ("newton_rtol", C.c_double), ("newton_atol", C.c_double),
-                ("newton_max_it", C.c_int32), ("blocks", C.c_int32)]
+                ("newton_max_it", C.c_int32), ("blocks", C.c_int32),
+                ("collect", C.c_void_p), ("collect_every", C.c_int32),
+                ("collect_max", C.c_int32)]
 
 
 class chns_step_stats(C.Structure):
@@ -109,6 +111,25 @@ _SIGS = {
                            C.POINTER(chns_solver_params), C.POINTER(chns_solve_stats), _P], C.c_int),
     "chns_step": ([_P, C.POINTER(chns_state), C.POINTER(chns_params), C.POINTER(chns_step_params),
                    C.POINTER(chns_step_stats), _P], C.c_int),
+    "chns_learned_create": ([C.c_int32, C.c_int32, C.c_uint64, _P, C.POINTER(_P)], C.c_int),
+    "chns_learned_destroy": ([_P], None),
+    "chns_learned_num_params": ([_P], C.c_int64),
+    "chns_learned_get_params": ([_P, _P], C.c_int),
+    "chns_learned_set_params": ([_P, _P], C.c_int),
+    "chns_learned_set_output_scale": ([_P, C.c_double], C.c_int),
+    "chns_learned_output_scale": ([_P], C.c_double),
+    "chns_learned_forward": ([_P, _P, _P, _P], C.c_int),
+    "chns_learned_backward": ([_P, _P, _P, _P], C.c_int),
+    "chns_learned_adam": ([_P, _P, C.c_double, _P], C.c_int),
+    "chns_learned_inputs": ([_P, _P, C.POINTER(chns_params), C.POINTER(chns_coef), _P, _P,
+                             C.POINTER(C.c_double), _P], C.c_int),
+    "chns_learned_prolong": ([_P, _P, _P, _P, _P], C.c_int),
+    "chns_learned_add_sample": ([_P, _P, C.POINTER(chns_params), C.POINTER(chns_coef), _P, _P],
+                                C.c_int),
+    "chns_learned_collect": ([_P, _P, C.POINTER(chns_params), C.POINTER(chns_coef), _P,
+                              C.c_int32, C.c_int32, C.POINTER(C.c_int32), _P], C.c_int),
+    "chns_learned_num_samples": ([_P], C.c_int32),
+    "chns_learned_train": ([_P, C.c_int32, C.c_double, C.c_uint64, _P, _P], C.c_int),
     "chns_last_error": ([], C.c_char_p),
     "chns_version": ([], C.c_char_p),
     "chns_kernel_launches": ([], C.c_uint64),
@@ -179,9 +200,10 @@ def make_coef(phi=None, u=(None, None, None), mu=None) -> chns_coef:
 
 
 def make_solver(ksp=KSP_CG, pc=PC_JACOBI, rtol=1e-8, max_it=10000, restart=30,
-                inner_precision=FP64, inner_rtol=1e-3, max_refine=20, check_every=1):
+                inner_precision=FP64, inner_rtol=1e-3, max_refine=20, check_every=1,
+                learned=None):
     return chns_solver_params(ksp, pc, rtol, max_it, restart, inner_precision, inner_rtol,
-                              max_refine, check_every)
+                              max_refine, check_every, learned)
 
 
 # ------------------------------------------------------------------ mesh
@@ -302,6 +324,93 @@ def chns_step(mesh, state: chns_state, prm, step_params, stream=None) -> chns_st
         err.stats = st
         raise err
     return st
+
+
+# ------------------------------------------------------------------ learned preconditioner
+def chns_learned_create(D, capacity=0, seed=0, stream=None):
+    out = C.c_void_p()
+    _check(LIB.chns_learned_create(int(D), int(capacity), int(seed), _stream(stream),
+                                   C.byref(out)), "chns_learned_create")
+    return out.value
+
+
+def chns_learned_destroy(net):
+    LIB.chns_learned_destroy(net)
+
+
+def chns_learned_num_params(net) -> int:
+    return int(LIB.chns_learned_num_params(net))
+
+
+def chns_learned_get_params(net) -> np.ndarray:
+    out = np.zeros(chns_learned_num_params(net), dtype=np.float32)
+    _check(LIB.chns_learned_get_params(net, out.ctypes.data), "chns_learned_get_params")
+    return out
+
+
+def chns_learned_set_params(net, params):
+    v = np.ascontiguousarray(params, dtype=np.float32)
+    if v.size != chns_learned_num_params(net):
+        raise ValueError("parameter vector has the wrong length")
+    _check(LIB.chns_learned_set_params(net, v.ctypes.data), "chns_learned_set_params")
+
+
+def chns_learned_set_output_scale(net, scale):
+    _check(LIB.chns_learned_set_output_scale(net, float(scale)), "chns_learned_set_output_scale")
+
+
+def chns_learned_output_scale(net) -> float:
+    return float(LIB.chns_learned_output_scale(net))
+
+
+def chns_learned_forward(net, x, out, stream=None):
+    _check(LIB.chns_learned_forward(net, _ptr(x), _ptr(out), _stream(stream)),
+           "chns_learned_forward")
+
+
+def chns_learned_backward(net, gout, grad, stream=None):
+    _check(LIB.chns_learned_backward(net, _ptr(gout), _ptr(grad), _stream(stream)),
+           "chns_learned_backward")
+
+
+def chns_learned_adam(net, grad, lr, stream=None):
+    _check(LIB.chns_learned_adam(net, _ptr(grad), float(lr), _stream(stream)), "chns_learned_adam")
+
+
+def chns_learned_inputs(net, mesh, prm, coef, r, x, stream=None) -> float:
+    s = C.c_double()
+    _check(LIB.chns_learned_inputs(net, mesh, C.byref(prm), C.byref(coef), _ptr(r), _ptr(x),
+                                   C.byref(s), _stream(stream)), "chns_learned_inputs")
+    return s.value
+
+
+def chns_learned_prolong(net, mesh, grid, y, stream=None):
+    _check(LIB.chns_learned_prolong(net, mesh, _ptr(grid), _ptr(y), _stream(stream)),
+           "chns_learned_prolong")
+
+
+def chns_learned_add_sample(net, mesh, prm, coef, e, stream=None):
+    _check(LIB.chns_learned_add_sample(net, mesh, C.byref(prm), C.byref(coef), _ptr(e),
+                                       _stream(stream)), "chns_learned_add_sample")
+
+
+def chns_learned_collect(net, mesh, prm, coef, b, every, max_samples, stream=None) -> int:
+    added = C.c_int32()
+    _check(LIB.chns_learned_collect(net, mesh, C.byref(prm), C.byref(coef), _ptr(b), int(every),
+                                    int(max_samples), C.byref(added), _stream(stream)),
+           "chns_learned_collect")
+    return added.value
+
+
+def chns_learned_num_samples(net) -> int:
+    return int(LIB.chns_learned_num_samples(net))
+
+
+def chns_learned_train(net, iterations, lr, seed=0, stream=None) -> np.ndarray:
+    loss = np.zeros(max(int(iterations), 1), dtype=np.float32)
+    _check(LIB.chns_learned_train(net, int(iterations), float(lr), int(seed), loss.ctypes.data,
+                                  _stream(stream)), "chns_learned_train")
+    return loss[:int(iterations)]
 
 
 def chns_version() -> str:

@@ -40,13 +40,12 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(MeshDev m, DevParams p,
 //  4. hanging accumulators are distributed to their parents with the same weights;
 //  5. each regular slot is written once: a plain store when the patch owns the node, a global
 //     atomic add otherwise (nodes on the patch boundary). y must be zero on entry.
-// With PQ the block sums of the element energies x_e . A_e x_e (summing to x^T A x) are written
-// to part[blockIdx.x]; the consumer kernel adds them in a fixed order.
+// With PQ the block sums of the element energies x_e . A_e x_e (summing to x^T A x) are added to
+// S_cg[kCgPq0 + par] with an FP64 atomic.
 template <class K, class T, class S, class C, bool PQ, bool CGP>
 __global__ void __launch_bounds__(kPatchElems)
 k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S* __restrict__ y,
-              double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ S_cg,
-              const S* __restrict__ zcg, S* __restrict__ pout) {
+              double* __restrict__ S_cg, int par, const S* __restrict__ zcg, S* __restrict__ pout) {
   constexpr int NC = K::NC, NF = K::NF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* xs = reinterpret_cast<T*>(smem_raw);       // [NC][kPatchSlots]
@@ -56,18 +55,17 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
   const int s0 = m.patch_slot[pidx], ns = m.patch_slot[pidx + 1] - s0, nreg = m.patch_nreg[pidx];
   const int64_t N = m.n_nodes;
   const C* fptr[5] = {cf.phi, cf.u[0], cf.u[1], cf.u[2], cf.mu};
-  // With PQ the last thread publishes the block's partial of p.Ap: it stores nothing to global
-  // memory before that, so that its fence is cheap.
-  constexpr int kPub = kPatchElems - 1;
-  const int gstride = PQ ? kPatchElems - 1 : kPatchElems;
-  const bool gworker = !PQ || (int)threadIdx.x != kPub;
   // CG direction update fused into the gather (CGP): p_new = z + beta p_old with
   // beta = rz_cur / rz_prev; x holds p_old and p_new goes to pout (separate buffers, so that a
   // patch never reads a p value another patch has already updated)
   __shared__ T s_beta;
   if (CGP && threadIdx.x == 0) {
-    const double rzc = S_cg[kCgRzCur], rzp = S_cg[kCgRzPrev];
+    const double rzc = S_cg[kCgRz0 + par], rzp = S_cg[kCgRzPrev];
     s_beta = (T)(rzp != 0.0 ? rzc / rzp : 0.0);
+    if (blockIdx.x == 0) {  // accumulators of the update kernel that follows
+      S_cg[kCgRz0 + (par ^ 1)] = 0.0;
+      S_cg[kCgRr0 + (par ^ 1)] = 0.0;
+    }
   }
   // the element's local corner slots and level are loaded first, so that their latency overlaps
   // the gather of the patch's nodes
@@ -81,8 +79,8 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
   }
   if (CGP) __syncthreads();
   // 1. regular slots
-  if (gworker) {
-    for (int i = threadIdx.x; i < nreg; i += gstride) {
+  {
+    for (int i = threadIdx.x; i < nreg; i += kPatchElems) {
       const int32_t v = m.slot_node[s0 + i];
       const int64_t g = v & kNodeMask;
       const bool dir = K::DIR && (v & kDirBit);
@@ -159,11 +157,11 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
         atomicAdd(ys + c * kPatchSlots + sl[a], r[c][a]);
       }
   }
-  // p.Ap: published before any global store of this block's results
+  // p.Ap
   if (PQ) {
-    __shared__ double tot[1];
-    if (block_reduce_ticket<1, kPatchElems>(en, part, 0, counter, kPub, tot) && threadIdx.x == 0)
-      S_cg[kCgPq] = tot[0];
+    double tot[1];
+    block_sum<1, kPatchElems>(en, tot);
+    if (threadIdx.x == 0) atomicAdd(S_cg + kCgPq0 + par, tot[0]);
   }
   __syncthreads();
   // 4. hanging slots -> parents
@@ -209,7 +207,7 @@ constexpr size_t patch_smem() {
 template <class K, class T, class S, class C, bool PQ, bool CGP = false>
 static void launch_patch(const chns_mesh* m, const DevParams& p, const CoefArgs<C>& cf,
                          const S* x, S* y, double* S_cg, cudaStream_t s, const S* z = nullptr,
-                         S* pout = nullptr) {
+                         S* pout = nullptr, int par = 0) {
   constexpr size_t smem = patch_smem<K, T>();
   static bool configured = false;  // per instantiation
   if (!configured) {
@@ -219,7 +217,7 @@ static void launch_patch(const chns_mesh* m, const DevParams& p, const CoefArgs<
   }
   note_launch();
   k_apply_patch<K, T, S, C, PQ, CGP><<<(unsigned)m->d.n_patch, kPatchElems, smem, s>>>(
-      m->d, p, cf, x, y, m->ws.part_big, m->ws.counter + 1, S_cg, z, pout);
+      m->d, p, cf, x, y, S_cg, par, z, pout);
 }
 
 // Reference (corner a, slot k) -> node reference with Dirichlet bit and its weight, or -1.
@@ -481,7 +479,7 @@ chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm
 
 chns_status apply_poisson_cg(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
                              const void* z, const void* p_old, void* p_new, void* y,
-                             chns_precision prec, double* S_cg, cudaStream_t s) {
+                             chns_precision prec, double* S_cg, int par, cudaStream_t s) {
   chns_status st = check_coef(CHNS_OP_POISSON, coef);
   if (st != CHNS_OK) return st;
   const DevParams p = make_dev_params(*prm);
@@ -490,17 +488,18 @@ chns_status apply_poisson_cg(const chns_mesh* m, const chns_params* prm, const c
       launch_patch<PoissonK<double, double>, double, double, double, true, true>(
           m, p, coef_args<double>(coef), static_cast<const double*>(p_old),
           static_cast<double*>(y), S_cg, s, static_cast<const double*>(z),
-          static_cast<double*>(p_new));
+          static_cast<double*>(p_new), par);
       break;
     case CHNS_FP32:
       launch_patch<PoissonK<float, float>, float, float, float, true, true>(
           m, p, coef_args<float>(coef), static_cast<const float*>(p_old), static_cast<float*>(y),
-          S_cg, s, static_cast<const float*>(z), static_cast<float*>(p_new));
+          S_cg, s, static_cast<const float*>(z), static_cast<float*>(p_new), par);
       break;
     case CHNS_FP32_BF16COEF:
       launch_patch<PoissonK<float, __nv_bfloat16>, float, float, __nv_bfloat16, true, true>(
           m, p, coef_args<__nv_bfloat16>(coef), static_cast<const float*>(p_old),
-          static_cast<float*>(y), S_cg, s, static_cast<const float*>(z), static_cast<float*>(p_new));
+          static_cast<float*>(y), S_cg, s, static_cast<const float*>(z), static_cast<float*>(p_new),
+          par);
       break;
     default:
       set_error("apply: bad precision");

@@ -66,6 +66,27 @@ struct Workspace {
   double* part_big = nullptr;  // per-block partials of element-level reductions (n_elem/64+64)
 };
 
+// ---- learned preconditioner (learned.cu)
+// density channel of the input for the coefficients of this solve
+chns_status learned_begin_solve(chns_learned* L, const chns_mesh* m, const chns_params* prm,
+                                const chns_coef* coef64, cudaStream_t s);
+// z = (dinv ? dinv r : 0) + s(r) out_scale P_g net(x(r)), with r.r read from rr_dev (device);
+// asynchronous, no allocation or host synchronisation (capturable in a CUDA graph)
+template <class T>
+chns_status learned_precondition(chns_learned* L, const chns_mesh* m, const T* r, const T* dinv,
+                                 const double* rr_dev, T* z, cudaStream_t s);
+chns_status learned_add_sample(chns_learned* L, const chns_mesh* m, const chns_params* prm,
+                               const chns_coef* coef, const double* e, cudaStream_t s);
+chns_status learned_collect(chns_learned* L, const chns_mesh* m, const chns_params* prm,
+                            const chns_coef* coef, const double* b, int every, int max_samples,
+                            int* added, cudaStream_t s);
+// FP64 Jacobi-PCG of the Poisson operator from x = 0 to ||r|| <= rtol ||b|| (b mean-projected),
+// copying the iterates k = every, 2 every, ... (at most max_snaps) to snaps [max_snaps][n_nodes]
+// (krylov.cu); x is returned mean-free
+chns_status pcg_snapshots(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
+                          const double* b, double rtol, int every, int max_snaps, double* snaps,
+                          int* n_snaps, double* x, cudaStream_t s);
+
 }  // namespace chns
 
 struct chns_mesh {
@@ -87,6 +108,7 @@ struct chns_mesh {
   ushort4* d_slot_par = nullptr;
   uint4* d_eloc = nullptr;
   chns::LevelGeo* d_geo = nullptr;
+  uint32_t* d_node_int = nullptr;    // node coordinates (3*n_nodes, units 2^-CHNS_MAXD)
   int64_t n_slots = 0;
   chns::Workspace ws;
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture CUDA graphs
@@ -131,14 +153,22 @@ constexpr int kScalarBase = 3 * 4096;  // scalars stored after three partial arr
 chns_status apply_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
                      const chns_coef* coef, const void* x, void* y, chns_precision prec,
                      cudaStream_t s);
-// Slots of the CG scalars (offsets from the scalar area of ws.red).
-constexpr int kCgRzCur = 0, kCgRzPrev = 1, kCgPq = 2, kCgRr = 3;
-// One fused CG step of the Poisson operator: p_new = z + beta p_old (beta = S[rz_cur]/S[rz_prev])
-// during the gather, y = A p_new (y zero on entry), and S[pq] = p_new.A p_new (deterministic
-// last-block sum).
+// Slots of the CG scalars (offsets from the scalar area of ws.red). Iteration k (parity
+// par = k & 1) reads r.z of its iterate from kCgRz0 + par and that of the previous one from
+// kCgRzPrev, accumulates p.Ap into kCgPq0 + par, and accumulates the next r.z and r.r into
+// kCgRz0 + (par ^ 1) and kCgRr0 + (par ^ 1). Block partials are added with FP64 atomics into
+// slots that the previous kernel of the iteration cleared (a kernel boundary orders them), so no
+// kernel waits for the last block of its grid.
+constexpr int kCgRz0 = 32, kCgRzPrev = 34, kCgPq0 = 35, kCgRr0 = 37;
+// flexible CG: r.z and alpha of the current iteration
+constexpr int kFcgRz = 4, kFcgAlpha = 5;
+// One fused CG step of the Poisson operator (iteration parity par): p_new = z + beta p_old with
+// beta = S[kCgRz0 + par] / S[kCgRzPrev] during the gather, y = A p_new (y zero on entry), and
+// S[kCgPq0 + par] += p_new.A p_new (cleared by the caller); clears S[kCgRz0 + (par ^ 1)] and
+// S[kCgRr0 + (par ^ 1)] for the update kernel that follows.
 chns_status apply_poisson_cg(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
                              const void* z, const void* p_old, void* p_new, void* y,
-                             chns_precision prec, double* S_cg, cudaStream_t s);
+                             chns_precision prec, double* S_cg, int par, cudaStream_t s);
 chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
                     const chns_coef* coef, void* d, chns_precision prec, cudaStream_t s);
 // 2x2 nodal blocks of the CH Jacobian, d4 = [d_pp, d_pm, d_mp, d_mm] x n_nodes (FP64 or FP32)
@@ -182,5 +212,26 @@ chns_status rhs_vu(const chns_mesh* m, const chns_params* prm, const chns_coef* 
 chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params* prm,
                          const chns_coef* coef, const double* b, double* x,
                          const chns_solver_params* sp, chns_solve_stats* stats, cudaStream_t s);
+
+// ---- learned preconditioner (learned.cu)
+// density channel of the input for the coefficients of this solve
+chns_status learned_begin_solve(chns_learned* L, const chns_mesh* m, const chns_params* prm,
+                                const chns_coef* coef64, cudaStream_t s);
+// z = (dinv ? dinv r : 0) + s(r) out_scale P_g net(x(r)), with r.r read from rr_dev (device);
+// asynchronous, no allocation or host synchronisation (capturable in a CUDA graph)
+template <class T>
+chns_status learned_precondition(chns_learned* L, const chns_mesh* m, const T* r, const T* dinv,
+                                 const double* rr_dev, T* z, cudaStream_t s);
+chns_status learned_add_sample(chns_learned* L, const chns_mesh* m, const chns_params* prm,
+                               const chns_coef* coef, const double* e, cudaStream_t s);
+chns_status learned_collect(chns_learned* L, const chns_mesh* m, const chns_params* prm,
+                            const chns_coef* coef, const double* b, int every, int max_samples,
+                            int* added, cudaStream_t s);
+// FP64 Jacobi-PCG of the Poisson operator from x = 0 to ||r|| <= rtol ||b|| (b mean-projected),
+// copying the iterates k = every, 2 every, ... (at most max_snaps) to snaps [max_snaps][n_nodes]
+// (krylov.cu); x is returned mean-free
+chns_status pcg_snapshots(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
+                          const double* b, double rtol, int every, int max_snaps, double* snaps,
+                          int* n_snaps, double* x, cudaStream_t s);
 
 }  // namespace chns

@@ -138,60 +138,128 @@ __global__ void k_mul_b2(const T* __restrict__ inv, const T* __restrict__ v, T* 
   }
 }
 
-// ---- CG kernels. Scalars live in device memory: S[kCgRzCur], S[kCgRzPrev], S[kCgPq], S[kCgRr].
-// k_cg_update: alpha = rz_cur / pq (one division per block); x += alpha p; r -= alpha q;
-// z = dinv r (q cleared when zero_q); r.z and r.r are reduced with the last thread of each block as
-// publisher (it stores nothing else, so its fence is cheap); the last block rotates
-// rz_prev <- rz_cur <- r.z and stores r.r.
+// ---- CG kernels. Scalars live in device memory at the parity slots of internal.h; iteration k
+// has parity par = k & 1.
+// alpha of the update: FP32 vectors divide in FP32 in every thread (no barrier before the loads);
+// FP64 vectors let thread 0 divide once per block.
+template <class T>
+__device__ __forceinline__ T cg_ratio(const double* S, int num, int den, bool positive) {
+  if (sizeof(T) == sizeof(float)) {
+    const float nf = (float)S[num], df = (float)S[den];
+    return (positive ? df > 0.f : df != 0.f) && isfinite(df) ? (T)(nf / df) : T(0);
+  }
+  __shared__ double s_v;
+  if (threadIdx.x == 0) {
+    const double nd = S[num], dd = S[den];
+    s_v = (positive ? dd > 0.0 : dd != 0.0) && isfinite(dd) ? nd / dd : 0.0;
+  }
+  __syncthreads();
+  return (T)s_v;
+}
+
+// k_cg_update: alpha = r.z / p.Ap; x += alpha p; r -= alpha q; z = dinv r (q cleared when
+// zero_q); the block sums of r.z and r.r are added to the next parity's slots; block 0 keeps
+// r.z as the previous value and clears the next p.Ap accumulator.
 template <class T>
 __global__ void __launch_bounds__(kVecThreads)
 k_cg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __restrict__ p,
             T* __restrict__ q, const T* __restrict__ dinv, int64_t n, double* __restrict__ S,
-            bool zero_q, double* __restrict__ part, unsigned* __restrict__ counter) {
-  constexpr int kPub = kVecThreads - 1;
-  __shared__ T s_alpha;
-  if (threadIdx.x == 0) {
-    const double rz = S[kCgRzCur], pq = S[kCgPq];
-    s_alpha = (T)((pq > 0.0 && isfinite(pq)) ? rz / pq : 0.0);
-  }
-  __syncthreads();
-  const T a = s_alpha;
+            bool zero_q, int par) {
+  const T a = cg_ratio<T>(S, kCgRz0 + par, kCgPq0 + par, true);
   typename Acc<T>::type v0 = Acc<T>::zero(), v1 = Acc<T>::zero();
-  if ((int)threadIdx.x != kPub) {
-    const int64_t stride = (int64_t)gridDim.x * (kVecThreads - 1);
-    for (int64_t i = blockIdx.x * (int64_t)(kVecThreads - 1) + threadIdx.x; i < n; i += stride) {
-      x[i] += a * p[i];
-      const T ri = r[i] - a * q[i];
-      if (zero_q) q[i] = T(0);
-      r[i] = ri;
-      const T zi = dinv ? dinv[i] * ri : ri;
-      z[i] = zi;
-      Acc<T>::fma(v0, ri, zi);
-      Acc<T>::fma(v1, ri, ri);
-    }
+  GRID_LOOP(i, n) {
+    x[i] += a * p[i];
+    const T ri = r[i] - a * q[i];
+    if (zero_q) q[i] = T(0);
+    r[i] = ri;
+    const T zi = dinv ? dinv[i] * ri : ri;
+    z[i] = zi;
+    Acc<T>::fma(v0, ri, zi);
+    Acc<T>::fma(v1, ri, ri);
   }
   typename Acc<T>::type v[2] = {v0, v1};
-  __shared__ double tot[2];
-  if (block_reduce_ticket<2, kVecThreads>(v, part, kRedSlots, counter, kPub, tot) &&
-      threadIdx.x == 0) {
-    S[kCgRzPrev] = S[kCgRzCur];
-    S[kCgRzCur] = tot[0];
-    S[kCgRr] = tot[1];
+  double tot[2];
+  block_sum<2, kVecThreads>(v, tot);
+  if (threadIdx.x == 0) {
+    atomicAdd(S + kCgRz0 + (par ^ 1), tot[0]);
+    atomicAdd(S + kCgRr0 + (par ^ 1), tot[1]);
+    if (blockIdx.x == 0) {
+      S[kCgRzPrev] = S[kCgRz0 + par];
+      S[kCgPq0 + (par ^ 1)] = 0.0;
+    }
   }
 }
 
-// p_new = z + beta p_old with beta = rz_cur / rz_prev (operators whose apply does not fuse it)
+// p_new = z + beta p_old with beta = r.z / r.z_prev (operators whose apply does not fuse it);
+// clears the accumulators of the update that follows
 template <class T>
 __global__ void k_cg_pupdate(const T* __restrict__ z, const T* __restrict__ p_old,
-                             T* __restrict__ p_new, int64_t n, const double* __restrict__ S) {
-  __shared__ T s_beta;
-  if (threadIdx.x == 0) {
-    const double rzc = S[kCgRzCur], rzp = S[kCgRzPrev];
-    s_beta = (T)(rzp != 0.0 ? rzc / rzp : 0.0);
+                             T* __restrict__ p_new, int64_t n, double* __restrict__ S, int par) {
+  const T b = cg_ratio<T>(S, kCgRz0 + par, kCgRzPrev, false);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S[kCgRz0 + (par ^ 1)] = 0.0;
+    S[kCgRr0 + (par ^ 1)] = 0.0;
   }
-  __syncthreads();
-  const T b = s_beta;
   GRID_LOOP(i, n) p_new[i] = z[i] + b * p_old[i];
+}
+
+// ---- flexible CG (Polak-Ribiere beta). S[kFcgRz] = r.z, S[kFcgAlpha] = alpha. The fused Poisson
+// apply forms p = z + beta p_old with beta = S[kCgRz0 + par] / S[kCgRzPrev], so the dot kernel
+// stores beta's numerator -alpha z_new.q (= z_new.(r_new - r_old)) and denominator r.z there.
+// k_fcg_update: alpha = r.z / p.q; x += alpha p; r -= alpha q; r.r added to the next parity slot
+template <class T>
+__global__ void __launch_bounds__(kVecThreads)
+k_fcg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+             const T* __restrict__ q, int64_t n, double* __restrict__ S, int par) {
+  const T a = cg_ratio<T>(S, kFcgRz, kCgPq0 + par, true);
+  typename Acc<T>::type v0 = Acc<T>::zero();
+  GRID_LOOP(i, n) {
+    x[i] += a * p[i];
+    const T ri = r[i] - a * q[i];
+    r[i] = ri;
+    Acc<T>::fma(v0, ri, ri);
+  }
+  typename Acc<T>::type v[1] = {v0};
+  double tot[1];
+  block_sum<1, kVecThreads>(v, tot);
+  if (threadIdx.x == 0) {
+    atomicAdd(S + kCgRr0 + (par ^ 1), tot[0]);
+    if (blockIdx.x == 0) {
+      S[kFcgAlpha] = (double)a;
+      S[kCgPq0 + (par ^ 1)] = 0.0;
+    }
+  }
+}
+
+// z.q and z.r; q cleared for the next apply. The last block (ticket) stores
+// S[kCgRz0 + (par ^ 1)] = -alpha z.q, S[kCgRzPrev] = r.z (old) and S[kFcgRz] = z.r (new).
+template <class T>
+__global__ void __launch_bounds__(kVecThreads)
+k_fcg_dots(const T* __restrict__ z, T* __restrict__ q, const T* __restrict__ r, int64_t n,
+           double* __restrict__ S, double* __restrict__ part, unsigned* __restrict__ counter,
+           int par) {
+  typename Acc<T>::type v0 = Acc<T>::zero(), v1 = Acc<T>::zero();
+  GRID_LOOP(i, n) {
+    const T zi = z[i];
+    Acc<T>::fma(v0, zi, q[i]);
+    q[i] = T(0);
+    Acc<T>::fma(v1, zi, r[i]);
+  }
+  typename Acc<T>::type v[2] = {v0, v1};
+  __shared__ double tot[2];
+  if (block_reduce_ticket<2, kVecThreads>(v, part, kRedSlots, counter, 0, tot) &&
+      threadIdx.x == 0) {
+    S[kCgRz0 + (par ^ 1)] = -S[kFcgAlpha] * tot[0];
+    S[kCgRzPrev] = S[kFcgRz];
+    S[kFcgRz] = tot[1];
+  }
+}
+
+// first FCG direction: p = z (beta = 0 / 1); p.Ap accumulator cleared
+__global__ void k_fcg_init(double* S) {
+  S[kCgRz0] = 0.0;
+  S[kCgRzPrev] = 1.0;
+  S[kCgPq0] = 0.0;
 }
 
 // ---- GMRES
@@ -429,72 +497,56 @@ chns_status project_mean(const Ctx& c, T* v) {
   return CHNS_OK;
 }
 
-// One CG iteration with direction buffers p_old -> p_new. Poisson: two kernels (the apply fuses
-// p_new = z + beta p_old into its gather and returns p.Ap; the update clears q for the next
-// apply). Other operators: p update, apply, dot, update.
+// One CG iteration (parity par) with direction buffers p_old -> p_new. Poisson: two kernels (the
+// apply fuses p_new = z + beta p_old into its gather and accumulates p.Ap; the update clears q for
+// the next apply). Other operators: p update, apply, dot, update.
 template <class T>
 chns_status cg_iteration(const Ctx& c, cudaStream_t s, T* x, T* r, T* z, const T* p_old,
-                         T* p_new, T* q, const T* dinv) {
+                         T* p_new, T* q, const T* dinv, int par) {
   const int64_t n = c.n;
   const unsigned rg = red_grid(c.m, n), vg = vgrid(c.m, n);
   const bool fused = c.op == CHNS_OP_POISSON;
   chns_status st;
   if (fused) {
     if (sizeof(T) == sizeof(double))
-      st = apply_poisson_cg(c.m, c.prm, c.coef64, z, p_old, p_new, q, CHNS_FP64, c.S, s);
+      st = apply_poisson_cg(c.m, c.prm, c.coef64, z, p_old, p_new, q, CHNS_FP64, c.S, par, s);
     else
-      st = apply_poisson_cg(c.m, c.prm, &c.coefR, z, p_old, p_new, q, c.inner, c.S, s);
+      st = apply_poisson_cg(c.m, c.prm, &c.coefR, z, p_old, p_new, q, c.inner, c.S, par, s);
     if (st != CHNS_OK) return st;
   } else {
     note_launch();
-    k_cg_pupdate<T><<<vg, kVecThreads, 0, s>>>(z, p_old, p_new, n, c.S);
+    k_cg_pupdate<T><<<vg, kVecThreads, 0, s>>>(z, p_old, p_new, n, c.S, par);
     Ctx cs = c;
     cs.s = s;
     st = apply_T<T>(cs, p_new, q);
     if (st != CHNS_OK) return st;
     note_launch();
     k_dot<T, T><<<rg, kVecThreads, 0, s>>>(p_new, q, n, c.m->ws.red, c.m->ws.counter,
-                                            c.S + kCgPq);
+                                            c.S + kCgPq0 + par);
   }
   note_launch();
-  k_cg_update<T><<<rg, kVecThreads, 0, s>>>(x, r, z, p_new, q, dinv, n, c.S, fused, c.m->ws.red,
-                                            c.m->ws.counter);
+  k_cg_update<T><<<rg, kVecThreads, 0, s>>>(x, r, z, p_new, q, dinv, n, c.S, fused, par);
   return CHNS_OK;
 }
 
-// Preconditioned CG on A x = b (type T); x holds the initial guess. Runs until sqrt(r.r) <= tol_abs
-// or max_it iterations. With chunk >= 2 the iterations run as CUDA graphs of `chunk` iterations
-// (captured once per solve on a private stream); two graph instances write r.r into alternating
-// pinned host slots so the host checks chunk k while chunk k+1 already runs. The solve may do up
-// to two chunks beyond the iteration that reached the tolerance; they only reduce the residual.
-template <class T>
-chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, int max_it,
-                int chunk, T* r, T* z, T* p, T* q, T* p2, int* iters, double* rnorm) {
-  T* pb[2] = {p, p2};  // direction buffers: iteration k reads pb[k & 1], writes pb[(k & 1) ^ 1]
-  const int64_t n = c.n;
-  const unsigned rg = red_grid(c.m, n), vg = vgrid(c.m, n);
-  chns_status st = apply_T<T>(c, x, q);
-  if (st != CHNS_OK) return st;
-  note_launch();
-  k_axpby<T><<<vg, kVecThreads, 0, c.s>>>(1.0, b, -1.0, q, r, n);
-  if (c.op == CHNS_OP_POISSON) project_mean<T>(c, r);
-  note_launch();
-  k_mul<T><<<vg, kVecThreads, 0, c.s>>>(dinv, r, z, n);
-  // p_old = 0 and rz_prev = rz_cur make the first direction p = z
-  CHNS_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), c.s));
-  CHNS_CUDA(cudaMemsetAsync(q, 0, n * sizeof(T), c.s));
-  note_launch();
-  k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, z, n, c.m->ws.red, c.m->ws.counter,
-                                          c.S + kCgRzCur);
-  CHNS_CUDA(cudaMemcpyAsync(c.S + kCgRzPrev, c.S + kCgRzCur, sizeof(double),
-                            cudaMemcpyDeviceToDevice, c.s));
-  note_launch();
-  k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, r, n, c.m->ws.red, c.m->ws.counter, c.S + kCgRr);
-  CHNS_CUDA(cudaGetLastError());
+// Copies of the iterate every `every` iterations (FP64 CG only; collection of training pairs).
+struct Snap {
+  double* buf;  // [max][n]
+  int every, max;
+  int* count;
+};
+
+// Runs step(stream, it) — one iteration, which leaves r.r in S[kCgRr0 + ((it & 1) ^ 1)] — until
+// sqrt(r.r) <= tol_abs or max_it iterations; rr is r.r before the first iteration. With chunk >= 2 the iterations run
+// as CUDA graphs of `chunk` iterations (captured once per solve on a private stream); two graph
+// instances write r.r into alternating pinned host slots so the host checks chunk k while chunk
+// k+1 already runs. The solve may do up to two chunks beyond the iteration that reached the
+// tolerance; they only reduce the residual. Iteration parities are preserved (chunks are even).
+template <class T, class Step>
+chns_status iterate(const Ctx& c, Step&& step, T* x, double tol_abs, int max_it, int chunk,
+                    double rr, int* iters, double* rnorm, const Snap* snap) {
   int it = 0;
-  double rr = 0.0;
-  st = read_dev(c.m, c.S + kCgRr, &rr, 1, c.s);
-  if (st != CHNS_OK) return st;
+  chns_status st = CHNS_OK;
   auto bad = [&](double v) {
     if (std::isfinite(v)) return false;
     set_error("krylov: NaN/Inf in the residual norm");
@@ -505,12 +557,17 @@ chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, i
     *rnorm = rr;
     return CHNS_ENAN;
   }
-  if (chunk < 2) {
+  if (chunk < 2 || snap) {
     while (std::sqrt(rr) > tol_abs && it < max_it) {
-      st = cg_iteration<T>(c, c.s, x, r, z, pb[it & 1], pb[(it & 1) ^ 1], q, dinv);
+      st = step(c.s, it);
       if (st != CHNS_OK) return st;
       ++it;
-      st = read_dev(c.m, c.S + kCgRr, &rr, 1, c.s);
+      if (snap && it % snap->every == 0 && *snap->count < snap->max) {
+        CHNS_CUDA(cudaMemcpyAsync(snap->buf + (int64_t)(*snap->count) * c.n, x, c.n * sizeof(T),
+                                  cudaMemcpyDeviceToDevice, c.s));
+        ++*snap->count;
+      }
+      st = read_dev(c.m, c.S + kCgRr0 + (it & 1), &rr, 1, c.s);  // written by iteration it - 1
       if (st != CHNS_OK) return st;
       if (bad(rr)) {
         *iters = it;
@@ -530,9 +587,9 @@ chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, i
       cudaGraph_t g = nullptr;
       CHNS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
       const unsigned long long l0 = chns_launches_now();
-      for (int i = 0; i < chunk && rc == CHNS_OK; ++i)
-        rc = cg_iteration<T>(c, cs, x, r, z, pb[i & 1], pb[(i & 1) ^ 1], q, dinv);
-      cudaMemcpyAsync((void*)(slot + v), c.S + kCgRr, sizeof(double), cudaMemcpyDeviceToHost, cs);
+      for (int i = 0; i < chunk && rc == CHNS_OK; ++i) rc = step(cs, i);
+      // an even chunk ends with an odd iteration, which leaves r.r in slot 0
+      cudaMemcpyAsync((void*)(slot + v), c.S + kCgRr0, sizeof(double), cudaMemcpyDeviceToHost, cs);
       per_graph = chns_launches_now() - l0;
       cudaError_t e1 = cudaStreamEndCapture(cs, &g);
       if (rc != CHNS_OK) {
@@ -563,9 +620,7 @@ chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, i
         }
         if (done || it >= max_it) {
           CHNS_CUDA(cudaEventSynchronize(ev[v]));
-          const double last = slot[v];
-          if (!bad(last)) rr = last;
-          else rr = last;
+          rr = slot[v];
           done = true;
         }
         ++k;
@@ -587,6 +642,98 @@ chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, i
   *iters = it;
   *rnorm = std::sqrt(rr);
   return std::sqrt(rr) <= tol_abs ? CHNS_OK : CHNS_ENOTCONV;
+}
+
+// Preconditioned CG on A x = b (type T); x holds the initial guess. Runs until sqrt(r.r) <= tol_abs
+// or max_it iterations (see iterate).
+template <class T>
+chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, int max_it,
+                int chunk, T* r, T* z, T* p, T* q, T* p2, int* iters, double* rnorm,
+                const Snap* snap = nullptr) {
+  T* pb[2] = {p, p2};  // direction buffers: iteration k reads pb[k & 1], writes pb[(k & 1) ^ 1]
+  const int64_t n = c.n;
+  const unsigned rg = red_grid(c.m, n), vg = vgrid(c.m, n);
+  chns_status st = apply_T<T>(c, x, q);
+  if (st != CHNS_OK) return st;
+  note_launch();
+  k_axpby<T><<<vg, kVecThreads, 0, c.s>>>(1.0, b, -1.0, q, r, n);
+  if (c.op == CHNS_OP_POISSON) project_mean<T>(c, r);
+  note_launch();
+  k_mul<T><<<vg, kVecThreads, 0, c.s>>>(dinv, r, z, n);
+  // p_old = 0 and rz_prev = rz_cur make the first direction p = z
+  CHNS_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), c.s));
+  CHNS_CUDA(cudaMemsetAsync(q, 0, n * sizeof(T), c.s));
+  note_launch();
+  k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, z, n, c.m->ws.red, c.m->ws.counter, c.S + kCgRz0);
+  CHNS_CUDA(cudaMemcpyAsync(c.S + kCgRzPrev, c.S + kCgRz0, sizeof(double),
+                            cudaMemcpyDeviceToDevice, c.s));
+  CHNS_CUDA(cudaMemsetAsync(c.S + kCgPq0, 0, sizeof(double), c.s));
+  note_launch();
+  k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, r, n, c.m->ws.red, c.m->ws.counter, c.S + kCgRr0);
+  CHNS_CUDA(cudaGetLastError());
+  double rr = 0.0;
+  st = read_dev(c.m, c.S + kCgRr0, &rr, 1, c.s);
+  if (st != CHNS_OK) return st;
+  auto step = [&](cudaStream_t s, int it) {
+    return cg_iteration<T>(c, s, x, r, z, pb[it & 1], pb[(it & 1) ^ 1], q, dinv, it & 1);
+  };
+  return iterate<T>(c, step, x, tol_abs, max_it, chunk, rr, iters, rnorm, snap);
+}
+
+// Flexible CG on the Poisson operator with the preconditioner z = M(r): the learned correction
+// plus Jacobi when L is given, else Jacobi (dinv) or the identity.
+template <class T>
+chns_status fcg(const Ctx& c, const T* b, T* x, const T* dinv, chns_learned* L, double tol_abs,
+                int max_it, int chunk, T* r, T* z, T* p, T* q, T* p2, int* iters, double* rnorm) {
+  T* pb[2] = {p, p2};
+  const int64_t n = c.n;
+  const unsigned rg = red_grid(c.m, n), vg = vgrid(c.m, n);
+  // rr_slot: where r.r of the current residual is
+  auto precond = [&](cudaStream_t s, int rr_slot) -> chns_status {
+    if (L) return learned_precondition<T>(L, c.m, r, dinv, c.S + rr_slot, z, s);
+    note_launch();
+    if (dinv) k_mul<T><<<vg, kVecThreads, 0, s>>>(dinv, r, z, n);
+    else k_axpby<T><<<vg, kVecThreads, 0, s>>>(1.0, r, 0.0, r, z, n);
+    return CHNS_OK;
+  };
+  chns_status st = apply_T<T>(c, x, q);
+  if (st != CHNS_OK) return st;
+  note_launch();
+  k_axpby<T><<<vg, kVecThreads, 0, c.s>>>(1.0, b, -1.0, q, r, n);
+  project_mean<T>(c, r);
+  note_launch();
+  k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, r, n, c.m->ws.red, c.m->ws.counter, c.S + kCgRr0);
+  st = precond(c.s, kCgRr0);
+  if (st != CHNS_OK) return st;
+  note_launch();
+  k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, z, n, c.m->ws.red, c.m->ws.counter, c.S + kFcgRz);
+  note_launch();
+  k_fcg_init<<<1, 1, 0, c.s>>>(c.S);
+  CHNS_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), c.s));
+  CHNS_CUDA(cudaMemsetAsync(q, 0, n * sizeof(T), c.s));
+  CHNS_CUDA(cudaGetLastError());
+  double rr = 0.0;
+  st = read_dev(c.m, c.S + kCgRr0, &rr, 1, c.s);
+  if (st != CHNS_OK) return st;
+  auto step = [&](cudaStream_t s, int it) -> chns_status {
+    const int par = it & 1;
+    T* p_old = pb[par];
+    T* p_new = pb[par ^ 1];
+    chns_status e;
+    if (sizeof(T) == sizeof(double))
+      e = apply_poisson_cg(c.m, c.prm, c.coef64, z, p_old, p_new, q, CHNS_FP64, c.S, par, s);
+    else
+      e = apply_poisson_cg(c.m, c.prm, &c.coefR, z, p_old, p_new, q, c.inner, c.S, par, s);
+    if (e != CHNS_OK) return e;
+    note_launch();
+    k_fcg_update<T><<<rg, kVecThreads, 0, s>>>(x, r, p_new, q, n, c.S, par);
+    e = precond(s, kCgRr0 + (par ^ 1));
+    if (e != CHNS_OK) return e;
+    note_launch();
+    k_fcg_dots<T><<<rg, kVecThreads, 0, s>>>(z, q, r, n, c.S, c.m->ws.red, c.m->ws.counter, par);
+    return CHNS_OK;
+  };
+  return iterate<T>(c, step, x, tol_abs, max_it, chunk, rr, iters, rnorm, nullptr);
 }
 
 // Right-preconditioned restarted GMRES with classical Gram-Schmidt and one re-orthogonalisation
@@ -758,8 +905,14 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
                          const chns_solver_params* sp, chns_solve_stats* stats, cudaStream_t s) {
   CHNS_CHECK(m && prm && coef && b_in && x && sp, CHNS_EINVAL, "chns_krylov_solve: null argument");
   CHNS_CHECK(op >= CHNS_OP_POISSON && op <= CHNS_OP_MOMENTUM, CHNS_EINVAL, "bad operator");
-  CHNS_CHECK(sp->ksp == CHNS_KSP_CG || sp->ksp == CHNS_KSP_GMRES, CHNS_EINVAL, "bad ksp");
-  CHNS_CHECK(sp->pc == CHNS_PC_NONE || sp->pc == CHNS_PC_JACOBI, CHNS_EINVAL, "bad preconditioner");
+  CHNS_CHECK(sp->ksp == CHNS_KSP_CG || sp->ksp == CHNS_KSP_GMRES || sp->ksp == CHNS_KSP_FCG,
+             CHNS_EINVAL, "bad ksp");
+  CHNS_CHECK(sp->pc == CHNS_PC_NONE || sp->pc == CHNS_PC_JACOBI || sp->pc == CHNS_PC_LEARNED,
+             CHNS_EINVAL, "bad preconditioner");
+  CHNS_CHECK(sp->ksp != CHNS_KSP_FCG || op == CHNS_OP_POISSON, CHNS_EINVAL,
+             "FCG is implemented for the Poisson operator only");
+  CHNS_CHECK(sp->pc != CHNS_PC_LEARNED || (sp->ksp == CHNS_KSP_FCG && sp->learned), CHNS_EINVAL,
+             "the learned preconditioner needs FCG and solver_params.learned");
   CHNS_CHECK(sp->rtol > 0.0 && sp->max_it >= 0, CHNS_EINVAL, "bad tolerance / max_it");
   CHNS_CHECK(sp->ksp != CHNS_KSP_GMRES ||
                  (sp->restart >= 1 && sp->restart <= CHNS_GMRES_MAX_RESTART),
@@ -808,7 +961,13 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
     // Jacobi preconditioner: the operator's exact diagonal (2x2 nodal blocks for the CH pair,
     // whose phi and mu unknowns are strongly coupled), computed in the precision of the Krylov
     // iteration that uses it.
-    const bool jac = sp->pc == CHNS_PC_JACOBI;
+    // the learned preconditioner is additive with the Jacobi smoother
+    const bool jac = sp->pc == CHNS_PC_JACOBI || sp->pc == CHNS_PC_LEARNED;
+    chns_learned* L = sp->pc == CHNS_PC_LEARNED ? sp->learned : nullptr;
+    if (L) {
+      st = learned_begin_solve(L, m, prm, coef, s);
+      if (st != CHNS_OK) return st;
+    }
     const bool block2 = (op == CHNS_OP_CH && jac);
     const int64_t Nn = m->d.n_nodes;
     const double* dinv64 = nullptr;
@@ -839,6 +998,9 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
       double rn = 0.0;
       if (sp->ksp == CHNS_KSP_CG)
         st = pcg<double>(c, b, x, dinv64, tol, sp->max_it, sp->check_every, r64, ws.v64[3],
+                         ws.v64[4], ws.v64[5], ws.v64[6], &its, &rn);
+      else if (sp->ksp == CHNS_KSP_FCG)
+        st = fcg<double>(c, b, x, dinv64, L, tol, sp->max_it, sp->check_every, r64, ws.v64[3],
                          ws.v64[4], ws.v64[5], ws.v64[6], &its, &rn);
       else
         st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it, sp->restart, ws.gm_V,
@@ -919,6 +1081,9 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
             if (sp->ksp == CHNS_KSP_CG)
               st = pcg<double>(c, b, x, dinv64, tol, sp->max_it - total, sp->check_every, r64,
                                ws.v64[3], ws.v64[4], ws.v64[5], ws.v64[6], &its, &frn);
+            else if (sp->ksp == CHNS_KSP_FCG)
+              st = fcg<double>(c, b, x, dinv64, L, tol, sp->max_it - total, sp->check_every,
+                               r64, ws.v64[3], ws.v64[4], ws.v64[5], ws.v64[6], &its, &frn);
             else
               st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it - total, sp->restart, ws.gm_V,
                                  ws.v64[7], &its, &frn);
@@ -943,6 +1108,9 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
         chns_status ist;
         if (sp->ksp == CHNS_KSP_CG)
           ist = pcg<float>(c, r32, d32, dinv32, itol, budget, sp->check_every, ws.v32[3],
+                           ws.v32[4], ws.v32[5], ws.v32[6], ws.v32[8], &its, &irn);
+        else if (sp->ksp == CHNS_KSP_FCG)
+          ist = fcg<float>(c, r32, d32, dinv32, L, itol, budget, sp->check_every, ws.v32[3],
                            ws.v32[4], ws.v32[5], ws.v32[6], ws.v32[8], &its, &irn);
         else
           ist = gmres<float>(c, r32, d32, dinv32, block2, itol, budget, sp->restart, ws.gm_V32,
@@ -985,6 +1153,45 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
   if (stats) *stats = out;
   if (st == CHNS_ENOTCONV) set_error("krylov: iteration limit reached before the tolerance");
   return st;
+}
+
+chns_status pcg_snapshots(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
+                          const double* b_in, double rtol, int every, int max_snaps, double* snaps,
+                          int* n_snaps, double* x, cudaStream_t s) {
+  CHNS_CHECK(every >= 1 && max_snaps >= 0, CHNS_EINVAL, "pcg_snapshots: bad sampling");
+  const Workspace& ws = m->ws;
+  const int64_t n = m->d.n_nodes;
+  Ctx c{};
+  c.m = m;
+  c.op = CHNS_OP_POISSON;
+  c.prm = prm;
+  c.coef64 = coef;
+  c.inner = CHNS_FP64;
+  c.s = s;
+  c.n = n;
+  c.S = scal(m);
+  double* b = ws.v64[0];
+  double* d = ws.v64[2];
+  CHNS_CUDA(cudaMemcpyAsync(b, b_in, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  chns_status st = project_mean<double>(c, b);
+  if (st != CHNS_OK) return st;
+  double bn2 = 0.0;
+  st = dot_to_host<double>(c, b, b, &bn2);
+  if (st != CHNS_OK) return st;
+  *n_snaps = 0;
+  CHNS_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  if (bn2 == 0.0) return CHNS_OK;
+  st = diag_op(m, CHNS_OP_POISSON, prm, coef, d, CHNS_FP64, s);
+  if (st != CHNS_OK) return st;
+  note_launch();
+  k_invert<double, double><<<vgrid(m, n), kVecThreads, 0, s>>>(d, d, n);
+  Snap sn{snaps, every, max_snaps, n_snaps};
+  int its = 0;
+  double rn = 0.0;
+  st = pcg<double>(c, b, x, d, rtol * std::sqrt(bn2), 100000, 1, ws.v64[1], ws.v64[3], ws.v64[4],
+                   ws.v64[5], ws.v64[6], &its, &rn, &sn);
+  if (st != CHNS_OK) return st;
+  return project_mean<double>(c, x);
 }
 
 }  // namespace chns

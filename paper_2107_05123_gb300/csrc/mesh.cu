@@ -151,6 +151,7 @@ static void free_mesh(chns_mesh* m) {
   dfree(m->d_slot_par);
   dfree(m->d_eloc);
   dfree(m->d_geo);
+  dfree(m->d_node_int);
   Workspace& w = m->ws;
   for (auto p : w.v64) dfree(p);
   for (auto p : w.v32) dfree(p);
@@ -518,6 +519,10 @@ static chns_status build(const uint32_t* anchors, const uint8_t* levels, int64_t
     CHNS_CUDA(cudaMemcpy(m->d_geo, geo.data(), CHNS_MAXD * sizeof(LevelGeo), cudaMemcpyHostToDevice));
     m->d.geo = m->d_geo;
   }
+  // node coordinates on the device (grid transfer of the learned preconditioner)
+  CHNS_CUDA(cudaMalloc(&m->d_node_int, std::max<size_t>(m->node_coords.size(), 3) * sizeof(uint32_t)));
+  CHNS_CUDA(cudaMemcpy(m->d_node_int, m->node_coords.data(),
+                       m->node_coords.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
   m->d.enode = m->d_enode;
   m->d.level = m->d_level;
   m->d.hang = m->d_hang;

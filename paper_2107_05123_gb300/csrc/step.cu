@@ -164,6 +164,13 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
       if (rc != CHNS_OK) STEP_FAIL("pressure Poisson", rc);
       S.ms_pp += t.stop();
     }
+    // ---- training pairs for the learned preconditioner (not part of the method)
+    if (sp->collect) {
+      int added = 0;
+      rc = learned_collect(sp->collect, m, prm, &cv, bv, std::max(1, sp->collect_every),
+                           std::max(0, sp->collect_max), &added, s);
+      if (rc != CHNS_OK) return rc;
+    }
     // ---- velocity update
     {
       Timer t(s);

@@ -78,3 +78,85 @@ def test_grid_transfer(D):
     r = np.random.default_rng(0).standard_normal(m.n_nodes)
     g = np.random.default_rng(1).standard_normal(D ** 3)
     assert np.isclose((Pg.T @ r) @ g, r @ (Pg @ g))
+
+
+def test_bf16_round_matches_library_conversion():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    a = np.concatenate([rng.standard_normal(1000) * 10.0 ** rng.integers(-8, 8, 1000),
+                        [1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(1.0 + 2.0 ** -8), 0.0, 65504.0]])
+    ref = torch.as_tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(L.bf16_round(a), ref)
+    # ties go to the even neighbour
+    assert L.bf16_round(1.0 + 2.0 ** -8) == 1.0 and L.bf16_round(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+
+
+def test_flatten_roundtrip():
+    P = L.init_params(C=16, seed=2)
+    v = L.flatten(P)
+    assert len(v) == 27 * 16 * 2 + 16 + 6 * (27 * 256 + 16) + 17
+    Q = L.unflatten(v)
+    assert all(np.array_equal(P[k], Q[k]) for k in P)
+
+
+def _mesh_and_grid(D=8):
+    a, l = configs.random_balanced(3, 1, 4, 0.3)
+    m = Mesh(a, l)
+    return m, L.grid_prolongation(m.node_int, m.extent, D)
+
+
+def test_constant_network_gives_scaled_constant_correction():
+    """All conv weights and biases zero, out.b = c: out = c everywhere, so the correction is
+    s(r) * out_scale * c at every node (P_g has unit row sums)."""
+    D = 8
+    m, Pg = _mesh_and_grid(D)
+    P = L.init_params(C=4, seed=0)
+    for k in P:
+        P[k] = np.zeros_like(P[k])
+    P["out.b"] = np.array([0.7])
+    r = np.random.default_rng(0).standard_normal(m.n_nodes)
+    lr = np.zeros((D, D, D))
+    c = L.coarse_correction(P, Pg, r, lr, D, 3.0)
+    s = np.sqrt(r @ r / D ** 3)
+    assert np.allclose(c, s * 3.0 * 0.7, rtol=1e-13)
+
+
+def test_correction_is_positively_homogeneous_and_zero_net_gives_jacobi():
+    D = 8
+    m, Pg = _mesh_and_grid(D)
+    P, _, _ = _net(D=D, C=4, seed=4)
+    rng = np.random.default_rng(1)
+    r = rng.standard_normal(m.n_nodes)
+    lr = rng.standard_normal((D, D, D))
+    c1 = L.coarse_correction(P, Pg, r, lr, D, 2.0)
+    c2 = L.coarse_correction(P, Pg, 3.5 * r, lr, D, 2.0)
+    assert np.allclose(c2, 3.5 * c1, rtol=1e-12, atol=0)
+    assert np.array_equal(L.coarse_correction(P, Pg, 0 * r, lr, D, 2.0), np.zeros(m.n_nodes))
+    Z = {k: np.zeros_like(v) for k, v in P.items()}
+    dinv = rng.uniform(0.5, 2.0, m.n_nodes)
+    assert np.allclose(L.precondition(Z, Pg, r, lr, D, 2.0, dinv), dinv * r, rtol=0, atol=0)
+
+
+def test_training_target_of_constant_error():
+    D = 8
+    m, Pg = _mesh_and_grid(D)
+    t = L.training_target(Pg, np.full(m.n_nodes, 2.5), 0.5, D)
+    reached = (Pg.T @ np.ones(m.n_nodes)).reshape(D, D, D) > 0
+    assert np.allclose(t[reached], 5.0) and np.all(t[~reached] == 0)
+
+
+def test_fcg_with_fixed_preconditioner_equals_pcg():
+    """With a fixed SPD preconditioner the Polak-Ribiere beta equals Fletcher-Reeves (r_new is
+    M-orthogonal to r_old), so flexible CG reproduces Jacobi-PCG."""
+    from oracle import fem, solvers
+    a, l = configs.random_balanced(2, 1, 4, 0.3)
+    m = Mesh(a, l)
+    co = fem.Coeffs(dict(Re=1, We=1, Cn=0.1, Pe=1, Fr=1, rho_ratio=10.0, eta_ratio=1.0, dt=1.0,
+                         C_I=6.0))
+    phi = np.tanh(3 * np.random.default_rng(0).standard_normal(m.n_nodes))
+    A = fem.poisson(fem.Elem(m), co, phi) + 1e-3 * fem.mass(fem.Elem(m), np.ones((m.n_elem, 8)))
+    b = np.random.default_rng(1).standard_normal(m.n_nodes)
+    dinv = 1.0 / A.diagonal()
+    x1, it1, _ = solvers.pcg(A, b, rtol=1e-10)
+    x2, it2, _ = L.fcg(A, b, lambda r: dinv * r, rtol=1e-10)
+    assert abs(it1 - it2) <= 1 and np.allclose(x1, x2, rtol=0, atol=1e-8 * np.abs(x1).max())
