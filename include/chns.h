@@ -74,8 +74,9 @@ typedef enum {
  * preconditioner that changes from one application to the next; POISSON only. */
 typedef enum { CHNS_KSP_CG = 0, CHNS_KSP_GMRES = 1, CHNS_KSP_FCG = 2 } chns_ksp;
 /* JACOBI: inverse of the exact diagonal; for CHNS_OP_CH the inverse of the exact 2x2 nodal
- * (phi, mu) blocks. LEARNED (with CHNS_KSP_FCG on POISSON): z = D^-1 r + c(r), the Jacobi
- * smoother plus the coarse correction c(r) of a trained network (see chns_learned below). */
+ * (phi, mu) blocks. LEARNED (with CHNS_KSP_FCG on POISSON): the coarse correction c(r) of a
+ * trained network (see chns_learned below) followed by one damped Jacobi step on what it
+ * leaves, z = c + omega D^-1 (r - A c) with omega = 2/3. */
 typedef enum { CHNS_PC_NONE = 0, CHNS_PC_JACOBI = 1, CHNS_PC_LEARNED = 2 } chns_pc;
 
 typedef struct chns_mesh chns_mesh;   /* opaque; owns device tables and workspace */
@@ -215,6 +216,9 @@ typedef struct {
   float ms;                 /* device time of the solve (CUDA events) */
   int32_t escalations;      /* refinement cycles that raised the inner precision */
   int32_t final_precision;  /* chns_precision of the last inner iterations */
+  int32_t fallbacks;        /* CHNS_PC_LEARNED: 1 if the learned correction stalled (the residual
+                               norm did not halve in 100 iterations) and the solve continued with
+                               the Jacobi preconditioner alone, else 0 */
 } chns_solve_stats;
 
 chns_status chns_krylov_solve(const chns_mesh* mesh, chns_operator op, const chns_params* prm,
@@ -241,13 +245,14 @@ typedef struct {
   int32_t newton_max_it;
   int32_t blocks;           /* block iterations per step (2 in the paper) */
   /* Training-pair collection (learned preconditioner): when `collect` is set, the right-hand
-   * side of every pressure-Poisson solve of the step is also solved by FP64 Jacobi-PCG from
-   * zero to relative residual 1e-10, and the errors x* - x_k of the iterates k = collect_every,
-   * 2 collect_every, ... (at most collect_max per solve) are added to its replay buffer (see
-   * chns_learned_add_sample). The step's own solution is not affected. */
+   * side of every pressure-Poisson solve of the step is also solved as chns_learned_collect
+   * does (FP64 from zero to relative residual 1e-10), and the errors x* - x_k of the iterates
+   * k = collect_every, 2 collect_every, ... (at most collect_max per solve) are added to its
+   * replay buffer. The step's own solution is not affected. */
   chns_learned* collect;
   int32_t collect_every;
   int32_t collect_max;
+  int32_t collect_with_net;  /* iterates of FCG with the network instead of Jacobi-PCG */
 } chns_step_params;
 
 typedef struct {
@@ -263,8 +268,8 @@ chns_status chns_step(const chns_mesh* mesh, chns_state* state, const chns_param
 /* ---------------------------------------------------------------- learned preconditioner
  * Not in the paper: a coarse correction for the pressure-Poisson solve, computed by a small
  * 3D convolutional network on a uniform D^3 grid of cells over the domain and applied inside
- * flexible CG together with the Jacobi smoother (CHNS_KSP_FCG + CHNS_PC_LEARNED):
- *     z = D^-1 r + s(r) out_scale P_g net(x(r)).
+ * flexible CG, followed by one damped Jacobi step (CHNS_KSP_FCG + CHNS_PC_LEARNED):
+ *     c(r) = s(r) out_scale P_g net(x(r)),   z = c + omega D^-1 (r - A c).
  * Grid transfer: P_g (n_nodes x D^3) interpolates cell-centred values trilinearly at the
  *   nodes; cell (i, j, k) has its centre at ((i + 1/2)/D, (j + 1/2)/D, (k + 1/2)/D) of the box,
  *   values beyond the outermost centres are extrapolated as constants. R = P_g^T restricts.
@@ -280,13 +285,16 @@ chns_status chns_step(const chns_mesh* mesh, chns_state* state, const chns_param
  *   weights W[27][16][cin] (tap t = 9 (dz+1) + 3 (dy+1) + (dx+1), the tap reads the input at
  *   offset (dx, dy, dz); output channel; input channel; cin = 2 for enc0, else 16) then its
  *   bias[16]; then out.W[16] and out.b[1].
- * Training: pairs (x(A e), cell_mean(e) / s(A e)) of error samples e; loss = mean over cells
- *   of (out - target / out_scale)^2 / 2; Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * Training: on pairs (x(r), e) of mean-free error samples e with r = A e, the relative energy
+ *   norm of the error the correction leaves, loss = (e - c(r))^T A (e - c(r)) / (e^T A e), with
+ *   A applied in FP32 with bfloat16 coefficients; Adam (beta1 0.9, beta2 0.999, eps 1e-8).
  * Grid arrays are FP32 device arrays indexed (channel, z, y, x), x fastest. The object owns its
  * device memory (activations, gradients, replay buffer of `capacity` pairs) and may be used
  * with any mesh. Calls are asynchronous on `stream` except those returning host values. */
+/* D: power of two, 8..256. Initial parameters: He-normal conv weights drawn from `seed`, zero
+ * biases, zero output layer (the untrained correction is c = 0). */
 chns_status chns_learned_create(int32_t D, int32_t capacity, uint64_t seed, void* stream,
-                                chns_learned** out);  /* D: power of two, 8..256 */
+                                chns_learned** out);
 void chns_learned_destroy(chns_learned* net);
 int64_t chns_learned_num_params(const chns_learned* net);
 /* host FP32 vectors of chns_learned_num_params values; set also clears the Adam state */
@@ -310,22 +318,31 @@ chns_status chns_learned_inputs(chns_learned* net, const chns_mesh* mesh, const 
 chns_status chns_learned_prolong(chns_learned* net, const chns_mesh* mesh, const float* grid,
                                  double* y, void* stream);
 /* Add the training pair of the error sample e (FP64 device, n_nodes) of the Poisson operator
- * with coefficients coef: r = A e, input x(r), target cell_mean(e) / s(r). The replay buffer is
- * a ring: beyond `capacity` pairs the oldest is replaced. e = 0 adds nothing. */
+ * with coefficients coef: e is first projected to nodal mean zero (constants are the operator's
+ * null space), then r = A e; the pair keeps x(r), e (FP32), 1 + phi~ (bfloat16), s(r), e^T A e
+ * and the grid target cell_mean(e) / s(r) (its RMS sets the default output scale). The replay
+ * buffer is a ring: beyond `capacity` pairs the oldest is replaced. Its nodal part is sized by
+ * the first mesh; pairs of another mesh are rejected (CHNS_EINVAL). A sample with r = 0 adds
+ * nothing. */
 chns_status chns_learned_add_sample(chns_learned* net, const chns_mesh* mesh,
                                     const chns_params* prm, const chns_coef* coef,
                                     const double* e, void* stream);
-/* Solve A x = b by FP64 Jacobi-PCG from zero to relative residual 1e-10 and add the pairs of
- * the iterate errors x* - x_k, k = every, 2 every, ... (at most max_samples); *added = count. */
+/* Solve A x = b in FP64 from zero to relative residual 1e-10 and add the pairs of the iterate
+ * errors x* - x_k, k = every, 2 every, ... (at most max_samples); *added = count. The iterates
+ * are those of Jacobi-PCG, or with with_net != 0 those of FCG with the network's own correction
+ * (the residuals the trained preconditioner meets; if it stalls, Jacobi-PCG finishes x*). */
 chns_status chns_learned_collect(chns_learned* net, const chns_mesh* mesh, const chns_params* prm,
                                  const chns_coef* coef, const double* b, int32_t every,
-                                 int32_t max_samples, int32_t* added, void* stream);
+                                 int32_t max_samples, int32_t with_net, int32_t* added,
+                                 void* stream);
 int32_t chns_learned_num_samples(const chns_learned* net);
 /* `iterations` Adam steps on pairs drawn from the replay buffer (sample k of step i chosen by a
- * hash of (seed, i)); loss_host (optional, `iterations` floats) receives each step's loss. If
- * the output scale was never set, it is first set to the RMS of the stored targets. */
-chns_status chns_learned_train(chns_learned* net, int32_t iterations, double lr, uint64_t seed,
-                               float* loss_host, void* stream);
+ * hash of (seed, i)); mesh and prm are those of the pairs (the Poisson operator of the loss);
+ * loss_host (optional, `iterations` floats) receives each step's loss. If the output scale was
+ * never set, it is first set to the RMS of the stored grid targets. */
+chns_status chns_learned_train(chns_learned* net, const chns_mesh* mesh, const chns_params* prm,
+                               int32_t iterations, double lr, uint64_t seed, float* loss_host,
+                               void* stream);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* chns_last_error(void);

@@ -5,22 +5,32 @@ TEST INFRASTRUCTURE ONLY (see the package header).
 Not in the paper: the learned coarse correction for the pressure-Poisson solve (a16 of the build's
 scope) restricts the nodal residual to a uniform grid of D^3 cells (D = 64 on the workloads),
 adds a second channel log(1/rho~) there, applies a convolutional network and prolongates its
-output back to the nodes.
+output back to the nodes; flexible CG uses z = c(r) + omega D^-1 (r - A c(r)), omega = 2/3.
 
 * Grid transfer. P_g (nodes x cells) interpolates cell-centred values trilinearly to the node
   positions (constant extrapolation beyond the outermost cell centres). The residual channel is
-  R r = P_g^T r (the adjoint: residuals are integrals against test functions); the density
-  channel is the P_g-weighted mean (P_g^T f) / (P_g^T 1) of f = log(1/rho(clamp(phi~))).
+  R r / s(r) with R = P_g^T (the adjoint: residuals are integrals against test functions) and
+  s(r) = sqrt(r.r / D^3); the density channel is the P_g-weighted mean (P_g^T f) / (P_g^T 1) of
+  f = log(1/rho(clamp(phi~))). The correction is c(r) = s(r) out_scale P_g net(x(r)).
 * Network (4 levels, C channels, C = 16): enc0 = relu(conv3(x)) at D; enc_l = relu(conv3(pool(
   enc_{l-1}))) at D/2^l for l = 1..3; dec_l = relu(conv3(up(dec_{l+1}) + enc_l)) for l = 2..0 with
   dec_3 = enc_3; out = conv1(dec_0) (linear, one channel). conv3: 3x3x3, zero padding, bias;
-  pool: 2x2x2 mean; up: nearest-neighbour copy. Activations are (C, D, D, D) arrays.
-* Training: loss = mean((out - target)^2) / 2; Adam.
+  pool: 2x2x2 mean; up: nearest-neighbour copy. Activations are (C, D, D, D) arrays. forward and
+  backward take optional rounding functions (bf16_round) applied where a bfloat16 implementation
+  stores a tensor: every activation, and every gradient after a ReLU mask.
+* Training pairs of a mean-free error sample e: input x(A e); loss = the relative energy norm
+  (e - c)^T A (e - c) / e^T A e of the error the correction leaves; Adam. The grid target
+  cell_mean(e) / s(A e) only sets the default output scale (its RMS).
 
 Pins (tests/test_oracle_learned.py): hand backward = central finite differences; a delta
 kernel reproduces its input; pool/up adjointness; P_g partition of unity and exact interpolation
-of trilinear-in-cell-centre fields; R = P_g^T. The network's values are otherwise only defined by
-this code: parity unpinned beyond these checks.
+of trilinear-in-cell-centre fields; R = P_g^T; bf16_round = the library's bfloat16 conversion
+(ties to even); a constant network gives the closed-form correction s out_scale c; the
+correction is positively homogeneous and zero for r = 0, and a zero network leaves Jacobi;
+constant errors give zero targets (null space); the energy-loss gradient = central finite
+differences of the energy loss, and a zero network gives loss 1; flexible CG with a fixed
+preconditioner equals Jacobi-PCG. The network's values are otherwise only defined by this code: parity unpinned beyond
+these checks.
 """
 from __future__ import annotations
 
@@ -85,8 +95,9 @@ def restrict_inputs(Pg: sp.csr_matrix, r: np.ndarray, lr_cell: np.ndarray, D: in
 
 
 def training_target(Pg: sp.csr_matrix, e: np.ndarray, s: float, D: int) -> np.ndarray:
-    """Grid target of an error sample e (residual r = A e): the cell mean of e divided by s(r)."""
-    return cell_mean(Pg, e, D) / s
+    """Grid target of an error sample e (residual r = A e): the cell mean of the mean-free e
+    (constants are the pure-Neumann operator's null space) divided by s(r)."""
+    return cell_mean(Pg, e - np.mean(e), D) / s
 
 
 def coarse_correction(P, Pg, r, lr_cell, D, out_scale, round_act=None):
@@ -98,10 +109,11 @@ def coarse_correction(P, Pg, r, lr_cell, D, out_scale, round_act=None):
     return s * out_scale * (Pg @ out.ravel())
 
 
-def precondition(P, Pg, r, lr_cell, D, out_scale, dinv, round_act=None):
-    """Additive two-level preconditioner z = D^-1 r + c(r) (Jacobi smoother + learned coarse
-    correction), used inside flexible CG."""
-    return dinv * r + coarse_correction(P, Pg, r, lr_cell, D, out_scale, round_act)
+def precondition(P, Pg, A, r, lr_cell, D, out_scale, dinv, omega=2.0 / 3.0, round_act=None):
+    """Two-level preconditioner used inside flexible CG: the learned coarse correction c(r), then
+    one damped Jacobi step on the residual it leaves, z = c + omega D^-1 (r - A c)."""
+    c = coarse_correction(P, Pg, r, lr_cell, D, out_scale, round_act)
+    return c + omega * dinv * (r - A @ c)
 
 
 # ------------------------------------------------------------------ layers (arrays: (C, D, D, D) with index [c, z, y, x])
@@ -217,6 +229,20 @@ def backward(P, cache, gout, round_grad=None):
         gin, G[f"enc{l}.W"], G[f"enc{l}.b"] = conv3_backward(cache[f"enc{l}.in"], P[f"enc{l}.W"], gz)
         ga = pool_backward(gin) if l > 0 else None
     return G
+
+
+def energy_loss_and_grad(P, Pg, A, e, x, s, D, out_scale, round_act=None):
+    """Training loss of one pair: the relative energy norm of the error the correction leaves,
+    c = s out_scale P_g out(x), d = e - c, loss = d^T A d / e^T A e (e mean-free, A symmetric),
+    and dL/d(out) = -2 s out_scale P_g^T A d / e^T A e. Returns (loss, gout (D,D,D), cache)."""
+    out, cache = forward(P, x, round_act)
+    c = s * out_scale * (Pg @ out.ravel())
+    d = e - c
+    Ad = A @ d
+    eae = float(e @ (A @ e))
+    loss = float(d @ Ad) / eae
+    gout = (-2.0 * s * out_scale / eae) * (Pg.T @ Ad)
+    return loss, gout.reshape(D, D, D), cache
 
 
 def flatten(P) -> np.ndarray:

@@ -63,7 +63,8 @@ class chns_solver_params(C.Structure):
 class chns_solve_stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("refinements", C.c_int32),
                 ("rel_residual", C.c_double), ("b_norm", C.c_double), ("status", C.c_int32),
-                ("ms", C.c_float), ("escalations", C.c_int32), ("final_precision", C.c_int32)]
+                ("ms", C.c_float), ("escalations", C.c_int32), ("final_precision", C.c_int32),
+                ("fallbacks", C.c_int32)]
 
 
 class chns_state(C.Structure):
@@ -77,7 +78,7 @@ class chns_step_params(C.Structure):
                 ("newton_rtol", C.c_double), ("newton_atol", C.c_double),
                 ("newton_max_it", C.c_int32), ("blocks", C.c_int32),
                 ("collect", C.c_void_p), ("collect_every", C.c_int32),
-                ("collect_max", C.c_int32)]
+                ("collect_max", C.c_int32), ("collect_with_net", C.c_int32)]
 
 
 class chns_step_stats(C.Structure):
@@ -127,9 +128,10 @@ _SIGS = {
     "chns_learned_add_sample": ([_P, _P, C.POINTER(chns_params), C.POINTER(chns_coef), _P, _P],
                                 C.c_int),
     "chns_learned_collect": ([_P, _P, C.POINTER(chns_params), C.POINTER(chns_coef), _P,
-                              C.c_int32, C.c_int32, C.POINTER(C.c_int32), _P], C.c_int),
+                              C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32), _P], C.c_int),
     "chns_learned_num_samples": ([_P], C.c_int32),
-    "chns_learned_train": ([_P, C.c_int32, C.c_double, C.c_uint64, _P, _P], C.c_int),
+    "chns_learned_train": ([_P, _P, C.POINTER(chns_params), C.c_int32, C.c_double, C.c_uint64, _P,
+                            _P], C.c_int),
     "chns_last_error": ([], C.c_char_p),
     "chns_version": ([], C.c_char_p),
     "chns_kernel_launches": ([], C.c_uint64),
@@ -394,11 +396,12 @@ def chns_learned_add_sample(net, mesh, prm, coef, e, stream=None):
                                        _stream(stream)), "chns_learned_add_sample")
 
 
-def chns_learned_collect(net, mesh, prm, coef, b, every, max_samples, stream=None) -> int:
+def chns_learned_collect(net, mesh, prm, coef, b, every, max_samples, with_net=False,
+                         stream=None) -> int:
     added = C.c_int32()
     _check(LIB.chns_learned_collect(net, mesh, C.byref(prm), C.byref(coef), _ptr(b), int(every),
-                                    int(max_samples), C.byref(added), _stream(stream)),
-           "chns_learned_collect")
+                                    int(max_samples), int(bool(with_net)), C.byref(added),
+                                    _stream(stream)), "chns_learned_collect")
     return added.value
 
 
@@ -406,10 +409,10 @@ def chns_learned_num_samples(net) -> int:
     return int(LIB.chns_learned_num_samples(net))
 
 
-def chns_learned_train(net, iterations, lr, seed=0, stream=None) -> np.ndarray:
+def chns_learned_train(net, mesh, prm, iterations, lr, seed=0, stream=None) -> np.ndarray:
     loss = np.zeros(max(int(iterations), 1), dtype=np.float32)
-    _check(LIB.chns_learned_train(net, int(iterations), float(lr), int(seed), loss.ctypes.data,
-                                  _stream(stream)), "chns_learned_train")
+    _check(LIB.chns_learned_train(net, mesh, C.byref(prm), int(iterations), float(lr), int(seed),
+                                  loss.ctypes.data, _stream(stream)), "chns_learned_train")
     return loss[:int(iterations)]
 
 

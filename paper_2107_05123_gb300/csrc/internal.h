@@ -66,27 +66,6 @@ struct Workspace {
   double* part_big = nullptr;  // per-block partials of element-level reductions (n_elem/64+64)
 };
 
-// ---- learned preconditioner (learned.cu)
-// density channel of the input for the coefficients of this solve
-chns_status learned_begin_solve(chns_learned* L, const chns_mesh* m, const chns_params* prm,
-                                const chns_coef* coef64, cudaStream_t s);
-// z = (dinv ? dinv r : 0) + s(r) out_scale P_g net(x(r)), with r.r read from rr_dev (device);
-// asynchronous, no allocation or host synchronisation (capturable in a CUDA graph)
-template <class T>
-chns_status learned_precondition(chns_learned* L, const chns_mesh* m, const T* r, const T* dinv,
-                                 const double* rr_dev, T* z, cudaStream_t s);
-chns_status learned_add_sample(chns_learned* L, const chns_mesh* m, const chns_params* prm,
-                               const chns_coef* coef, const double* e, cudaStream_t s);
-chns_status learned_collect(chns_learned* L, const chns_mesh* m, const chns_params* prm,
-                            const chns_coef* coef, const double* b, int every, int max_samples,
-                            int* added, cudaStream_t s);
-// FP64 Jacobi-PCG of the Poisson operator from x = 0 to ||r|| <= rtol ||b|| (b mean-projected),
-// copying the iterates k = every, 2 every, ... (at most max_snaps) to snaps [max_snaps][n_nodes]
-// (krylov.cu); x is returned mean-free
-chns_status pcg_snapshots(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
-                          const double* b, double rtol, int every, int max_snaps, double* snaps,
-                          int* n_snaps, double* x, cudaStream_t s);
-
 }  // namespace chns
 
 struct chns_mesh {
@@ -226,12 +205,13 @@ chns_status learned_add_sample(chns_learned* L, const chns_mesh* m, const chns_p
                                const chns_coef* coef, const double* e, cudaStream_t s);
 chns_status learned_collect(chns_learned* L, const chns_mesh* m, const chns_params* prm,
                             const chns_coef* coef, const double* b, int every, int max_samples,
-                            int* added, cudaStream_t s);
+                            bool with_net, int* added, cudaStream_t s);
 // FP64 Jacobi-PCG of the Poisson operator from x = 0 to ||r|| <= rtol ||b|| (b mean-projected),
 // copying the iterates k = every, 2 every, ... (at most max_snaps) to snaps [max_snaps][n_nodes]
-// (krylov.cu); x is returned mean-free
+// (krylov.cu); x is returned mean-free. With L the iterates are those of FCG with the network's
+// correction (Jacobi-PCG finishes the solve if it stalls).
 chns_status pcg_snapshots(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
                           const double* b, double rtol, int every, int max_snaps, double* snaps,
-                          int* n_snaps, double* x, cudaStream_t s);
+                          int* n_snaps, double* x, cudaStream_t s, chns_learned* L = nullptr);
 
 }  // namespace chns

@@ -255,6 +255,13 @@ k_fcg_dots(const T* __restrict__ z, T* __restrict__ q, const T* __restrict__ r, 
   }
 }
 
+// z += omega dinv (r - w)  (w = A z)
+template <class T>
+__global__ void k_smooth(T* __restrict__ z, const T* __restrict__ r, const T* __restrict__ w,
+                         const T* __restrict__ dinv, T omega, int64_t n) {
+  GRID_LOOP(i, n) z[i] += omega * dinv[i] * (r[i] - w[i]);
+}
+
 // first FCG direction: p = z (beta = 0 / 1); p.Ap accumulator cleared
 __global__ void k_fcg_init(double* S) {
   S[kCgRz0] = 0.0;
@@ -458,6 +465,12 @@ chns_status sum_host(const chns_mesh* m, const double* a, int64_t n, double* out
 // ------------------------------------------------------------------ solvers
 namespace {
 
+// FCG with the learned correction stops when the residual norm has not halved in this many
+// iterations; the solve then continues with the Jacobi preconditioner alone.
+constexpr int kLearnedStall = 100;
+// damping of the Jacobi step that follows the learned correction
+constexpr double kLearnedOmega = 2.0 / 3.0;
+
 struct Ctx {
   const chns_mesh* m;
   chns_operator op;
@@ -542,10 +555,23 @@ struct Snap {
 // instances write r.r into alternating pinned host slots so the host checks chunk k while chunk
 // k+1 already runs. The solve may do up to two chunks beyond the iteration that reached the
 // tolerance; they only reduce the residual. Iteration parities are preserved (chunks are even).
+// With stall > 0 the iteration also stops (status CHNS_ENOTCONV) when the residual norm has not
+// halved over the last `stall` iterations (checked at the host checks).
 template <class T, class Step>
 chns_status iterate(const Ctx& c, Step&& step, T* x, double tol_abs, int max_it, int chunk,
-                    double rr, int* iters, double* rnorm, const Snap* snap) {
+                    double rr, int* iters, double* rnorm, const Snap* snap, int stall = 0) {
   int it = 0;
+  int ref_it = 0;
+  double ref_rr = rr;
+  auto stalled = [&](int now, double v) {
+    if (stall <= 0) return false;
+    if (v <= 0.25 * ref_rr) {
+      ref_rr = v;
+      ref_it = now;
+      return false;
+    }
+    return now - ref_it >= stall;
+  };
   chns_status st = CHNS_OK;
   auto bad = [&](double v) {
     if (std::isfinite(v)) return false;
@@ -574,6 +600,7 @@ chns_status iterate(const Ctx& c, Step&& step, T* x, double tol_abs, int max_it,
         *rnorm = rr;
         return CHNS_ENAN;
       }
+      if (stalled(it, rr)) break;
     }
   } else if (std::sqrt(rr) > tol_abs && max_it > 0) {
     chunk += chunk & 1;  // even: every chunk starts at parity 0
@@ -616,7 +643,7 @@ chns_status iterate(const Ctx& c, Step&& step, T* x, double tol_abs, int max_it,
         if (k >= 1) {
           CHNS_CUDA(cudaEventSynchronize(ev[v ^ 1]));
           rr = slot[v ^ 1];
-          if (bad(rr) || std::sqrt(rr) <= tol_abs) done = true;
+          if (bad(rr) || std::sqrt(rr) <= tol_abs || stalled(it - chunk, rr)) done = true;
         }
         if (done || it >= max_it) {
           CHNS_CUDA(cudaEventSynchronize(ev[v]));
@@ -680,17 +707,29 @@ chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, i
   return iterate<T>(c, step, x, tol_abs, max_it, chunk, rr, iters, rnorm, snap);
 }
 
-// Flexible CG on the Poisson operator with the preconditioner z = M(r): the learned correction
-// plus Jacobi when L is given, else Jacobi (dinv) or the identity.
+// Flexible CG on the Poisson operator with the preconditioner z = M(r): with L the learned
+// correction c followed by one damped Jacobi step, z = c + omega dinv (r - A c) (w: scratch
+// vector); else Jacobi (dinv) or the identity.
 template <class T>
 chns_status fcg(const Ctx& c, const T* b, T* x, const T* dinv, chns_learned* L, double tol_abs,
-                int max_it, int chunk, T* r, T* z, T* p, T* q, T* p2, int* iters, double* rnorm) {
+                int max_it, int chunk, T* r, T* z, T* p, T* q, T* p2, T* w, int* iters,
+                double* rnorm, int stall = 0, const Snap* snap = nullptr) {
   T* pb[2] = {p, p2};
   const int64_t n = c.n;
   const unsigned rg = red_grid(c.m, n), vg = vgrid(c.m, n);
   // rr_slot: where r.r of the current residual is
   auto precond = [&](cudaStream_t s, int rr_slot) -> chns_status {
-    if (L) return learned_precondition<T>(L, c.m, r, dinv, c.S + rr_slot, z, s);
+    if (L) {
+      chns_status e = learned_precondition<T>(L, c.m, r, nullptr, c.S + rr_slot, z, s);
+      if (e != CHNS_OK) return e;
+      Ctx cs = c;
+      cs.s = s;
+      e = apply_T<T>(cs, z, w);
+      if (e != CHNS_OK) return e;
+      note_launch();
+      k_smooth<T><<<vg, kVecThreads, 0, s>>>(z, r, w, dinv, (T)kLearnedOmega, n);
+      return CHNS_OK;
+    }
     note_launch();
     if (dinv) k_mul<T><<<vg, kVecThreads, 0, s>>>(dinv, r, z, n);
     else k_axpby<T><<<vg, kVecThreads, 0, s>>>(1.0, r, 0.0, r, z, n);
@@ -733,7 +772,7 @@ chns_status fcg(const Ctx& c, const T* b, T* x, const T* dinv, chns_learned* L, 
     k_fcg_dots<T><<<rg, kVecThreads, 0, s>>>(z, q, r, n, c.S, c.m->ws.red, c.m->ws.counter, par);
     return CHNS_OK;
   };
-  return iterate<T>(c, step, x, tol_abs, max_it, chunk, rr, iters, rnorm, nullptr);
+  return iterate<T>(c, step, x, tol_abs, max_it, chunk, rr, iters, rnorm, snap, stall);
 }
 
 // Right-preconditioned restarted GMRES with classical Gram-Schmidt and one re-orthogonalisation
@@ -999,9 +1038,19 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
       if (sp->ksp == CHNS_KSP_CG)
         st = pcg<double>(c, b, x, dinv64, tol, sp->max_it, sp->check_every, r64, ws.v64[3],
                          ws.v64[4], ws.v64[5], ws.v64[6], &its, &rn);
-      else if (sp->ksp == CHNS_KSP_FCG)
+      else if (sp->ksp == CHNS_KSP_FCG) {
         st = fcg<double>(c, b, x, dinv64, L, tol, sp->max_it, sp->check_every, r64, ws.v64[3],
-                         ws.v64[4], ws.v64[5], ws.v64[6], &its, &rn);
+                         ws.v64[4], ws.v64[5], ws.v64[6], ws.v64[7], &its, &rn,
+                         L ? kLearnedStall : 0);
+        if (L && st == CHNS_ENOTCONV && its < sp->max_it) {
+          // the learned correction stalled: Jacobi-PCG from the current iterate
+          ++out.fallbacks;
+          int its2 = 0;
+          st = pcg<double>(c, b, x, dinv64, tol, sp->max_it - its, sp->check_every, r64,
+                           ws.v64[3], ws.v64[4], ws.v64[5], ws.v64[6], &its2, &rn);
+          its += its2;
+        }
+      }
       else
         st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it, sp->restart, ws.gm_V,
                            ws.v64[7], &its, &rn);
@@ -1037,6 +1086,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
         c.coefR = coef32;
       }
       int total = 0, refine = 0;
+      bool learned_ok = true;
       double prev_rn = 0.0;
       chns_precision cur = c.inner;
       (void)d32;
@@ -1082,8 +1132,9 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
               st = pcg<double>(c, b, x, dinv64, tol, sp->max_it - total, sp->check_every, r64,
                                ws.v64[3], ws.v64[4], ws.v64[5], ws.v64[6], &its, &frn);
             else if (sp->ksp == CHNS_KSP_FCG)
-              st = fcg<double>(c, b, x, dinv64, L, tol, sp->max_it - total, sp->check_every,
-                               r64, ws.v64[3], ws.v64[4], ws.v64[5], ws.v64[6], &its, &frn);
+              st = fcg<double>(c, b, x, dinv64, nullptr, tol, sp->max_it - total,
+                               sp->check_every, r64, ws.v64[3], ws.v64[4], ws.v64[5], ws.v64[6],
+                               ws.v64[7], &its, &frn);
             else
               st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it - total, sp->restart, ws.gm_V,
                                  ws.v64[7], &its, &frn);
@@ -1109,9 +1160,17 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
         if (sp->ksp == CHNS_KSP_CG)
           ist = pcg<float>(c, r32, d32, dinv32, itol, budget, sp->check_every, ws.v32[3],
                            ws.v32[4], ws.v32[5], ws.v32[6], ws.v32[8], &its, &irn);
-        else if (sp->ksp == CHNS_KSP_FCG)
-          ist = fcg<float>(c, r32, d32, dinv32, L, itol, budget, sp->check_every, ws.v32[3],
-                           ws.v32[4], ws.v32[5], ws.v32[6], ws.v32[8], &its, &irn);
+        else if (sp->ksp == CHNS_KSP_FCG) {
+          chns_learned* Lc = learned_ok ? L : nullptr;
+          ist = fcg<float>(c, r32, d32, dinv32, Lc, itol, budget, sp->check_every, ws.v32[3],
+                           ws.v32[4], ws.v32[5], ws.v32[6], ws.v32[8], ws.v32[7], &its, &irn,
+                           Lc ? kLearnedStall : 0);
+          if (Lc && ist == CHNS_ENOTCONV && its < budget) {
+            // the learned correction stalled: Jacobi only from the next refinement cycle on
+            learned_ok = false;
+            ++out.fallbacks;
+          }
+        }
         else
           ist = gmres<float>(c, r32, d32, dinv32, block2, itol, budget, sp->restart, ws.gm_V32,
                              ws.v32[7], &its, &irn);
@@ -1157,7 +1216,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
 
 chns_status pcg_snapshots(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
                           const double* b_in, double rtol, int every, int max_snaps, double* snaps,
-                          int* n_snaps, double* x, cudaStream_t s) {
+                          int* n_snaps, double* x, cudaStream_t s, chns_learned* L) {
   CHNS_CHECK(every >= 1 && max_snaps >= 0, CHNS_EINVAL, "pcg_snapshots: bad sampling");
   const Workspace& ws = m->ws;
   const int64_t n = m->d.n_nodes;
@@ -1188,8 +1247,21 @@ chns_status pcg_snapshots(const chns_mesh* m, const chns_params* prm, const chns
   Snap sn{snaps, every, max_snaps, n_snaps};
   int its = 0;
   double rn = 0.0;
-  st = pcg<double>(c, b, x, d, rtol * std::sqrt(bn2), 100000, 1, ws.v64[1], ws.v64[3], ws.v64[4],
-                   ws.v64[5], ws.v64[6], &its, &rn, &sn);
+  const double tol = rtol * std::sqrt(bn2);
+  if (L) {
+    // iterates of FCG with the network's own correction; if it stalls, Jacobi-PCG finishes the
+    // solve (without snapshots) so that x is the converged solution
+    st = learned_begin_solve(L, m, prm, coef, s);
+    if (st != CHNS_OK) return st;
+    st = fcg<double>(c, b, x, d, L, tol, 100000, 1, ws.v64[1], ws.v64[3], ws.v64[4], ws.v64[5],
+                     ws.v64[6], ws.v64[7], &its, &rn, kLearnedStall, &sn);
+    if (st == CHNS_ENOTCONV)
+      st = pcg<double>(c, b, x, d, tol, 100000, 1, ws.v64[1], ws.v64[3], ws.v64[4], ws.v64[5],
+                       ws.v64[6], &its, &rn);
+  } else {
+    st = pcg<double>(c, b, x, d, tol, 100000, 1, ws.v64[1], ws.v64[3], ws.v64[4], ws.v64[5],
+                     ws.v64[6], &its, &rn, &sn);
+  }
   if (st != CHNS_OK) return st;
   return project_mean<double>(c, x);
 }

@@ -189,6 +189,87 @@ k_conv(const bf16* __restrict__ in, const bf16* __restrict__ W, const float* __r
     }
 }
 
+// First layer (2 input channels): the contraction index k = 2 tap + channel runs over 54 values,
+// padded to 64 = 4 MMA k-steps instead of 27 (16 channels x 27 taps). A register holds the two
+// channels of one voxel at one tap (one 32-bit shared load); B the two weights of one tap.
+__global__ void __launch_bounds__(kThreads)
+k_conv_c2(const __nv_bfloat162* __restrict__ in, const bf16* __restrict__ W,
+          const float* __restrict__ bias, bf16* __restrict__ out, int D) {
+  __shared__ uint32_t hs[kHalo];
+  __shared__ uint32_t wsm[27 * kC];
+  const TileXYZ o = tile_origin(blockIdx.x, D);
+  for (int i = threadIdx.x; i < 27 * kC; i += kThreads)
+    wsm[i] = reinterpret_cast<const uint32_t*>(W)[i * 8];  // W[tap][co][0..1]
+  for (int v = threadIdx.x; v < kHalo; v += kThreads) {
+    const int hx = v % kHX, hy = (v / kHX) % kHY, hz = v / (kHX * kHY);
+    const int gx = o.x0 - 1 + hx, gy = o.y0 - 1 + hy, gz = o.z0 - 1 + hz;
+    uint32_t val = 0u;
+    if (gx >= 0 && gx < D && gy >= 0 && gy < D && gz >= 0 && gz < D)
+      val = reinterpret_cast<const uint32_t*>(in)[((int64_t)gz * D + gy) * D + gx];
+    hs[v] = val;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gid = lane >> 2, tq = lane & 3;
+  int hrow[2][2];  // halo index of fragment rows gid and gid + 8 of each M-tile
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      int x, y, z;
+      tile_voxel((warp * 2 + mt) * 16 + gid + 8 * hf, x, y, z);
+      hrow[mt][hf] = ((z + 1) * kHY + (y + 1)) * kHX + (x + 1);
+    }
+  float acc[2][2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    const int ta = kk * 8 + tq, tb = ta + 4;
+    const bool va = ta < 27, vb = tb < 27;
+    const int sa = va ? ((ta / 9 - 1) * kHY + (ta / 3) % 3 - 1) * kHX + ta % 3 - 1 : 0;
+    const int sb = vb ? ((tb / 9 - 1) * kHY + (tb / 3) % 3 - 1) * kHX + tb % 3 - 1 : 0;
+    uint32_t b[2][2];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      b[nt][0] = va ? wsm[ta * kC + nt * 8 + gid] : 0u;
+      b[nt][1] = vb ? wsm[tb * kC + nt * 8 + gid] : 0u;
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const uint32_t a0 = va ? hs[hrow[mt][0] + sa] : 0u;
+      const uint32_t a1 = va ? hs[hrow[mt][1] + sa] : 0u;
+      const uint32_t a2 = vb ? hs[hrow[mt][0] + sb] : 0u;
+      const uint32_t a3 = vb ? hs[hrow[mt][1] + sb] : 0u;
+      mma16816(acc[mt][0], a0, a1, a2, a3, b[0][0], b[0][1]);
+      mma16816(acc[mt][1], a0, a1, a2, a3, b[1][0], b[1][1]);
+    }
+  }
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      int x, y, z;
+      tile_voxel((warp * 2 + mt) * 16 + gid + 8 * hf, x, y, z);
+      x += o.x0;
+      y += o.y0;
+      z += o.z0;
+      if (x >= D || y >= D || z >= D) continue;
+      const int64_t vox = ((int64_t)z * D + y) * D + x;
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int co = nt * 8 + 2 * tq;
+        const float v0 = fmaxf(acc[mt][nt][2 * hf] + bias[co], 0.f);
+        const float v1 = fmaxf(acc[mt][nt][2 * hf + 1] + bias[co + 1], 0.f);
+        reinterpret_cast<__nv_bfloat162*>(out)[(vox * kC + co) >> 1] = __floats2bfloat162_rn(v0, v1);
+      }
+    }
+}
+
 // ---------------------------------------------------------------- weight gradient
 // part[blk][t][co][ci] = sum over the voxels v of the CTA's tiles of gz[v][co] in[v + d_t][ci];
 // part[blk][27*256 + co] = sum_v gz[v][co] (bias). GEMM per tap: M = co, N = ci, K = voxels,
@@ -609,29 +690,33 @@ __device__ __forceinline__ float inv_scale(const double* rr, float inv_s_host, f
   return q > 0.f ? rsqrtf(q) : 0.f;
 }
 
-// x0[v] = {bf16(gr[v] / s), bf16(lr[v]), 0 ...} (channel-last, 16 channels)
-__global__ void k_pack_input(const float* __restrict__ gr, const float* __restrict__ lr,
-                             const double* __restrict__ rr, float inv_s_host, float inv_nv,
-                             bf16* __restrict__ x0, int64_t nv) {
-  const float is = inv_scale(rr, inv_s_host, inv_nv);
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv;
-       v += (int64_t)gridDim.x * blockDim.x) {
+// x2[v] = (bf16(gr[v] / s), bf16(lr[v])); x16 (optional): the same as 16 channels, zero-padded
+__device__ __forceinline__ void put_input(__nv_bfloat162 v2, int64_t v, __nv_bfloat162* x2,
+                                          bf16* x16) {
+  x2[v] = v2;
+  if (x16) {
     uint4 r0 = make_uint4(0u, 0u, 0u, 0u);
-    *reinterpret_cast<__nv_bfloat162*>(&r0.x) = __floats2bfloat162_rn(gr[v] * is, lr[v]);
-    reinterpret_cast<uint4*>(x0)[v << 1] = r0;
-    reinterpret_cast<uint4*>(x0)[(v << 1) + 1] = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<__nv_bfloat162*>(&r0.x) = v2;
+    reinterpret_cast<uint4*>(x16)[v << 1] = r0;
+    reinterpret_cast<uint4*>(x16)[(v << 1) + 1] = make_uint4(0u, 0u, 0u, 0u);
   }
 }
 
-// planar FP32 (2, D^3) -> channel-last bf16 (16 channels)
-__global__ void k_pack_planar(const float* __restrict__ x, bf16* __restrict__ x0, int64_t nv) {
+__global__ void k_pack_input(const float* __restrict__ gr, const float* __restrict__ lr,
+                             const double* __restrict__ rr, float inv_s_host, float inv_nv,
+                             __nv_bfloat162* __restrict__ x2, bf16* __restrict__ x16, int64_t nv) {
+  const float is = inv_scale(rr, inv_s_host, inv_nv);
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    uint4 r0 = make_uint4(0u, 0u, 0u, 0u);
-    *reinterpret_cast<__nv_bfloat162*>(&r0.x) = __floats2bfloat162_rn(x[v], x[nv + v]);
-    reinterpret_cast<uint4*>(x0)[v << 1] = r0;
-    reinterpret_cast<uint4*>(x0)[(v << 1) + 1] = make_uint4(0u, 0u, 0u, 0u);
-  }
+       v += (int64_t)gridDim.x * blockDim.x)
+    put_input(__floats2bfloat162_rn(gr[v] * is, lr[v]), v, x2, x16);
+}
+
+// planar FP32 (2, D^3) -> bf16 inputs
+__global__ void k_pack_planar(const float* __restrict__ x, __nv_bfloat162* __restrict__ x2,
+                              bf16* __restrict__ x16, int64_t nv) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv;
+       v += (int64_t)gridDim.x * blockDim.x)
+    put_input(__floats2bfloat162_rn(x[v], x[nv + v]), v, x2, x16);
 }
 
 // replay pair k: (x (2 bf16 per voxel), target FP32)
@@ -641,26 +726,12 @@ __global__ void k_store_pair(const float* __restrict__ gr, const float* __restri
        v += (int64_t)gridDim.x * blockDim.x)
     xs[v] = __floats2bfloat162_rn(gr[v] * inv_s, lr[v]);
 }
-__global__ void k_load_pair(const __nv_bfloat162* __restrict__ xs, bf16* __restrict__ x0,
-                            int64_t nv) {
+__global__ void k_load_pair(const __nv_bfloat162* __restrict__ xs, __nv_bfloat162* __restrict__ x2,
+                            bf16* __restrict__ x16, int64_t nv) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    uint4 r0 = make_uint4(0u, 0u, 0u, 0u);
-    *reinterpret_cast<__nv_bfloat162*>(&r0.x) = xs[v];
-    reinterpret_cast<uint4*>(x0)[v << 1] = r0;
-    reinterpret_cast<uint4*>(x0)[(v << 1) + 1] = make_uint4(0u, 0u, 0u, 0u);
-  }
+       v += (int64_t)gridDim.x * blockDim.x)
+    put_input(xs[v], v, x2, x16);
 }
-__global__ void k_unpack_x(const bf16* __restrict__ x0, float* __restrict__ x, int64_t nv) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    const __nv_bfloat162 p = reinterpret_cast<const __nv_bfloat162*>(x0)[v * 8];
-    const float2 f = __bfloat1622float2(p);
-    x[v] = f.x;
-    x[nv + v] = f.y;
-  }
-}
-
 // z[i] = (dinv ? dinv[i] r[i] : 0) + s out_scale sum_c w_c grid[cell_c]  (s = 1 without rr)
 template <class T>
 __global__ void k_prolong(const float* __restrict__ grid, const uint32_t* __restrict__ xyz,
@@ -682,6 +753,33 @@ __global__ void k_prolong(const float* __restrict__ grid, const uint32_t* __rest
     if (dinv) out += dinv[i] * r[i];
     z[i] = out;
   }
+}
+
+// d[i] = e[i] - sc sum_c w_c grid[cell_c]  (the error left by the correction, FP32)
+__global__ void k_prolong_diff(const float* __restrict__ grid, const uint32_t* __restrict__ xyz,
+                               int64_t N, int D, float scale, float sc, const float* __restrict__ e,
+                               float* __restrict__ d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const Tri w = trilinear(xyz, i, D, scale);
+    float c = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) c = fmaf(tri_w(w, k), grid[tri_cell(w, k, D)], c);
+    d[i] = e[i] - sc * c;
+  }
+}
+
+// *out += f * (a . b) (block sums in FP64, one float atomic per block)
+__global__ void __launch_bounds__(kThreads)
+k_dot_acc(const float* __restrict__ a, const float* __restrict__ b, int64_t n, float f,
+          float* __restrict__ out) {
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[0] += (double)a[i] * (double)b[i];
+  double t[1];
+  block_sum<1, kThreads>(v, t);
+  if (threadIdx.x == 0) atomicAdd(out, (float)(f * t[0]));
 }
 
 __global__ void k_scale_f(const float* __restrict__ a, float* __restrict__ b, int64_t n, float f) {
@@ -729,7 +827,8 @@ struct chns_learned {
   float *P = nullptr, *G = nullptr, *Am = nullptr, *Av = nullptr;
   bf16 *Wf = nullptr, *Wt = nullptr;
   // activations (bf16 channel-last, 16 channels); level l has (D >> l)^3 voxels
-  bf16* x0 = nullptr;
+  bf16* x0 = nullptr;            // input, 16 channels (zero-padded; weight gradient of enc0)
+  __nv_bfloat162* x2 = nullptr;  // input, 2 channels (forward)
   bf16* enc[4] = {};
   bf16* ein[4] = {};   // pooled inputs of enc1..enc3
   bf16* din[3] = {};   // inputs of dec0..dec2
@@ -745,9 +844,16 @@ struct chns_learned {
   // grid scratch
   float *g_r = nullptr, *g_lr = nullptr, *g_w = nullptr, *g_t = nullptr;
   double* dscal = nullptr;  // device scalars
-  // replay buffer
+  // replay buffer: grid inputs and targets; per pair the mean-free error e (FP32) and the
+  // coefficient 1 + phi~ (bfloat16) on the nodes of the bound mesh, s(A e) and e^T A e
   __nv_bfloat162* rx = nullptr;
   float* rt = nullptr;
+  const chns_mesh* bound = nullptr;
+  int64_t bound_n = 0;
+  float* re = nullptr;
+  bf16* rphi = nullptr;
+  float *d32 = nullptr, *w32 = nullptr;
+  std::vector<double> hs, heae;
   float* loss_dev = nullptr;
   int loss_cap = 0;
 };
@@ -793,9 +899,10 @@ static void wgrad(chns_learned* L, const bf16* in, int layer, int D, cudaStream_
                                                      L->G + L->off.w[layer], L->G + L->off.b[layer]);
 }
 
-// Forward pass from L->x0; output in L->out.
+// Forward pass from L->x2; output in L->out.
 static chns_status forward(chns_learned* L, cudaStream_t s) {
-  conv(L, true, L->x0, 0, L->enc[0], lvl(L, 0), s);
+  note_launch();
+  k_conv_c2<<<num_tiles(L->D), kThreads, 0, s>>>(L->x2, L->Wf, L->P + L->off.b[0], L->enc[0], L->D);
   for (int l = 1; l < 4; ++l) {
     note_launch();
     k_pool<<<grid_for(vox(L, l) * 2), kThreads, 0, s>>>(L->enc[l - 1], L->ein[l], lvl(L, l));
@@ -929,8 +1036,8 @@ chns_status learned_precondition(chns_learned* L, const chns_mesh* m, const T* r
   restrict_to<T>(L, m, r, L->g_r, s);
   const float inv_nv = (float)(1.0 / (double)L->nv);
   note_launch();
-  k_pack_input<<<grid_for(L->nv), kThreads, 0, s>>>(L->g_r, L->g_lr, rr_dev, 0.f, inv_nv, L->x0,
-                                                    L->nv);
+  k_pack_input<<<grid_for(L->nv), kThreads, 0, s>>>(L->g_r, L->g_lr, rr_dev, 0.f, inv_nv, L->x2,
+                                                    nullptr, L->nv);
   chns_status st = forward(L, s);
   if (st != CHNS_OK) return st;
   const int64_t N = m->d.n_nodes;
@@ -951,10 +1058,36 @@ chns_status learned_add_sample(chns_learned* L, const chns_mesh* m, const chns_p
   using namespace lp;
   CHNS_CHECK(L && m && prm && coef && e, CHNS_EINVAL, "chns_learned_add_sample: null argument");
   CHNS_CHECK(L->capacity > 0, CHNS_EINVAL, "chns_learned_add_sample: no replay buffer");
+  CHNS_CHECK(coef->phi_tilde, CHNS_EINVAL, "chns_learned_add_sample: coefficient phi~ missing");
   const int64_t N = m->d.n_nodes;
+  if (!L->bound) {  // the nodal part of the replay buffer is sized for the first mesh
+    const size_t cap = (size_t)L->capacity;
+    if (cudaMalloc(&L->re, cap * N * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&L->rphi, cap * N * sizeof(bf16)) != cudaSuccess ||
+        cudaMalloc(&L->d32, N * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&L->w32, N * sizeof(float)) != cudaSuccess) {
+      set_error("chns_learned_add_sample: device allocation of the replay buffer failed");
+      return CHNS_ENOMEM;
+    }
+    L->bound = m;
+    L->bound_n = N;
+  }
+  CHNS_CHECK(L->bound == m && L->bound_n == N, CHNS_EINVAL,
+             "chns_learned_add_sample: the replay buffer holds pairs of another mesh");
   double* r = nullptr;
+  double* ep = nullptr;
   CHNS_CUDA(cudaMallocAsync(&r, N * sizeof(double), s));
-  chns_status st = apply_op(m, CHNS_OP_POISSON, prm, coef, e, r, CHNS_FP64, s);
+  CHNS_CUDA(cudaMallocAsync(&ep, N * sizeof(double), s));
+  // the error sample without its nodal mean: constants are the Poisson operator's null space, so
+  // r = A e carries no information about them (and the solver returns mean-free iterates)
+  double esum = 0.0;
+  chns_status st = sum_host(m, e, N, &esum, s);
+  if (st == CHNS_OK) {
+    vec_copy(e, ep, N, s);
+    CHNS_CUDA(cudaMemcpyAsync(L->dscal, &esum, sizeof(double), cudaMemcpyHostToDevice, s));
+    vec_add_scalar(ep, L->dscal, -1.0 / (double)N, N, s);
+    st = apply_op(m, CHNS_OP_POISSON, prm, coef, ep, r, CHNS_FP64, s);
+  }
   double rr = 0.0;
   if (st == CHNS_OK) st = dot_host(m, r, r, N, &rr, s);
   if (st == CHNS_OK && rr > 0.0 && std::isfinite(rr)) {
@@ -967,21 +1100,29 @@ chns_status learned_add_sample(chns_learned* L, const chns_mesh* m, const chns_p
       k_store_pair<<<grid_for(L->nv), kThreads, 0, s>>>(L->g_r, L->g_lr, (float)(1.0 / sc),
                                                         L->rx + (size_t)k * L->nv, L->nv);
       float* t = L->rt + (size_t)k * L->nv;
-      restrict_to<double>(L, m, e, t, s);
+      restrict_to<double>(L, m, ep, t, s);
       note_launch();
       k_cell_mean<<<grid_for(L->nv), kThreads, 0, s>>>(t, L->g_w, L->nv, (float)(1.0 / sc));
+      double eae = 0.0;
+      st = dot_host(m, ep, r, N, &eae, s);
+      vec_convert_f64_f32(ep, L->re + (size_t)k * N, N, s);
+      vec_convert_f64_bf16(static_cast<const double*>(coef->phi_tilde), L->rphi + (size_t)k * N, N,
+                           1.0, s);
+      L->hs[k] = sc;
+      L->heae[k] = eae;
       L->next = (k + 1) % L->capacity;
       L->count = std::min(L->count + 1, L->capacity);
     }
   }
   cudaFreeAsync(r, s);
+  cudaFreeAsync(ep, s);
   CHNS_CUDA(cudaGetLastError());
   return st;
 }
 
 chns_status learned_collect(chns_learned* L, const chns_mesh* m, const chns_params* prm,
                             const chns_coef* coef, const double* b, int every, int max_samples,
-                            int* added, cudaStream_t s) {
+                            bool with_net, int* added, cudaStream_t s) {
   CHNS_CHECK(L && m && prm && coef && b && added, CHNS_EINVAL, "chns_learned_collect: null argument");
   CHNS_CHECK(every >= 1 && max_samples >= 0, CHNS_EINVAL, "chns_learned_collect: bad sampling");
   *added = 0;
@@ -991,7 +1132,10 @@ chns_status learned_collect(chns_learned* L, const chns_mesh* m, const chns_para
   CHNS_CUDA(cudaMallocAsync(&snaps, (size_t)max_samples * N * sizeof(double), s));
   CHNS_CUDA(cudaMallocAsync(&xs, (size_t)N * sizeof(double), s));
   int ns = 0;
-  chns_status st = pcg_snapshots(m, prm, coef, b, 1e-10, every, max_samples, snaps, &ns, xs, s);
+  CHNS_CHECK(!with_net || L->out_scale > 0.0, CHNS_EINVAL,
+             "chns_learned_collect: the network has no output scale yet (train first)");
+  chns_status st = pcg_snapshots(m, prm, coef, b, 1e-10, every, max_samples, snaps, &ns, xs, s,
+                                 with_net ? L : nullptr);
   for (int k = 0; k < ns && st == CHNS_OK; ++k) {
     double* e = snaps + (size_t)k * N;
     vec_axpby(1.0, xs, -1.0, e, e, N, s);  // e_k = x* - x_k
@@ -1044,6 +1188,7 @@ chns_status chns_learned_create(int32_t D, int32_t capacity, uint64_t seed, void
   alloc(&L->Wt, kLayers * 27 * 256 * 2);
   auto act = [&](int l) { return (size_t)vox(L, l) * kC * 2; };
   alloc(&L->x0, act(0));
+  alloc(&L->x2, (size_t)L->nv * 4);
   for (int l = 0; l < 4; ++l) alloc(&L->enc[l], act(l));
   for (int l = 1; l < 4; ++l) alloc(&L->ein[l], act(l));
   for (int l = 0; l < 3; ++l) {
@@ -1064,14 +1209,16 @@ chns_status chns_learned_create(int32_t D, int32_t capacity, uint64_t seed, void
   if (capacity > 0) {
     alloc(&L->rx, (size_t)capacity * L->nv * 4);
     alloc(&L->rt, (size_t)capacity * L->nv * 4);
+    L->hs.assign(capacity, 0.0);
+    L->heae.assign(capacity, 0.0);
   }
   if (!ok) {
     chns_learned_destroy(L);
     set_error("chns_learned_create: device allocation failed");
     return CHNS_ENOMEM;
   }
-  // He-normal weights (std sqrt(2 / (27 cin)); out layer sqrt(1 / 16)), zero biases, drawn by
-  // a seeded splitmix64 + Box-Muller generator on the host
+  // He-normal conv weights (std sqrt(2 / (27 cin))), zero biases, drawn by a seeded
+  // splitmix64 + Box-Muller generator on the host
   std::vector<float> h(np, 0.f);
   uint64_t state = seed;
   auto normal = [&]() {
@@ -1083,7 +1230,9 @@ chns_status chns_learned_create(int32_t D, int32_t capacity, uint64_t seed, void
     const double sd = std::sqrt(2.0 / (27.0 * L->off.cin[k]));
     for (int i = 0; i < 27 * kC * L->off.cin[k]; ++i) h[L->off.w[k] + i] = (float)(sd * normal());
   }
-  for (int c = 0; c < kC; ++c) h[L->off.outw + c] = (float)(std::sqrt(1.0 / kC) * normal());
+  // the output layer starts at zero: the first correction is c = 0 (energy loss 1), and the
+  // gradient reaches the convolutions only once out.W has moved (no early blow-up that would
+  // switch all ReLUs off)
   st = chns_learned_set_params(L, h.data());
   if (st != CHNS_OK) {
     chns_learned_destroy(L);
@@ -1096,11 +1245,12 @@ chns_status chns_learned_create(int32_t D, int32_t capacity, uint64_t seed, void
 
 void chns_learned_destroy(chns_learned* L) {
   if (!L) return;
-  void* ptrs[] = {L->P, L->G, L->Am, L->Av, L->Wf, L->Wt, L->x0, L->enc[0], L->enc[1], L->enc[2],
+  void* ptrs[] = {L->P, L->G, L->Am, L->Av, L->Wf, L->Wt, L->x0, L->x2, L->enc[0], L->enc[1], L->enc[2],
                   L->enc[3], L->ein[1], L->ein[2], L->ein[3], L->din[0], L->din[1], L->din[2],
                   L->dec[0], L->dec[1], L->dec[2], L->gdec[0], L->gdec[1], L->gdec[2],
                   L->gein[1], L->gein[2], L->gein[3], L->gz, L->out, L->wpart, L->opart,
-                  L->g_r, L->g_lr, L->g_w, L->g_t, L->dscal, L->rx, L->rt, L->loss_dev};
+                  L->g_r, L->g_lr, L->g_w, L->g_t, L->dscal, L->rx, L->rt, L->loss_dev,
+                  L->re, L->rphi, L->d32, L->w32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete L;
@@ -1140,7 +1290,7 @@ chns_status chns_learned_forward(chns_learned* L, const float* x, float* out, vo
   CHNS_CHECK(L && x && out, CHNS_EINVAL, "chns_learned_forward: null argument");
   cudaStream_t s = as_stream(stream);
   note_launch();
-  k_pack_planar<<<grid_for(L->nv), kThreads, 0, s>>>(x, L->x0, L->nv);
+  k_pack_planar<<<grid_for(L->nv), kThreads, 0, s>>>(x, L->x2, L->x0, L->nv);
   chns_status st = forward(L, s);
   if (st != CHNS_OK) return st;
   CHNS_CUDA(cudaMemcpyAsync(out, L->out, L->nv * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -1207,20 +1357,25 @@ chns_status chns_learned_add_sample(chns_learned* L, const chns_mesh* m, const c
 
 chns_status chns_learned_collect(chns_learned* L, const chns_mesh* m, const chns_params* prm,
                                  const chns_coef* coef, const double* b, int32_t every,
-                                 int32_t max_samples, int32_t* added, void* stream) {
+                                 int32_t max_samples, int32_t with_net, int32_t* added,
+                                 void* stream) {
   int a = 0;
-  chns_status st = chns::learned_collect(L, m, prm, coef, b, every, max_samples, &a, as_stream(stream));
+  chns_status st = chns::learned_collect(L, m, prm, coef, b, every, max_samples, with_net != 0, &a,
+                                         as_stream(stream));
   if (added) *added = a;
   return st;
 }
 
 int32_t chns_learned_num_samples(const chns_learned* L) { return L ? L->count : 0; }
 
-chns_status chns_learned_train(chns_learned* L, int32_t iterations, double lr, uint64_t seed,
-                               float* loss_host, void* stream) {
+chns_status chns_learned_train(chns_learned* L, const chns_mesh* m, const chns_params* prm,
+                               int32_t iterations, double lr, uint64_t seed, float* loss_host,
+                               void* stream) {
   using namespace chns::lp;
-  CHNS_CHECK(L && iterations >= 0 && lr > 0.0, CHNS_EINVAL, "chns_learned_train: bad argument");
+  CHNS_CHECK(L && m && prm && iterations >= 0 && lr > 0.0, CHNS_EINVAL,
+             "chns_learned_train: bad argument");
   CHNS_CHECK(L->count > 0, CHNS_EINVAL, "chns_learned_train: the replay buffer is empty");
+  CHNS_CHECK(L->bound == m, CHNS_EINVAL, "chns_learned_train: the pairs belong to another mesh");
   cudaStream_t s = as_stream(stream);
   if (L->out_scale <= 0.0) {
     double tot = 0.0;
@@ -1239,14 +1394,36 @@ chns_status chns_learned_train(chns_learned* L, int32_t iterations, double lr, u
     CHNS_CUDA(cudaMalloc(&L->loss_dev, std::max(iterations, 1) * sizeof(float)));
     L->loss_cap = iterations;
   }
-  const float inv_ts = (float)(1.0 / L->out_scale);
+  if (iterations > 0)
+    CHNS_CUDA(cudaMemsetAsync(L->loss_dev, 0, iterations * sizeof(float), s));
+  const int64_t N = L->bound_n;
+  const unsigned nb = std::min<unsigned>(grid_for(N), 1024);
   uint64_t st_rng = seed;
   for (int it = 0; it < iterations; ++it) {
     const int k = (int)(splitmix64(st_rng) % (uint64_t)L->count);
+    const double sc = L->hs[k] * L->out_scale, eae = L->heae[k];
+    if (!(eae > 0.0) || !std::isfinite(eae)) continue;
     note_launch();
-    k_load_pair<<<grid_for(L->nv), kThreads, 0, s>>>(L->rx + (size_t)k * L->nv, L->x0, L->nv);
+    k_load_pair<<<grid_for(L->nv), kThreads, 0, s>>>(L->rx + (size_t)k * L->nv, L->x2, L->x0,
+                                                     L->nv);
     chns_status st = forward(L, s);
-    if (st == CHNS_OK) st = backward(L, L->rt + (size_t)k * L->nv, inv_ts, nullptr, L->loss_dev + it, s);
+    if (st != CHNS_OK) return st;
+    // d = e - c, w = A d with the pair's coefficients (FP32 apply, bfloat16 coefficient)
+    note_launch();
+    k_prolong_diff<<<grid_for(N), kThreads, 0, s>>>(L->out, m->d_node_int, N, L->D,
+                                                    grid_scale(L->D), (float)sc,
+                                                    L->re + (size_t)k * N, L->d32);
+    chns_coef ck{};
+    ck.phi_tilde = L->rphi + (size_t)k * N;
+    st = apply_op(m, CHNS_OP_POISSON, prm, &ck, L->d32, L->w32, CHNS_FP32_BF16COEF, s);
+    if (st != CHNS_OK) return st;
+    note_launch();
+    k_dot_acc<<<nb, kThreads, 0, s>>>(L->d32, L->w32, N, (float)(1.0 / eae), L->loss_dev + it);
+    // dL/d(out) = -2 sc P_g^T (A d) / e^T A e
+    restrict_to<float>(L, m, L->w32, L->g_t, s);
+    note_launch();
+    k_scale_f<<<grid_for(L->nv), kThreads, 0, s>>>(L->g_t, L->g_r, L->nv, (float)(-2.0 * sc / eae));
+    st = backward(L, nullptr, 0.f, L->g_r, nullptr, s);
     if (st != CHNS_OK) return st;
     adam(L, L->G, lr, s);
   }

@@ -168,7 +168,7 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
     if (sp->collect) {
       int added = 0;
       rc = learned_collect(sp->collect, m, prm, &cv, bv, std::max(1, sp->collect_every),
-                           std::max(0, sp->collect_max), &added, s);
+                           std::max(0, sp->collect_max), sp->collect_with_net != 0, &added, s);
       if (rc != CHNS_OK) return rc;
     }
     // ---- velocity update

@@ -125,6 +125,37 @@ def test_grid_transfer_matches_oracle(capi, name):
     assert relerr(y.cpu().numpy(), Pg @ grid.astype(np.float64)) < 1e-6
 
 
+def test_energy_loss_matches_oracle(capi):
+    """One pair through the C ABI (projection, r = A e, inputs, stored e and bfloat16
+    coefficients) and the first training loss against the oracle's energy loss."""
+    import torch
+    om, gm = meshes("drop_l3_5")
+    D = 16
+    net, flat = _randomised_net(capi, D, 13)
+    net2 = capi.chns_learned_create(D, 4, 13)
+    capi.chns_learned_set_params(net2, flat)
+    capi.chns_learned_destroy(net)
+    capi.chns_learned_set_output_scale(net2, 0.05)
+    rng = np.random.default_rng(14)
+    n = om.n_nodes
+    phi = np.tanh(2.0 * rng.standard_normal(n))
+    e = rng.standard_normal(n) + 3.0
+    prm = capi.make_params(PRM)
+    capi.chns_learned_add_sample(net2, gm.handle, prm, capi.make_coef(dev(phi)), dev(e))
+    loss = capi.chns_learned_train(net2, gm.handle, prm, 1, 1e-9, 0)
+    capi.chns_learned_destroy(net2)
+    co = fem.Coeffs(PRM)
+    ep = e - e.mean()
+    A64 = fem.poisson(fem.Elem(om), co, phi)
+    r = A64 @ ep
+    Pg = L.grid_prolongation(om.node_int, om.extent, D)
+    x, s = L.restrict_inputs(Pg, r, L.cell_mean(Pg, L.log_inv_rho(co, phi), D), D)
+    A16 = fem.poisson(fem.Elem(om), co, L.bf16_round(1.0 + phi) - 1.0)   # the loss's operator
+    ref, _, _ = L.energy_loss_and_grad(_oracle_params(flat), Pg, A16, ep, x, s, D, 0.05,
+                                       round_act=L.bf16_round)
+    assert abs(loss[0] - ref) <= 2e-2 * ref, (loss[0], ref)
+
+
 def _poisson_system(om, seed):
     rng = np.random.default_rng(seed)
     n = om.n_nodes
@@ -206,8 +237,9 @@ def test_trained_network_reduces_iterations(capi):
     for _ in range(16):
         capi.chns_learned_collect(net, gm.handle, prm, coef, dev(rhs()), 4, 32)
     assert capi.chns_learned_num_samples(net) >= 64
-    loss = capi.chns_learned_train(net, 1500, 1e-3, 1)
-    assert np.mean(loss[-100:]) < 0.5 * np.mean(loss[:20]), (loss[:20].mean(), loss[-100:].mean())
+    loss = capi.chns_learned_train(net, gm.handle, prm, 1500, 1e-3, 1)
+    # the energy loss starts at 1 (zero output layer: c = 0)
+    assert np.mean(loss[-100:]) < 0.7 * np.mean(loss[:20]), (loss[:20].mean(), loss[-100:].mean())
     its_j, its_l = [], []
     for _ in range(3):
         b = dev(rhs())

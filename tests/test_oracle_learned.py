@@ -134,15 +134,29 @@ def test_correction_is_positively_homogeneous_and_zero_net_gives_jacobi():
     assert np.array_equal(L.coarse_correction(P, Pg, 0 * r, lr, D, 2.0), np.zeros(m.n_nodes))
     Z = {k: np.zeros_like(v) for k, v in P.items()}
     dinv = rng.uniform(0.5, 2.0, m.n_nodes)
-    assert np.allclose(L.precondition(Z, Pg, r, lr, D, 2.0, dinv), dinv * r, rtol=0, atol=0)
+    A = np.eye(m.n_nodes) * 3.0
+    assert np.allclose(L.precondition(Z, Pg, A, r, lr, D, 2.0, dinv), (2.0 / 3.0) * dinv * r,
+                       rtol=1e-15, atol=0)
+    # with a network, the Jacobi step acts on what the correction leaves
+    z = L.precondition(P, Pg, A, r, lr, D, 2.0, dinv, omega=0.5)
+    assert np.allclose(z, c1 + 0.5 * dinv * (r - 3.0 * c1), rtol=1e-12)
 
 
 def test_training_target_of_constant_error():
+    """Constants are the Poisson null space: a constant error gives a zero target, adding one
+    changes nothing; the cell mean of a constant is that constant where nodes reach."""
     D = 8
     m, Pg = _mesh_and_grid(D)
-    t = L.training_target(Pg, np.full(m.n_nodes, 2.5), 0.5, D)
-    reached = (Pg.T @ np.ones(m.n_nodes)).reshape(D, D, D) > 0
-    assert np.allclose(t[reached], 5.0) and np.all(t[~reached] == 0)
+    n = m.n_nodes
+    reached = (Pg.T @ np.ones(n)).reshape(D, D, D) > 0
+    cm = L.cell_mean(Pg, np.full(n, 2.5), D)
+    assert np.allclose(cm[reached], 2.5) and np.all(cm[~reached] == 0)
+    assert np.allclose(L.training_target(Pg, np.full(n, 2.5), 0.5, D), 0.0, atol=1e-14)
+    e = np.random.default_rng(0).standard_normal(n)
+    t = L.training_target(Pg, e, 0.5, D)
+    assert np.allclose(L.training_target(Pg, e + 7.0, 0.5, D), t, atol=1e-12)
+    assert np.allclose(L.training_target(Pg, 3.0 * e, 1.5, D), t, atol=1e-12)
+    assert np.allclose(t, L.cell_mean(Pg, e - e.mean(), D) / 0.5)
 
 
 def test_fcg_with_fixed_preconditioner_equals_pcg():
@@ -160,3 +174,27 @@ def test_fcg_with_fixed_preconditioner_equals_pcg():
     x1, it1, _ = solvers.pcg(A, b, rtol=1e-10)
     x2, it2, _ = L.fcg(A, b, lambda r: dinv * r, rtol=1e-10)
     assert abs(it1 - it2) <= 1 and np.allclose(x1, x2, rtol=0, atol=1e-8 * np.abs(x1).max())
+
+
+def test_energy_loss_gradient_matches_finite_differences():
+    """dL/d(out) of the energy loss against central differences through a linear output layer:
+    perturbing out.b by t shifts out by t everywhere, so dL/d(out.b) = sum of dL/d(out)."""
+    from oracle import fem
+    D = 8
+    m, Pg = _mesh_and_grid(D)
+    co = fem.Coeffs(dict(Re=1, We=1, Cn=0.1, Pe=1, Fr=1, rho_ratio=10.0, eta_ratio=1.0, dt=1.0,
+                         C_I=6.0))
+    rng = np.random.default_rng(3)
+    A = fem.poisson(fem.Elem(m), co, np.tanh(rng.standard_normal(m.n_nodes)))
+    e = rng.standard_normal(m.n_nodes)
+    e -= e.mean()
+    P, x, _ = _net(D=D, C=4, seed=6)
+    loss, gout, _ = L.energy_loss_and_grad(P, Pg, A, e, x, 0.7, D, 1.3)
+    eps = 1e-6
+    P["out.b"] = P["out.b"] + eps
+    lp = L.energy_loss_and_grad(P, Pg, A, e, x, 0.7, D, 1.3)[0]
+    P["out.b"] = P["out.b"] - 2 * eps
+    lm = L.energy_loss_and_grad(P, Pg, A, e, x, 0.7, D, 1.3)[0]
+    assert abs((lp - lm) / (2 * eps) - gout.sum()) <= 1e-6 * max(1.0, abs(gout.sum()))
+    Z = {k: np.zeros_like(v) for k, v in P.items()}
+    assert np.isclose(L.energy_loss_and_grad(Z, Pg, A, e, x, 0.7, D, 1.3)[0], 1.0, rtol=1e-13)
