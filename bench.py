@@ -12,7 +12,10 @@ plain_fp64  = the same numbers for the all-FP64 path on the same GPU;
 bf16_coefficients = the headline path with bfloat16 coefficient storage for Poisson / mass;
 e2e         = one Poisson solve through the C ABI from pinned host buffers (copies timed);
 roofline    = the dominant apply kernel timed alone from a cold L2 (algorithmic bytes / time);
-cpu_baseline= the FP64 CPU oracle (assembled matrix + Jacobi-PCG) on a bounded sample.
+cpu_baseline= the FP64 CPU oracle (assembled matrix + Jacobi-PCG) on a bounded sample;
+learned     = the learned coarse correction for the pressure-Poisson solve on the 8-drop
+              workload: pairs from time steps, training, and the solves of one more step with
+              and without it (untimed setup; see run_learned).
 
 Under torchrun (N > 1) every rank runs an independent replica (the method is not sharded) and
 value sums the replicas; timing is the max over ranks.
@@ -241,6 +244,9 @@ def run_ours(args):
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_val = ws * N / (statistics.mean(e2e_ms) * 1e-3)
 
+    learned = None
+    if rank == 0 and not args.no_learned:
+        learned = run_learned(args)
     if rank == 0:
         cpu = cpu_baseline(w, mesh.node_xyz, f0, budget_s=args.cpu_budget) if not args.no_cpu else None
         line = {
@@ -269,12 +275,136 @@ def run_ours(args):
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "alg_bytes": int(alg_bytes), "ms": t_apply * 1e3},
             "cpu_baseline": cpu,
+            "learned": learned,
             "clocks": clocks,
             "gpu_launches": headline["launches"],
         }
         print(json.dumps(line))
     if pg:
         pg.destroy_process_group()
+
+
+def run_learned(args):
+    """The learned coarse correction on the 8-drop workload (levels 5-8, drops of radius
+    0.05-0.12, Cn 0.01, density ratio 1000): training pairs from the pressure-Poisson solves of
+    `--learned-steps` time steps (iterates of FP64 Jacobi-PCG, every 8th, at most 24 per solve),
+    energy-norm training on the GPU, then the pressure-Poisson solves of one more step from the
+    same state with Jacobi-PCG (FP32 + FP64 refinement), FCG + learned correction (same
+    precision) and plain FP64 Jacobi-PCG. Returns the summary object of the bench line."""
+    import torch
+
+    from chns_workloads import configs
+    from paper_2107_05123_gb300 import capi
+    from paper_2107_05123_gb300.session import DeviceState, Mesh, default_step_params
+
+    t_all = time.perf_counter()
+    w = configs.many_drops(seed=0, n=8, rmin=0.05, rmax=0.12, lmin=5, lmax=8, Cn=0.01)
+    mesh = Mesh(w.anchors, w.levels, w.extent)
+    prm = capi.make_params(w.params.as_dict())
+    f0 = w.init(mesh.node_xyz)
+    D = args.learned_grid
+    net = capi.chns_learned_create(D, 4096, 1)
+
+    def params(pp=None, collect=None):
+        sp = default_step_params(rtol=1e-8, inner=capi.FP32, pp_check_every=8)
+        sp.vp.max_it = 20000
+        if pp is not None:
+            sp.pp = pp
+        if collect is not None:
+            sp.collect, sp.collect_every, sp.collect_max = collect, 8, 24
+        return sp
+
+    ds = DeviceState(dict(phi=f0["phi"], mu=f0["mu"], u=f0["u"], p=f0["p"]))
+    t0 = time.perf_counter()
+    for _ in range(args.learned_steps):
+        capi.chns_step(mesh.handle, ds.c, prm, params(collect=net))
+    torch.cuda.synchronize()
+    t_collect = time.perf_counter() - t0
+    pairs = capi.chns_learned_num_samples(net)
+    t0 = time.perf_counter()
+    loss = capi.chns_learned_train(net, mesh.handle, prm, args.learned_iters, args.learned_lr, 0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    snap = ds.host()
+    res = {}
+    solvers = {
+        "jacobi_fp32": capi.make_solver(capi.KSP_CG, capi.PC_JACOBI, 1e-8, 20000, 30, capi.FP32,
+                                        1e-6, 30, check_every=8),
+        "learned_fp32": capi.make_solver(capi.KSP_FCG, capi.PC_LEARNED, 1e-8, 20000, 30,
+                                         capi.FP32, 1e-6, 30, check_every=8, learned=net),
+        "jacobi_fp64": capi.make_solver(capi.KSP_CG, capi.PC_JACOBI, 1e-8, 20000, 30, capi.FP64,
+                                        check_every=8),
+    }
+    for name, sol in solvers.items():
+        st = capi.chns_step(mesh.handle, DeviceState(snap).c, prm, params(pp=sol))
+        res[name] = dict(pp_iters=[st.pp[l].iterations for l in range(2)],
+                         pp_ms=[round(st.pp[l].ms, 3) for l in range(2)],
+                         fallbacks=[st.pp[l].fallbacks for l in range(2)],
+                         rel_residual=[st.pp[l].rel_residual for l in range(2)])
+    capi.chns_learned_destroy(net)
+    small = _learned_small_drops(args)
+    return {"workload": "drops8_levels5-8", "n_elem": int(mesh.n_elem),
+            "n_nodes": int(mesh.n_nodes), "grid": D, "channels": 16, "levels": 4,
+            "collect_steps": args.learned_steps, "pairs": int(pairs),
+            "train_iterations": args.learned_iters, "lr": args.learned_lr,
+            "collect_s": round(t_collect, 2), "train_s": round(t_train, 2),
+            "train_ms_per_iteration": round(1e3 * t_train / max(args.learned_iters, 1), 3),
+            "energy_loss_first_100": float(loss[:100].mean()) if len(loss) else None,
+            "energy_loss_last_500": float(loss[-500:].mean()) if len(loss) else None,
+            "pp_solves_next_step": res, "small_drops": small,
+            "wall_s": round(time.perf_counter() - t_all, 1)}
+
+
+def _learned_small_drops(args):
+    """The same method on a small 4-drop octree (levels 3-6, Cn 0.02, density ratio 1000) with
+    D = 16: pairs from FP64 Jacobi-PCG solves of 16 seeded smooth right-hand sides, 1,500
+    training iterations, then Jacobi-PCG and FCG + learned correction (FP64) on 3 unseen ones."""
+    import numpy as np
+    import torch
+
+    from chns_workloads import configs
+    from paper_2107_05123_gb300 import capi
+    from paper_2107_05123_gb300.session import Mesh
+
+    w = configs.many_drops(seed=3, n=4, lmin=3, lmax=6, Cn=0.02)
+    mesh = Mesh(w.anchors, w.levels, w.extent)
+    n = mesh.n_nodes
+    prm = capi.make_params(w.params.as_dict())
+    phi = torch.as_tensor(w.init(mesh.node_xyz)["phi"], device="cuda")
+    coef = capi.make_coef(phi)
+    rng = np.random.default_rng(12)
+
+    def rhs():
+        f = np.zeros(n)
+        for _ in range(6):
+            k = rng.integers(1, 4, size=3)
+            f += rng.standard_normal() * np.cos(np.pi * (k * mesh.node_xyz).sum(axis=1)
+                                                + rng.uniform(0, 6.3))
+        return torch.as_tensor(f - f.mean(), device="cuda")
+
+    net = capi.chns_learned_create(16, 512, 5)
+    for _ in range(16):
+        capi.chns_learned_collect(net, mesh.handle, prm, coef, rhs(), 4, 32)
+    t0 = time.perf_counter()
+    capi.chns_learned_train(net, mesh.handle, prm, 1500, 1e-3, 1)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    out = {"jacobi_pcg": [], "fcg_learned": [], "jacobi_ms": [], "learned_ms": []}
+    for _ in range(3):
+        b = rhs()
+        for pc, ksp, key in ((capi.PC_JACOBI, capi.KSP_CG, "jacobi"),
+                             (capi.PC_LEARNED, capi.KSP_FCG, "learned")):
+            x = torch.zeros(n, device="cuda", dtype=torch.float64)
+            st = capi.chns_krylov_solve(mesh.handle, capi.OP_POISSON, prm, coef, b, x,
+                                        capi.make_solver(ksp, pc, 1e-8, 20000, 30, capi.FP64,
+                                                         check_every=8, learned=net))
+            out["jacobi_pcg" if key == "jacobi" else "fcg_learned"].append(st.iterations)
+            out[key + "_ms"].append(round(st.ms, 3))
+    pairs = capi.chns_learned_num_samples(net)
+    capi.chns_learned_destroy(net)
+    out.update(workload="drops4_levels3-6", n_nodes=int(n), grid=16, pairs=int(pairs),
+               train_iterations=1500, train_s=round(t_train, 2))
+    return out
 
 
 # --------------------------------------------------------------------------- CPU oracle
@@ -426,6 +556,13 @@ def main():
                     help="time only one path and print a detail line (profiling runs)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the roofline kernel from an ncu capture")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-preconditioner measurement (8-drop workload)")
+    ap.add_argument("--learned-steps", type=int, default=8,
+                    help="time steps whose pressure-Poisson solves give the training pairs")
+    ap.add_argument("--learned-iters", type=int, default=8000, help="training iterations")
+    ap.add_argument("--learned-lr", type=float, default=3e-4)
+    ap.add_argument("--learned-grid", type=int, default=64, help="grid size D of the network")
     ap.add_argument("--mode", choices=["bench", "apply", "pp"], default="bench",
                     help="apply / pp: time only the roofline kernel / the Poisson solve (profiling)")
     args = ap.parse_args()

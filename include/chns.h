@@ -287,7 +287,8 @@ chns_status chns_step(const chns_mesh* mesh, chns_state* state, const chns_param
  *   bias[16]; then out.W[16] and out.b[1].
  * Training: on pairs (x(r), e) of mean-free error samples e with r = A e, the relative energy
  *   norm of the error the correction leaves, loss = (e - c(r))^T A (e - c(r)) / (e^T A e), with
- *   A applied in FP32 with bfloat16 coefficients; Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ *   A applied in FP32 with bfloat16 coefficients; where a pair's loss exceeds 1 its gradient is
+ *   divided by the loss (the gradient of log(loss)); Adam (beta1 0.9, beta2 0.999, eps 1e-8).
  * Grid arrays are FP32 device arrays indexed (channel, z, y, x), x fastest. The object owns its
  * device memory (activations, gradients, replay buffer of `capacity` pairs) and may be used
  * with any mesh. Calls are asynchronous on `stream` except those returning host values. */

@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(MeshDev m, DevParams p,
 template <class K, class T, class S, class C, bool PQ, bool CGP>
 __global__ void __launch_bounds__(kPatchElems)
 k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S* __restrict__ y,
-              double* __restrict__ S_cg, int par, const S* __restrict__ zcg, S* __restrict__ pout) {
+              double* __restrict__ S_cg, int par, int fcg, const S* __restrict__ zcg,
+              S* __restrict__ pout) {
   constexpr int NC = K::NC, NF = K::NF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* xs = reinterpret_cast<T*>(smem_raw);       // [NC][kPatchSlots]
@@ -60,8 +61,15 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
   // patch never reads a p value another patch has already updated)
   __shared__ T s_beta;
   if (CGP && threadIdx.x == 0) {
-    const double rzc = S_cg[kCgRz0 + par], rzp = S_cg[kCgRzPrev];
-    s_beta = (T)(rzp != 0.0 ? rzc / rzp : 0.0);
+    double bn, bd;
+    if (fcg) {
+      bn = -S_cg[kFcgAlpha] * S_cg[kFcgZq0 + (par ^ 1)];
+      bd = S_cg[kFcgRz0 + (par ^ 1)];
+    } else {
+      bn = S_cg[kCgRz0 + par];
+      bd = S_cg[kCgRzPrev];
+    }
+    s_beta = (T)(bd != 0.0 ? bn / bd : 0.0);
     if (blockIdx.x == 0) {  // accumulators of the update kernel that follows
       S_cg[kCgRz0 + (par ^ 1)] = 0.0;
       S_cg[kCgRr0 + (par ^ 1)] = 0.0;
@@ -207,7 +215,7 @@ constexpr size_t patch_smem() {
 template <class K, class T, class S, class C, bool PQ, bool CGP = false>
 static void launch_patch(const chns_mesh* m, const DevParams& p, const CoefArgs<C>& cf,
                          const S* x, S* y, double* S_cg, cudaStream_t s, const S* z = nullptr,
-                         S* pout = nullptr, int par = 0) {
+                         S* pout = nullptr, int par = 0, int fcg = 0) {
   constexpr size_t smem = patch_smem<K, T>();
   static bool configured = false;  // per instantiation
   if (!configured) {
@@ -217,7 +225,7 @@ static void launch_patch(const chns_mesh* m, const DevParams& p, const CoefArgs<
   }
   note_launch();
   k_apply_patch<K, T, S, C, PQ, CGP><<<(unsigned)m->d.n_patch, kPatchElems, smem, s>>>(
-      m->d, p, cf, x, y, S_cg, par, z, pout);
+      m->d, p, cf, x, y, S_cg, par, fcg, z, pout);
 }
 
 // Reference (corner a, slot k) -> node reference with Dirichlet bit and its weight, or -1.
@@ -479,7 +487,8 @@ chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm
 
 chns_status apply_poisson_cg(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
                              const void* z, const void* p_old, void* p_new, void* y,
-                             chns_precision prec, double* S_cg, int par, cudaStream_t s) {
+                             chns_precision prec, double* S_cg, int par, cudaStream_t s,
+                             bool fcg) {
   chns_status st = check_coef(CHNS_OP_POISSON, coef);
   if (st != CHNS_OK) return st;
   const DevParams p = make_dev_params(*prm);
@@ -488,18 +497,18 @@ chns_status apply_poisson_cg(const chns_mesh* m, const chns_params* prm, const c
       launch_patch<PoissonK<double, double>, double, double, double, true, true>(
           m, p, coef_args<double>(coef), static_cast<const double*>(p_old),
           static_cast<double*>(y), S_cg, s, static_cast<const double*>(z),
-          static_cast<double*>(p_new), par);
+          static_cast<double*>(p_new), par, fcg);
       break;
     case CHNS_FP32:
       launch_patch<PoissonK<float, float>, float, float, float, true, true>(
           m, p, coef_args<float>(coef), static_cast<const float*>(p_old), static_cast<float*>(y),
-          S_cg, s, static_cast<const float*>(z), static_cast<float*>(p_new), par);
+          S_cg, s, static_cast<const float*>(z), static_cast<float*>(p_new), par, fcg);
       break;
     case CHNS_FP32_BF16COEF:
       launch_patch<PoissonK<float, __nv_bfloat16>, float, float, __nv_bfloat16, true, true>(
           m, p, coef_args<__nv_bfloat16>(coef), static_cast<const float*>(p_old),
           static_cast<float*>(y), S_cg, s, static_cast<const float*>(z), static_cast<float*>(p_new),
-          par);
+          par, fcg);
       break;
     default:
       set_error("apply: bad precision");

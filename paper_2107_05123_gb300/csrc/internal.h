@@ -139,15 +139,19 @@ chns_status apply_op(const chns_mesh* m, chns_operator op, const chns_params* pr
 // slots that the previous kernel of the iteration cleared (a kernel boundary orders them), so no
 // kernel waits for the last block of its grid.
 constexpr int kCgRz0 = 32, kCgRzPrev = 34, kCgPq0 = 35, kCgRr0 = 37;
-// flexible CG: r.z and alpha of the current iteration
-constexpr int kFcgRz = 4, kFcgAlpha = 5;
+// flexible CG: iteration k reads r.z of its iterate from kFcgRz0 + par, alpha from kFcgAlpha;
+// it accumulates z_new.q into kFcgZq0 + par and r_new.z_new into kFcgRz0 + (par ^ 1), and the
+// next apply forms beta = -alpha z_new.q / r.z (Polak-Ribiere).
+constexpr int kFcgAlpha = 5, kFcgZq0 = 40, kFcgRz0 = 42;
 // One fused CG step of the Poisson operator (iteration parity par): p_new = z + beta p_old with
-// beta = S[kCgRz0 + par] / S[kCgRzPrev] during the gather, y = A p_new (y zero on entry), and
+// beta = S[kCgRz0 + par] / S[kCgRzPrev] (fcg: -S[kFcgAlpha] S[kFcgZq0 + (par ^ 1)] /
+// S[kFcgRz0 + (par ^ 1)]) during the gather, y = A p_new (y zero on entry), and
 // S[kCgPq0 + par] += p_new.A p_new (cleared by the caller); clears S[kCgRz0 + (par ^ 1)] and
 // S[kCgRr0 + (par ^ 1)] for the update kernel that follows.
 chns_status apply_poisson_cg(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
                              const void* z, const void* p_old, void* p_new, void* y,
-                             chns_precision prec, double* S_cg, int par, cudaStream_t s);
+                             chns_precision prec, double* S_cg, int par, cudaStream_t s,
+                             bool fcg = false);
 chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
                     const chns_coef* coef, void* d, chns_precision prec, cudaStream_t s);
 // 2x2 nodal blocks of the CH Jacobian, d4 = [d_pp, d_pm, d_mp, d_mm] x n_nodes (FP64 or FP32)

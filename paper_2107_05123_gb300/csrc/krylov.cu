@@ -190,6 +190,18 @@ k_cg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __
   }
 }
 
+// *out += a.b (block sums added with an FP64 atomic; out cleared by an earlier kernel)
+template <class T>
+__global__ void __launch_bounds__(kVecThreads)
+k_dot_atomic(const T* __restrict__ a, const T* __restrict__ b, int64_t n, double* __restrict__ out) {
+  typename Acc<T>::type t = Acc<T>::zero();
+  GRID_LOOP(i, n) Acc<T>::fma(t, a[i], b[i]);
+  typename Acc<T>::type v[1] = {t};
+  double tot[1];
+  block_sum<1, kVecThreads>(v, tot);
+  if (threadIdx.x == 0) atomicAdd(out, tot[0]);
+}
+
 // p_new = z + beta p_old with beta = r.z / r.z_prev (operators whose apply does not fuse it);
 // clears the accumulators of the update that follows
 template <class T>
@@ -203,15 +215,14 @@ __global__ void k_cg_pupdate(const T* __restrict__ z, const T* __restrict__ p_ol
   GRID_LOOP(i, n) p_new[i] = z[i] + b * p_old[i];
 }
 
-// ---- flexible CG (Polak-Ribiere beta). S[kFcgRz] = r.z, S[kFcgAlpha] = alpha. The fused Poisson
-// apply forms p = z + beta p_old with beta = S[kCgRz0 + par] / S[kCgRzPrev], so the dot kernel
-// stores beta's numerator -alpha z_new.q (= z_new.(r_new - r_old)) and denominator r.z there.
-// k_fcg_update: alpha = r.z / p.q; x += alpha p; r -= alpha q; r.r added to the next parity slot
+// ---- flexible CG (Polak-Ribiere beta), slots of internal.h.
+// k_fcg_update: alpha = r.z / p.q; x += alpha p; r -= alpha q; r.r added to the next parity slot;
+// block 0 stores alpha and clears the accumulators of the dot kernel and of the next apply
 template <class T>
 __global__ void __launch_bounds__(kVecThreads)
 k_fcg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
              const T* __restrict__ q, int64_t n, double* __restrict__ S, int par) {
-  const T a = cg_ratio<T>(S, kFcgRz, kCgPq0 + par, true);
+  const T a = cg_ratio<T>(S, kFcgRz0 + par, kCgPq0 + par, true);
   typename Acc<T>::type v0 = Acc<T>::zero();
   GRID_LOOP(i, n) {
     x[i] += a * p[i];
@@ -227,17 +238,17 @@ k_fcg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
     if (blockIdx.x == 0) {
       S[kFcgAlpha] = (double)a;
       S[kCgPq0 + (par ^ 1)] = 0.0;
+      S[kFcgZq0 + par] = 0.0;
+      S[kFcgRz0 + (par ^ 1)] = 0.0;
     }
   }
 }
 
-// z.q and z.r; q cleared for the next apply. The last block (ticket) stores
-// S[kCgRz0 + (par ^ 1)] = -alpha z.q, S[kCgRzPrev] = r.z (old) and S[kFcgRz] = z.r (new).
+// z.q into kFcgZq0 + par and z.r into kFcgRz0 + (par ^ 1); q cleared for the next apply
 template <class T>
 __global__ void __launch_bounds__(kVecThreads)
 k_fcg_dots(const T* __restrict__ z, T* __restrict__ q, const T* __restrict__ r, int64_t n,
-           double* __restrict__ S, double* __restrict__ part, unsigned* __restrict__ counter,
-           int par) {
+           double* __restrict__ S, int par) {
   typename Acc<T>::type v0 = Acc<T>::zero(), v1 = Acc<T>::zero();
   GRID_LOOP(i, n) {
     const T zi = z[i];
@@ -246,13 +257,20 @@ k_fcg_dots(const T* __restrict__ z, T* __restrict__ q, const T* __restrict__ r, 
     Acc<T>::fma(v1, zi, r[i]);
   }
   typename Acc<T>::type v[2] = {v0, v1};
-  __shared__ double tot[2];
-  if (block_reduce_ticket<2, kVecThreads>(v, part, kRedSlots, counter, 0, tot) &&
-      threadIdx.x == 0) {
-    S[kCgRz0 + (par ^ 1)] = -S[kFcgAlpha] * tot[0];
-    S[kCgRzPrev] = S[kFcgRz];
-    S[kFcgRz] = tot[1];
+  double tot[2];
+  block_sum<2, kVecThreads>(v, tot);
+  if (threadIdx.x == 0) {
+    atomicAdd(S + kFcgZq0 + par, tot[0]);
+    atomicAdd(S + kFcgRz0 + (par ^ 1), tot[1]);
   }
+}
+
+// first FCG direction: p = z (beta = -0 x 0 / 1); p.Ap accumulator cleared
+__global__ void k_fcg_init(double* S) {
+  S[kFcgAlpha] = 0.0;
+  S[kFcgZq0 + 1] = 0.0;
+  S[kFcgRz0 + 1] = 1.0;
+  S[kCgPq0] = 0.0;
 }
 
 // z += omega dinv (r - w)  (w = A z)
@@ -260,13 +278,6 @@ template <class T>
 __global__ void k_smooth(T* __restrict__ z, const T* __restrict__ r, const T* __restrict__ w,
                          const T* __restrict__ dinv, T omega, int64_t n) {
   GRID_LOOP(i, n) z[i] += omega * dinv[i] * (r[i] - w[i]);
-}
-
-// first FCG direction: p = z (beta = 0 / 1); p.Ap accumulator cleared
-__global__ void k_fcg_init(double* S) {
-  S[kCgRz0] = 0.0;
-  S[kCgRzPrev] = 1.0;
-  S[kCgPq0] = 0.0;
 }
 
 // ---- GMRES
@@ -534,8 +545,7 @@ chns_status cg_iteration(const Ctx& c, cudaStream_t s, T* x, T* r, T* z, const T
     st = apply_T<T>(cs, p_new, q);
     if (st != CHNS_OK) return st;
     note_launch();
-    k_dot<T, T><<<rg, kVecThreads, 0, s>>>(p_new, q, n, c.m->ws.red, c.m->ws.counter,
-                                            c.S + kCgPq0 + par);
+    k_dot_atomic<T><<<rg, kVecThreads, 0, s>>>(p_new, q, n, c.S + kCgPq0 + par);
   }
   note_launch();
   k_cg_update<T><<<rg, kVecThreads, 0, s>>>(x, r, z, p_new, q, dinv, n, c.S, fused, par);
@@ -745,7 +755,7 @@ chns_status fcg(const Ctx& c, const T* b, T* x, const T* dinv, chns_learned* L, 
   st = precond(c.s, kCgRr0);
   if (st != CHNS_OK) return st;
   note_launch();
-  k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, z, n, c.m->ws.red, c.m->ws.counter, c.S + kFcgRz);
+  k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, z, n, c.m->ws.red, c.m->ws.counter, c.S + kFcgRz0);
   note_launch();
   k_fcg_init<<<1, 1, 0, c.s>>>(c.S);
   CHNS_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), c.s));
@@ -760,16 +770,16 @@ chns_status fcg(const Ctx& c, const T* b, T* x, const T* dinv, chns_learned* L, 
     T* p_new = pb[par ^ 1];
     chns_status e;
     if (sizeof(T) == sizeof(double))
-      e = apply_poisson_cg(c.m, c.prm, c.coef64, z, p_old, p_new, q, CHNS_FP64, c.S, par, s);
+      e = apply_poisson_cg(c.m, c.prm, c.coef64, z, p_old, p_new, q, CHNS_FP64, c.S, par, s, true);
     else
-      e = apply_poisson_cg(c.m, c.prm, &c.coefR, z, p_old, p_new, q, c.inner, c.S, par, s);
+      e = apply_poisson_cg(c.m, c.prm, &c.coefR, z, p_old, p_new, q, c.inner, c.S, par, s, true);
     if (e != CHNS_OK) return e;
     note_launch();
     k_fcg_update<T><<<rg, kVecThreads, 0, s>>>(x, r, p_new, q, n, c.S, par);
     e = precond(s, kCgRr0 + (par ^ 1));
     if (e != CHNS_OK) return e;
     note_launch();
-    k_fcg_dots<T><<<rg, kVecThreads, 0, s>>>(z, q, r, n, c.S, c.m->ws.red, c.m->ws.counter, par);
+    k_fcg_dots<T><<<rg, kVecThreads, 0, s>>>(z, q, r, n, c.S, par);
     return CHNS_OK;
   };
   return iterate<T>(c, step, x, tol_abs, max_it, chunk, rr, iters, rnorm, snap, stall);

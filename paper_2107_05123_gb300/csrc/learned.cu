@@ -788,6 +788,16 @@ __global__ void k_scale_f(const float* __restrict__ a, float* __restrict__ b, in
     b[i] = a[i] * f;
 }
 
+// b = a f / max(1, *loss): a pair whose correction makes the error worse than no correction
+// (relative energy above 1) contributes a gradient of bounded size (that of log(loss))
+__global__ void k_scale_grad(const float* __restrict__ a, float* __restrict__ b, int64_t n, float f,
+                             const float* __restrict__ loss) {
+  const float g = f / fmaxf(1.f, *loss);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i] * g;
+}
+
 __global__ void k_square_sum(const float* __restrict__ a, int64_t n, double* __restrict__ part) {
   double v[1] = {0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -1419,10 +1429,11 @@ chns_status chns_learned_train(chns_learned* L, const chns_mesh* m, const chns_p
     if (st != CHNS_OK) return st;
     note_launch();
     k_dot_acc<<<nb, kThreads, 0, s>>>(L->d32, L->w32, N, (float)(1.0 / eae), L->loss_dev + it);
-    // dL/d(out) = -2 sc P_g^T (A d) / e^T A e
+    // dL/d(out) = -2 sc P_g^T (A d) / e^T A e, divided by the loss where it exceeds 1
     restrict_to<float>(L, m, L->w32, L->g_t, s);
     note_launch();
-    k_scale_f<<<grid_for(L->nv), kThreads, 0, s>>>(L->g_t, L->g_r, L->nv, (float)(-2.0 * sc / eae));
+    k_scale_grad<<<grid_for(L->nv), kThreads, 0, s>>>(L->g_t, L->g_r, L->nv,
+                                                      (float)(-2.0 * sc / eae), L->loss_dev + it);
     st = backward(L, nullptr, 0.f, L->g_r, nullptr, s);
     if (st != CHNS_OK) return st;
     adam(L, L->G, lr, s);
