@@ -64,6 +64,7 @@ struct Workspace {
   void* coef16 = nullptr;      // bf16 copies (5 fields)
   double* coef64 = nullptr;    // FP64 step coefficients (phi~, u_hat x3, mu~ + scratch)
   double* part_big = nullptr;  // per-block partials of element-level reductions (n_elem/64+64)
+  double* md_part = nullptr;   // GMRES multi-dot partials: [restart + 2][kMdMaxBlocks]
 };
 
 }  // namespace chns
@@ -126,6 +127,7 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 constexpr int kNumVec64 = 16;
 constexpr int kNumVec32 = 10;
 constexpr int kRedSlots = 4096;   // partial sums per reduction
+constexpr int kMdMaxBlocks = 1024; // blocks of the GMRES multi-dot
 constexpr int kScalarBase = 3 * 4096;  // scalars stored after three partial arrays
 
 // ---- apply dispatch (apply.cu)

@@ -20,7 +20,6 @@ namespace chns {
 
 constexpr int kVecThreads = 256;
 constexpr int kMdBlocks = 256;  // blocks per multi-dot row (partials: rows x kMdBlocks)
-constexpr int kMd2Blocks = 256;  // blocks of the one-pass multi-dot (partials: rows x blocks)
 
 // device scalar slots (offsets from ws.red + kScalarBase)
 enum Slot { S_RZ0 = 0, S_RZ1 = 1, S_PQ = 2, S_RR = 3, S_TMP = 8, S_AUX = 16, S_MD = 64 };
@@ -322,51 +321,57 @@ __global__ void k_gmres_update_b2(const T* __restrict__ V, int64_t ld, int nk,
 // Multi-dot of rows V_0..V_{nk-1} with w, plus w.w as row nk. Each block stages a slice of w in
 // shared memory once and sweeps all rows over it (the rows are read once, w once); per-warp sums
 // accumulate in shared memory across the block's slices; partials land in part[k][blockIdx.x].
-constexpr int kMd2Threads = 256, kMd2Slice = 2048, kMd2MaxRows = CHNS_GMRES_MAX_RESTART + 2;
-template <class T>
+constexpr int kMd2Threads = 256;
+// GMRES multi-dot: h_k = V_k . w for k < nk and h_nk = w.w in one pass over w. Every thread
+// keeps all nk + 1 running sums in registers over its few elements (FP32 products, one element
+// per vector per iteration, so each warp reads 128 contiguous bytes of every basis vector), then
+// the sums go through double-float warp reductions and FP64 across warps; block partials land
+// in part[k * gridDim.x + block] for k_multidot_final.
+template <class T, int NK>
 __global__ void __launch_bounds__(kMd2Threads)
 k_multidot2(const T* __restrict__ V, int64_t ld, int nk, const T* __restrict__ w, int64_t n,
             double* __restrict__ part) {
-  __shared__ T wsl[kMd2Slice];
-  __shared__ double acc[kMd2MaxRows][kMd2Threads / 32];
+  __shared__ double accs[NK + 1][kMd2Threads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = threadIdx.x; k < (nk + 1) * (kMd2Threads / 32); k += kMd2Threads)
-    acc[k / (kMd2Threads / 32)][k % (kMd2Threads / 32)] = 0.0;
-  const int64_t nsl = (n + kMd2Slice - 1) / kMd2Slice;
-  for (int64_t sl = blockIdx.x; sl < nsl; sl += gridDim.x) {
-    const int64_t i0 = sl * kMd2Slice;
-    __syncthreads();
-    for (int t = threadIdx.x; t < kMd2Slice; t += kMd2Threads)
-      wsl[t] = (i0 + t < n) ? w[i0 + t] : T(0);
-    __syncthreads();
-    for (int k = 0; k <= nk; ++k) {
-      typename Acc<T>::type sum = Acc<T>::zero();
-      if (k < nk) {
-        const T* vk = V + (int64_t)k * ld + i0;
-        for (int t = threadIdx.x; t < kMd2Slice; t += kMd2Threads)
-          if (i0 + t < n) Acc<T>::fma(sum, vk[t], wsl[t]);
-      } else {
-        for (int t = threadIdx.x; t < kMd2Slice; t += kMd2Threads) Acc<T>::fma(sum, wsl[t], wsl[t]);
-      }
-      const auto d = warp_sum(sum);
-      if (lane == 0) acc[k][warp] += acc_value(d);
+  T acc[NK + 1];
+#pragma unroll
+  for (int k = 0; k <= NK; ++k) acc[k] = T(0);
+  GRID_LOOP(i, n) {
+    const T wi = w[i];
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+      if (k < nk) acc[k] += V[(int64_t)k * ld + i] * wi;
+    acc[NK] += wi * wi;
+  }
+#pragma unroll
+  for (int k = 0; k <= NK; ++k) {
+    if (k < nk || k == NK) {
+      typename Acc<T>::type a = Acc<T>::zero();
+      Acc<T>::add(a, acc[k]);
+      const auto d = warp_sum(a);
+      if (lane == 0) accs[k][warp] = acc_value(d);
     }
   }
   __syncthreads();
   for (int k = threadIdx.x; k <= nk; k += kMd2Threads) {
+    const int src = k < nk ? k : NK;
     double t = 0.0;
 #pragma unroll
-    for (int q = 0; q < kMd2Threads / 32; ++q) t += acc[k][q];
+    for (int q = 0; q < kMd2Threads / 32; ++q) t += accs[src][q];
     part[(int64_t)k * gridDim.x + blockIdx.x] = t;
   }
 }
 
 // w = (w - sum_k h_k V_k) * scale, with scale = 1/sqrt(h[nk] - sum_k h_k^2) when NORMALISE
-// (h[nk] = w.w from the same multi-dot: Pythagoras for the classical Gram-Schmidt step).
+// (h[nk] = w.w from the same multi-dot: Pythagoras for the classical Gram-Schmidt step). The
+// update runs in the vector type (FP32 for FP32 vectors: FP64 arithmetic per element and basis
+// vector would bound this kernel on GB300), the coefficients from shared memory.
 template <class T, bool NORMALISE>
 __global__ void k_orth_update_scale(const T* __restrict__ V, int64_t ld, int nk,
                                     const double* __restrict__ h, T* __restrict__ w, int64_t n) {
-  __shared__ double s_scale;
+  __shared__ T hs[CHNS_GMRES_MAX_RESTART + 1];
+  __shared__ T s_scale;
+  if (threadIdx.x < nk) hs[threadIdx.x] = (T)h[threadIdx.x];
   if (threadIdx.x == 0) {
     double sc = 1.0;
     if (NORMALISE) {
@@ -375,14 +380,14 @@ __global__ void k_orth_update_scale(const T* __restrict__ V, int64_t ld, int nk,
       const double r = h[nk] - hh;
       sc = r > 0.0 ? rsqrt(r) : 1.0;
     }
-    s_scale = sc;
+    s_scale = (T)sc;
   }
   __syncthreads();
-  const double sc = s_scale;
+  const T sc = s_scale;
   GRID_LOOP(i, n) {
-    double acc = (double)w[i];
-    for (int k = 0; k < nk; ++k) acc -= h[k] * (double)V[(int64_t)k * ld + i];
-    w[i] = (T)(acc * sc);
+    T acc = w[i];
+    for (int k = 0; k < nk; ++k) acc -= hs[k] * V[(int64_t)k * ld + i];
+    w[i] = acc * sc;
   }
 }
 
@@ -785,6 +790,23 @@ chns_status fcg(const Ctx& c, const T* b, T* x, const T* dinv, chns_learned* L, 
   return iterate<T>(c, step, x, tol_abs, max_it, chunk, rr, iters, rnorm, snap, stall);
 }
 
+// multi-dot launch with the register count fitted to the number of basis vectors
+template <class T>
+void multidot(const T* V, int64_t ld, int nk, const T* w, int64_t n, unsigned grid, double* part,
+              cudaStream_t s) {
+  note_launch();
+  if (nk <= 8)
+    k_multidot2<T, 8><<<grid, kMd2Threads, 0, s>>>(V, ld, nk, w, n, part);
+  else if (nk <= 16)
+    k_multidot2<T, 16><<<grid, kMd2Threads, 0, s>>>(V, ld, nk, w, n, part);
+  else if (nk <= 24)
+    k_multidot2<T, 24><<<grid, kMd2Threads, 0, s>>>(V, ld, nk, w, n, part);
+  else if (nk <= 32)
+    k_multidot2<T, 32><<<grid, kMd2Threads, 0, s>>>(V, ld, nk, w, n, part);
+  else
+    k_multidot2<T, CHNS_GMRES_MAX_RESTART + 1><<<grid, kMd2Threads, 0, s>>>(V, ld, nk, w, n, part);
+}
+
 // Right-preconditioned restarted GMRES with classical Gram-Schmidt and one re-orthogonalisation
 // pass; the second pass also returns w.w so that the new norm needs no extra reduction.
 template <class T>
@@ -834,12 +856,12 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, do
       // classical Gram-Schmidt: h = V^T w and w.w in one pass; a second pass only when the
       // new vector lost more than half its norm to the projection (cancellation)
       const unsigned md2 = (unsigned)std::max<int64_t>(
-          1, std::min<int64_t>((n + kMd2Slice - 1) / kMd2Slice, kMd2Blocks));
+          1, std::min<int64_t>((n + 2 * kMd2Threads - 1) / (2 * kMd2Threads),
+                               std::min<int64_t>(kMdMaxBlocks, 4 * (int64_t)c.m->sm_count)));
       int nk = j + 1;
+      multidot(V, ld, nk, w, n, md2, c.m->ws.md_part, c.s);
       note_launch();
-      k_multidot2<T><<<md2, kMd2Threads, 0, c.s>>>(V, ld, nk, w, n, c.m->ws.red);
-      note_launch();
-      k_multidot_final<<<nk + 1, kVecThreads, 0, c.s>>>(c.m->ws.red, (int)md2, hdev);
+      k_multidot_final<<<nk + 1, kVecThreads, 0, c.s>>>(c.m->ws.md_part, (int)md2, hdev);
       CHNS_CUDA(cudaGetLastError());
       st = read_dev(c.m, hdev, h.data(), nk + 1, c.s);
       if (st != CHNS_OK) return st;
@@ -854,10 +876,9 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, do
         // re-orthogonalise: w -= V h, then a second multi-dot on the updated vector
         note_launch();
         k_orth_update_scale<T, false><<<vg, kVecThreads, 0, c.s>>>(V, ld, nk, hdev, w, n);
+        multidot(V, ld, nk, w, n, md2, c.m->ws.md_part, c.s);
         note_launch();
-        k_multidot2<T><<<md2, kMd2Threads, 0, c.s>>>(V, ld, nk, w, n, c.m->ws.red);
-        note_launch();
-        k_multidot_final<<<nk + 1, kVecThreads, 0, c.s>>>(c.m->ws.red, (int)md2, hdev);
+        k_multidot_final<<<nk + 1, kVecThreads, 0, c.s>>>(c.m->ws.md_part, (int)md2, hdev);
         CHNS_CUDA(cudaGetLastError());
         st = read_dev(c.m, hdev, h.data(), nk + 1, c.s);
         if (st != CHNS_OK) return st;
