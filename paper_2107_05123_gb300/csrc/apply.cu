@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(MeshDev m, DevParams p,
 // With PQ the block sums of the element energies x_e . A_e x_e (summing to x^T A x) are added to
 // S_cg[kCgPq0 + par] with an FP64 atomic.
 template <class K, class T, class S, class C, bool PQ, bool CGP>
-__global__ void __launch_bounds__(kPatchElems)
+__global__ void __launch_bounds__(kPatchElems, K::MIN_CTAS)
 k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S* __restrict__ y,
               double* __restrict__ S_cg, int par, int fcg, const S* __restrict__ zcg,
               S* __restrict__ pout) {
