@@ -498,8 +498,8 @@ def run_reference(args):
 
 
 def run_apply_only(args):
-    """Profiling aid: the roofline kernel alone (Poisson apply, BF16 coefficients, FP32 vectors)
-    on the bench mesh, a few launches, with one timing line."""
+    """Profiling aid: the roofline kernel alone (Poisson apply, FP32 coefficients and vectors)
+    on the bench mesh, a few launches from a cold L2, with one timing line."""
     import torch
 
     from chns_workloads import configs
@@ -510,7 +510,7 @@ def run_apply_only(args):
     mesh = Mesh(w.anchors, w.levels, w.extent)
     f0 = w.init(mesh.node_xyz)
     prm = capi.make_params(w.params.as_dict())
-    coef = capi.make_coef((torch.as_tensor(f0["phi"], device="cuda") + 1.0).to(torch.bfloat16))
+    coef = capi.make_coef(torch.as_tensor(f0["phi"], device="cuda").float())
     x = torch.randn(mesh.n_nodes, device="cuda")
     y = torch.empty_like(x)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -519,7 +519,7 @@ def run_apply_only(args):
         flush.fill_(1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        capi.chns_apply_poisson(mesh.handle, prm, coef, x, y, capi.FP32_BF16COEF)
+        capi.chns_apply_poisson(mesh.handle, prm, coef, x, y, capi.FP32)
         e1.record()
         torch.cuda.synchronize()
         if i >= args.warmup:
