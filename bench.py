@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Poisson+PCG DOFs/s and time/step vs plain FP64 GPU at 1e-8 residual; HBM frac"
 UNIT = "DOFs/s"
 WORKLOAD = "rising_drop_levels5-8"
+APPLY_DRAM_BYTES = 11.58e6
 
 
 def _peaks():
@@ -105,6 +106,26 @@ def _dist():
 
 
 # --------------------------------------------------------------------------- our arm
+def field_errors(final_fields, n_steps):
+    """Relative L2 difference per field between the reduced-precision paths and the all-FP64
+    path after the same number of steps from the same initial state."""
+    import numpy as np
+
+    ref = final_fields.get("fp64")
+    if ref is None:
+        return None
+    out = {"steps": n_steps}
+    for label, f in final_fields.items():
+        if label == "fp64":
+            continue
+        e = {}
+        for k in ("phi", "mu", "p"):
+            e[k] = float(np.linalg.norm(f[k] - ref[k]) / max(np.linalg.norm(ref[k]), 1e-300))
+        e["u"] = float(np.linalg.norm(f["u"] - ref["u"]) / max(np.linalg.norm(ref["u"]), 1e-300))
+        out[label] = e
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -168,6 +189,7 @@ def run_ours(args):
             pg.all_reduce(t, op=pg.ReduceOp.MAX)
             tmax, pp_ms = float(t[0]), float(t[1])
         last = stats[-1]
+        final_fields[label] = ds.host()
         return dict(label=label, ms_per_step=tmax / args.steps,
                     value=ws * N * pp_n / (pp_ms * 1e-3),
                     pp_ms_per_solve=pp_ms / pp_n, pp_iters_per_solve=pp_it / pp_n,
@@ -176,6 +198,8 @@ def run_ours(args):
                     newton_its=list(last.newton_its),
                     mass_drift=abs(last.phi_mass_after - last.phi_mass_before),
                     pp_refinements=last.pp[1].refinements)
+
+    final_fields = {}
 
     with ClockSampler(local) as clk:
         headline = plain = bf16 = None
@@ -215,7 +239,10 @@ def run_ours(args):
     alg_bytes = N * (4 + 4 + 4) + E * 33 + H * 16
     peak, peak_kind = _peaks()
     achieved = alg_bytes / t_apply / 1e9
-    traffic = args.traffic  # dram bytes per launch from an ncu capture, when supplied
+    # DRAM bytes of one launch from an ncu capture of this kernel on this workload
+    # (dram__bytes.sum.per_second x gpu__time_duration: 667.8 GB/s x 17.344 us; profiles/
+    # poisson_apply_fp32_rising_drop.md); --traffic overrides it
+    traffic = args.traffic if args.traffic is not None else APPLY_DRAM_BYTES
 
     # ---- end to end: one Poisson solve through the C ABI with pinned host buffers
     b_dev = torch.zeros(N, dtype=torch.float64, device="cuda")
@@ -271,6 +298,7 @@ def run_ours(args):
                                   "pp_iters_per_solve": bf16["pp_iters_per_solve"]},
             "speedup_vs_plain_fp64": {"pp": headline["value"] / plain["value"],
                                       "step": plain["ms_per_step"] / headline["ms_per_step"]},
+            "field_error_vs_fp64": field_errors(final_fields, args.warmup + args.steps),
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(2 * N * 8),
                     "d2h_bytes_per_step": int(N * 8)},
             "roofline": {"kernel": "k_apply_patch<PoissonK<float,float>>", "bound": "hbm",
