@@ -13,6 +13,9 @@ bf16_coefficients = the headline path with bfloat16 coefficient storage for Pois
 e2e         = one Poisson solve through the C ABI from pinned host buffers (copies timed);
 roofline    = the dominant apply kernel timed alone from a cold L2 (algorithmic bytes / time);
 cpu_baseline= the FP64 CPU oracle (assembled matrix + Jacobi-PCG) on a bounded sample;
+large_interface = the Rayleigh-Taylor workload at scale (~7e6 leaves): one step of the
+              BF16-coefficient path and of the FP64 path, their per-field difference, and the
+              Poisson apply alone (see run_large);
 learned     = the learned coarse correction for the pressure-Poisson solve on the 8-drop
               workload: pairs from time steps, training, and the solves of one more step with
               and without it (untimed setup; see run_learned).
@@ -271,6 +274,12 @@ def run_ours(args):
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_val = ws * N / (statistics.mean(e2e_ms) * 1e-3)
 
+    large = None
+    if rank == 0 and not args.no_large:
+        try:
+            large = run_large(args)
+        except Exception as e:  # the headline line is printed whatever happens here
+            large = {"error": f"{type(e).__name__}: {e}"}
     learned = None
     if rank == 0 and not args.no_learned:
         try:
@@ -306,6 +315,7 @@ def run_ours(args):
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "alg_bytes": int(alg_bytes), "ms": t_apply * 1e3},
             "cpu_baseline": cpu,
+            "large_interface": large,
             "learned": learned,
             "clocks": clocks,
             "gpu_launches": headline["launches"],
@@ -313,6 +323,80 @@ def run_ours(args):
         print(json.dumps(line))
     if pg:
         pg.destroy_process_group()
+
+
+def run_large(args):
+    """The Rayleigh-Taylor interface at scale (box 1 x 4 x 1, levels 6-10 refined in the
+    interface band, Cn 0.005, density ratio 3, Re 1000): one step of the BF16-coefficient path
+    (FP32 applies, FP64 refinement) and one of the all-FP64 path from the same state, the
+    per-field difference, and the Poisson apply timed alone from a cold L2 (HBM regime)."""
+    import numpy as np
+    import torch
+
+    from chns_workloads import configs
+    from paper_2107_05123_gb300 import capi
+    from paper_2107_05123_gb300.session import DeviceState, Mesh, default_step_params
+
+    t_all = time.perf_counter()
+    w = configs.rayleigh_taylor(6, 10, 0.005)
+    t0 = time.perf_counter()
+    mesh = Mesh(w.anchors, w.levels, w.extent)
+    t_mesh = time.perf_counter() - t0
+    N, E, H = mesh.n_nodes, mesh.n_elem, mesh.n_hanging
+    f0 = w.init(mesh.node_xyz)
+    prm = capi.make_params(w.params.as_dict())
+    out = {"workload": "rayleigh_taylor_levels6-10", "n_elem": int(E), "n_nodes": int(N),
+           "n_hanging": int(H), "mesh_create_s": round(t_mesh, 1)}
+    fields = {}
+    for label, inner, warm in (("fp32_bf16coef_fp64refine", capi.FP32_BF16COEF, 1),
+                               ("fp64", capi.FP64, 0)):
+        ds = DeviceState(dict(phi=f0["phi"], mu=f0["mu"], u=f0["u"], p=f0["p"]))
+        sp = default_step_params(rtol=1e-8, inner=inner, pp_check_every=8)
+        sp.vp.max_it = 20000
+        try:
+            if warm:  # compile-time state and graph caches of the path, from a copy
+                capi.chns_step(mesh.handle, DeviceState(dict(phi=f0["phi"], mu=f0["mu"],
+                                                             u=f0["u"], p=f0["p"])).c, prm, sp)
+            torch.cuda.synchronize()
+            st = capi.chns_step(mesh.handle, ds.c, prm, sp)
+        except capi.ChnsError as e:
+            out[label] = {"error": str(e)}
+            continue
+        fields[label] = ds.host()
+        out[label] = dict(ms_step=round(st.ms_total, 2),
+                          phases_ms=dict(ch=round(st.ms_ch, 2), vp=round(st.ms_vp, 2),
+                                         pp=round(st.ms_pp, 2), vu=round(st.ms_vu, 2)),
+                          pp_iters=[st.pp[l].iterations for l in range(2)],
+                          pp_ms=[round(st.pp[l].ms, 3) for l in range(2)],
+                          pp_dofs_per_s=2 * N / (1e-3 * (st.pp[0].ms + st.pp[1].ms)))
+    if len(fields) == 2:
+        a, b = fields["fp32_bf16coef_fp64refine"], fields["fp64"]
+        out["field_error_vs_fp64"] = {
+            k: float(np.linalg.norm(a[k] - b[k]) / max(np.linalg.norm(b[k]), 1e-300))
+            for k in ("phi", "mu", "u", "p")}
+    # the Poisson apply alone, FP32, from a cold L2
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    c32 = capi.make_coef(torch.as_tensor(f0["phi"], device="cuda").float())
+    x32 = torch.randn(N, device="cuda", dtype=torch.float32)
+    y32 = torch.empty_like(x32)
+    ts = []
+    for i in range(8):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        capi.chns_apply_poisson(mesh.handle, prm, c32, x32, y32, capi.FP32)
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= 3:
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+    alg = N * 12 + E * 33 + H * 16
+    peak, kind = _peaks()
+    ach = alg / statistics.mean(ts) / 1e9
+    out["poisson_apply_fp32"] = {"ms": round(statistics.mean(ts) * 1e3, 4), "alg_bytes": int(alg),
+                                 "achieved_gbs": ach, "peak_gbs": peak, "peak_kind": kind,
+                                 "frac": ach / peak}
+    out["wall_s"] = round(time.perf_counter() - t_all, 1)
+    return out
 
 
 def run_learned(args):
@@ -605,6 +689,8 @@ def main():
                     help="time only one path and print a detail line (profiling runs)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the roofline kernel from an ncu capture")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the Rayleigh-Taylor workload at scale (~7e6 leaves)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-preconditioner measurement (8-drop workload)")
     ap.add_argument("--learned-steps", type=int, default=3,
@@ -612,13 +698,16 @@ def main():
     ap.add_argument("--learned-iters", type=int, default=6000, help="training iterations")
     ap.add_argument("--learned-lr", type=float, default=3e-4)
     ap.add_argument("--learned-grid", type=int, default=64, help="grid size D of the network")
-    ap.add_argument("--mode", choices=["bench", "apply", "pp"], default="bench",
-                    help="apply / pp: time only the roofline kernel / the Poisson solve (profiling)")
+    ap.add_argument("--mode", choices=["bench", "apply", "pp", "large"], default="bench",
+                    help="apply / pp: time only the roofline kernel / the Poisson solve "
+                         "(profiling); large: only the Rayleigh-Taylor workload")
     args = ap.parse_args()
     if args.mode == "apply":
         run_apply_only(args)
     elif args.mode == "pp":
         run_pp_only(args)
+    elif args.mode == "large":
+        print(json.dumps(run_large(args)))
     elif args.impl == "reference":
         run_reference(args)
     else:
