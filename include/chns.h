@@ -77,7 +77,17 @@ typedef enum { CHNS_KSP_CG = 0, CHNS_KSP_GMRES = 1, CHNS_KSP_FCG = 2 } chns_ksp;
  * (phi, mu) blocks. LEARNED (with CHNS_KSP_FCG on POISSON): the coarse correction c(r) of a
  * trained network (see chns_learned below) followed by one damped Jacobi step on what it
  * leaves, z = c + omega D^-1 (r - A c) with omega = 2/3. */
-typedef enum { CHNS_PC_NONE = 0, CHNS_PC_JACOBI = 1, CHNS_PC_LEARNED = 2 } chns_pc;
+/* CHEBYSHEV (POISSON, with CG or FCG): z = p(D^-1 A) D^-1 r, `restart` (1..16) steps of the
+ * Chebyshev iteration on [lmax/30, lmax] with lmax = 1.1 x the largest eigenvalue of D^-1 A
+ * from 15 power iterations at the start of the solve (in the precision of the iteration);
+ * restart - 1 extra applies per iteration. A fixed SPD preconditioner (as long as lmax bounds
+ * the spectrum), run through the flexible-CG driver. */
+typedef enum {
+  CHNS_PC_NONE = 0,
+  CHNS_PC_JACOBI = 1,
+  CHNS_PC_LEARNED = 2,
+  CHNS_PC_CHEBYSHEV = 3
+} chns_pc;
 
 typedef struct chns_mesh chns_mesh;   /* opaque; owns device tables and workspace */
 typedef struct chns_learned chns_learned;  /* opaque; learned coarse correction (below) */
@@ -199,7 +209,7 @@ typedef struct {
   int32_t pc;               /* chns_pc */
   double rtol;
   int32_t max_it;           /* total Krylov iterations over all refinement cycles */
-  int32_t restart;          /* GMRES restart length, 1..CHNS_GMRES_MAX_RESTART */
+  int32_t restart;          /* GMRES restart length, 1..CHNS_GMRES_MAX_RESTART; Chebyshev degree */
   int32_t inner_precision;  /* chns_precision */
   double inner_rtol;        /* FP32 modes: relative tolerance of each correction solve */
   int32_t max_refine;       /* FP32 modes: maximum refinement cycles */

@@ -7,6 +7,9 @@ TEST INFRASTRUCTURE ONLY (see the package header).
   are projected to discrete mean zero (pure-Neumann pressure, reading R7).
 * ``dirichlet``: row/column elimination with identity rows for velocity (H^1_0, Sec. 4).
 * ``direct`` and ``gmres``: library sparse LU (SuperLU) and GMRES used as solver steps.
+* ``chebyshev_precond``: the Chebyshev iteration for D^-1 A z = D^-1 r from z = 0 on an interval
+  [lmin, lmax] (three-term recurrence), i.e. z = p(D^-1 A) D^-1 r; the polynomial preconditioner
+  beside Jacobi in the build's Krylov row (not in the paper, whose PETSc solves use AMG/ASM).
 * ``newton``: plain Newton on the CH residual (Appendix A uses Newton; Sec. 6.2 reports one
   iteration at the time steps used).
 
@@ -88,3 +91,18 @@ def newton(residual, jacobian, x0, rtol=1e-10, atol=1e-13, maxit=20, linsolve=di
         F = residual(x)
         its += 1
     return x, its, float(np.linalg.norm(F))
+
+
+def chebyshev_precond(A, dinv, r, lmin, lmax, degree):
+    """z after `degree` Chebyshev steps for D^-1 A z = D^-1 r from z = 0 on [lmin, lmax]."""
+    theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    sigma = theta / delta
+    rho_old = 1.0 / sigma
+    d = dinv * r / theta
+    z = d.copy()
+    for _ in range(1, degree):
+        rho = 1.0 / (2.0 * sigma - rho_old)
+        d = rho * rho_old * d + (2.0 * rho / delta) * dinv * (r - A @ z)
+        z = z + d
+        rho_old = rho
+    return z

@@ -29,7 +29,7 @@ OP_POISSON, OP_MASS, OP_CH, OP_MOMENTUM = 0, 1, 2, 3
 OP_NCOMP = {OP_POISSON: 1, OP_MASS: 3, OP_CH: 2, OP_MOMENTUM: 3}
 # chns_ksp / chns_pc
 KSP_CG, KSP_GMRES, KSP_FCG = 0, 1, 2
-PC_NONE, PC_JACOBI, PC_LEARNED = 0, 1, 2
+PC_NONE, PC_JACOBI, PC_LEARNED, PC_CHEBYSHEV = 0, 1, 2, 3
 
 
 class ChnsError(RuntimeError):

@@ -557,6 +557,95 @@ chns_status cg_iteration(const Ctx& c, cudaStream_t s, T* x, T* r, T* z, const T
   return CHNS_OK;
 }
 
+// ---- Chebyshev polynomial preconditioner: `degree` steps of the Chebyshev iteration for
+// D^-1 A z = D^-1 r from z = 0 on the interval [lmin, lmax] = [theta - delta, theta + delta]
+// (three-term recurrence with rho_k = 1 / (2 sigma - rho_{k-1}), sigma = theta / delta), i.e.
+// z = p(D^-1 A) D^-1 r with p the scaled Chebyshev polynomial; SPD while lmax bounds the
+// spectrum of D^-1 A.
+struct Cheb {
+  double theta = 0.0, delta = 0.0;
+  int degree = 0;
+};
+
+template <class T>
+__global__ void k_cheb_init(const T* __restrict__ dinv, const T* __restrict__ r, T* __restrict__ z,
+                            T* __restrict__ d, T f, int64_t n) {
+  GRID_LOOP(i, n) {
+    const T v = f * dinv[i] * r[i];
+    z[i] = v;
+    d[i] = v;
+  }
+}
+
+template <class T>
+__global__ void k_cheb_step(const T* __restrict__ dinv, const T* __restrict__ r,
+                            const T* __restrict__ w, T* __restrict__ z, T* __restrict__ d, T a,
+                            T b, int64_t n) {
+  GRID_LOOP(i, n) {
+    const T di = a * d[i] + b * dinv[i] * (r[i] - w[i]);
+    d[i] = di;
+    z[i] += di;
+  }
+}
+
+template <class T>
+chns_status cheb_apply(const Ctx& c, cudaStream_t s, const Cheb& ch, const T* dinv, const T* r,
+                       T* z, T* w, T* d) {
+  const unsigned vg = vgrid(c.m, c.n);
+  const double sigma = ch.theta / ch.delta;
+  double rho_old = 1.0 / sigma;
+  note_launch();
+  k_cheb_init<T><<<vg, kVecThreads, 0, s>>>(dinv, r, z, d, (T)(1.0 / ch.theta), c.n);
+  Ctx cs = c;
+  cs.s = s;
+  for (int i = 1; i < ch.degree; ++i) {
+    const double rho = 1.0 / (2.0 * sigma - rho_old);
+    chns_status e = apply_T<T>(cs, z, w);
+    if (e != CHNS_OK) return e;
+    note_launch();
+    k_cheb_step<T><<<vg, kVecThreads, 0, s>>>(dinv, r, w, z, d, (T)(rho * rho_old),
+                                              (T)(2.0 * rho / ch.delta), c.n);
+    rho_old = rho;
+  }
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
+// Interval of the Chebyshev preconditioner: lambda_max of D^-1 A from 15 power iterations
+// started at D^-1 start, enlarged by 10 %; lmin = lmax / 30 (the polynomial damps the upper
+// part of the spectrum, CG handles the rest).
+template <class T>
+chns_status cheb_bounds(const Ctx& c, const T* dinv, const T* start, T* v, T* w, int degree,
+                        Cheb* ch) {
+  const unsigned vg = vgrid(c.m, c.n);
+  note_launch();
+  k_mul<T><<<vg, kVecThreads, 0, c.s>>>(dinv, start, v, c.n);
+  double nn = 0.0;
+  chns_status st = dot_to_host<T>(c, v, v, &nn);
+  if (st != CHNS_OK) return st;
+  CHNS_CHECK(nn > 0.0 && std::isfinite(nn), CHNS_EBREAKDOWN, "Chebyshev: zero start vector");
+  note_launch();
+  k_scale<T><<<vg, kVecThreads, 0, c.s>>>(v, 1.0 / std::sqrt(nn), c.n);
+  double lam = 0.0;
+  for (int it = 0; it < 15; ++it) {
+    st = apply_T<T>(c, v, w);
+    if (st != CHNS_OK) return st;
+    note_launch();
+    k_mul<T><<<vg, kVecThreads, 0, c.s>>>(dinv, w, v, c.n);
+    st = dot_to_host<T>(c, v, v, &nn);
+    if (st != CHNS_OK) return st;
+    CHNS_CHECK(nn > 0.0 && std::isfinite(nn), CHNS_EBREAKDOWN, "Chebyshev: power iteration failed");
+    lam = std::sqrt(nn);
+    note_launch();
+    k_scale<T><<<vg, kVecThreads, 0, c.s>>>(v, 1.0 / lam, c.n);
+  }
+  const double lmax = 1.1 * lam, lmin = lmax / 30.0;
+  ch->theta = 0.5 * (lmax + lmin);
+  ch->delta = 0.5 * (lmax - lmin);
+  ch->degree = degree;
+  return CHNS_OK;
+}
+
 // Copies of the iterate every `every` iterations (FP64 CG only; collection of training pairs).
 struct Snap {
   double* buf;  // [max][n]
@@ -724,11 +813,13 @@ chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, i
 
 // Flexible CG on the Poisson operator with the preconditioner z = M(r): with L the learned
 // correction c followed by one damped Jacobi step, z = c + omega dinv (r - A c) (w: scratch
-// vector); else Jacobi (dinv) or the identity.
+// vector); with cheb the Chebyshev polynomial (scratch w, dcheb); else Jacobi (dinv) or the
+// identity.
 template <class T>
 chns_status fcg(const Ctx& c, const T* b, T* x, const T* dinv, chns_learned* L, double tol_abs,
                 int max_it, int chunk, T* r, T* z, T* p, T* q, T* p2, T* w, int* iters,
-                double* rnorm, int stall = 0, const Snap* snap = nullptr) {
+                double* rnorm, int stall = 0, const Snap* snap = nullptr,
+                const Cheb* cheb = nullptr, T* dcheb = nullptr) {
   T* pb[2] = {p, p2};
   const int64_t n = c.n;
   const unsigned rg = red_grid(c.m, n), vg = vgrid(c.m, n);
@@ -745,6 +836,7 @@ chns_status fcg(const Ctx& c, const T* b, T* x, const T* dinv, chns_learned* L, 
       k_smooth<T><<<vg, kVecThreads, 0, s>>>(z, r, w, dinv, (T)kLearnedOmega, n);
       return CHNS_OK;
     }
+    if (cheb) return cheb_apply<T>(c, s, *cheb, dinv, r, z, w, dcheb);
     note_launch();
     if (dinv) k_mul<T><<<vg, kVecThreads, 0, s>>>(dinv, r, z, n);
     else k_axpby<T><<<vg, kVecThreads, 0, s>>>(1.0, r, 0.0, r, z, n);
@@ -977,8 +1069,13 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
   CHNS_CHECK(op >= CHNS_OP_POISSON && op <= CHNS_OP_MOMENTUM, CHNS_EINVAL, "bad operator");
   CHNS_CHECK(sp->ksp == CHNS_KSP_CG || sp->ksp == CHNS_KSP_GMRES || sp->ksp == CHNS_KSP_FCG,
              CHNS_EINVAL, "bad ksp");
-  CHNS_CHECK(sp->pc == CHNS_PC_NONE || sp->pc == CHNS_PC_JACOBI || sp->pc == CHNS_PC_LEARNED,
+  CHNS_CHECK(sp->pc == CHNS_PC_NONE || sp->pc == CHNS_PC_JACOBI || sp->pc == CHNS_PC_LEARNED ||
+                 sp->pc == CHNS_PC_CHEBYSHEV,
              CHNS_EINVAL, "bad preconditioner");
+  CHNS_CHECK(sp->pc != CHNS_PC_CHEBYSHEV ||
+                 (op == CHNS_OP_POISSON && sp->ksp != CHNS_KSP_GMRES && sp->restart >= 1 &&
+                  sp->restart <= 16),
+             CHNS_EINVAL, "Chebyshev: Poisson operator, CG or FCG, degree (restart) 1..16");
   CHNS_CHECK(sp->ksp != CHNS_KSP_FCG || op == CHNS_OP_POISSON, CHNS_EINVAL,
              "FCG is implemented for the Poisson operator only");
   CHNS_CHECK(sp->pc != CHNS_PC_LEARNED || (sp->ksp == CHNS_KSP_FCG && sp->learned), CHNS_EINVAL,
@@ -1032,7 +1129,13 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
     // whose phi and mu unknowns are strongly coupled), computed in the precision of the Krylov
     // iteration that uses it.
     // the learned preconditioner is additive with the Jacobi smoother
-    const bool jac = sp->pc == CHNS_PC_JACOBI || sp->pc == CHNS_PC_LEARNED;
+    const bool jac = sp->pc == CHNS_PC_JACOBI || sp->pc == CHNS_PC_LEARNED ||
+                     sp->pc == CHNS_PC_CHEBYSHEV;
+    // the Chebyshev preconditioner runs through the flexible-CG driver (with a fixed SPD
+    // preconditioner its iterates are those of PCG)
+    const bool cheb = sp->pc == CHNS_PC_CHEBYSHEV;
+    const bool use_fcg = sp->ksp == CHNS_KSP_FCG || cheb;
+    Cheb cheb64, cheb32;
     chns_learned* L = sp->pc == CHNS_PC_LEARNED ? sp->learned : nullptr;
     if (L) {
       st = learned_begin_solve(L, m, prm, coef, s);
@@ -1067,13 +1170,17 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
       if (st != CHNS_OK) return st;
       int its = 0;
       double rn = 0.0;
-      if (sp->ksp == CHNS_KSP_CG)
+      if (cheb) {
+        st = cheb_bounds<double>(c, dinv64, b, ws.v64[14], ws.v64[15], sp->restart, &cheb64);
+        if (st != CHNS_OK) return st;
+      }
+      if (sp->ksp == CHNS_KSP_CG && !cheb)
         st = pcg<double>(c, b, x, dinv64, tol, sp->max_it, sp->check_every, r64, ws.v64[3],
                          ws.v64[4], ws.v64[5], ws.v64[6], &its, &rn);
-      else if (sp->ksp == CHNS_KSP_FCG) {
+      else if (use_fcg) {
         st = fcg<double>(c, b, x, dinv64, L, tol, sp->max_it, sp->check_every, r64, ws.v64[3],
                          ws.v64[4], ws.v64[5], ws.v64[6], ws.v64[7], &its, &rn,
-                         L ? kLearnedStall : 0);
+                         L ? kLearnedStall : 0, nullptr, cheb ? &cheb64 : nullptr, ws.v64[14]);
         if (L && st == CHNS_ENOTCONV && its < sp->max_it) {
           // the learned correction stalled: Jacobi-PCG from the current iterate
           ++out.fallbacks;
@@ -1162,13 +1269,19 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
             if (st != CHNS_OK) return st;
             int its = 0;
             double frn = 0.0;
-            if (sp->ksp == CHNS_KSP_CG)
+            if (cheb && cheb64.degree == 0) {
+              st = cheb_bounds<double>(c, dinv64, b, ws.v64[14], ws.v64[15], sp->restart,
+                                       &cheb64);
+              if (st != CHNS_OK) return st;
+            }
+            if (sp->ksp == CHNS_KSP_CG && !cheb)
               st = pcg<double>(c, b, x, dinv64, tol, sp->max_it - total, sp->check_every, r64,
                                ws.v64[3], ws.v64[4], ws.v64[5], ws.v64[6], &its, &frn);
-            else if (sp->ksp == CHNS_KSP_FCG)
+            else if (use_fcg)
               st = fcg<double>(c, b, x, dinv64, nullptr, tol, sp->max_it - total,
                                sp->check_every, r64, ws.v64[3], ws.v64[4], ws.v64[5], ws.v64[6],
-                               ws.v64[7], &its, &frn);
+                               ws.v64[7], &its, &frn, 0, nullptr, cheb ? &cheb64 : nullptr,
+                               ws.v64[14]);
             else
               st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it - total, sp->restart, ws.gm_V,
                                  ws.v64[7], &its, &frn);
@@ -1192,14 +1305,19 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
         const int cap = sp->ksp == CHNS_KSP_GMRES ? 4 * sp->restart : std::max(1000, sp->max_it / 4);
         const int budget = std::min(sp->max_it - total, cap);
         chns_status ist;
-        if (sp->ksp == CHNS_KSP_CG)
+        if (cheb && cheb32.degree == 0) {
+          st = cheb_bounds<float>(c, dinv32, r32, ws.v32[9], ws.v32[7], sp->restart, &cheb32);
+          if (st != CHNS_OK) return st;
+        }
+        if (sp->ksp == CHNS_KSP_CG && !cheb)
           ist = pcg<float>(c, r32, d32, dinv32, itol, budget, sp->check_every, ws.v32[3],
                            ws.v32[4], ws.v32[5], ws.v32[6], ws.v32[8], &its, &irn);
-        else if (sp->ksp == CHNS_KSP_FCG) {
+        else if (use_fcg) {
           chns_learned* Lc = learned_ok ? L : nullptr;
           ist = fcg<float>(c, r32, d32, dinv32, Lc, itol, budget, sp->check_every, ws.v32[3],
                            ws.v32[4], ws.v32[5], ws.v32[6], ws.v32[8], ws.v32[7], &its, &irn,
-                           Lc ? kLearnedStall : 0);
+                           Lc ? kLearnedStall : 0, nullptr, cheb ? &cheb32 : nullptr,
+                           ws.v32[9]);
           if (Lc && ist == CHNS_ENOTCONV && its < budget) {
             // the learned correction stalled: Jacobi only from the next refinement cycle on
             learned_ok = false;

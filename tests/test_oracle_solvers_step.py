@@ -79,3 +79,23 @@ def test_step_on_adaptive_drop_mesh():
     m, st, ms, es, logs = _run(w, 1)
     assert m.n_hanging > 0
     assert abs(ms[1] - ms[0]) < 1e-12
+
+
+def test_chebyshev_preconditioner_is_the_scaled_chebyshev_polynomial():
+    """On an eigenvector v of A (D = I) with eigenvalue lam, k steps give z = p(lam) v with
+    1 - lam p(lam) = T_k((theta - lam) / delta) / T_k(theta / delta) (library Chebyshev T_k)."""
+    from numpy.polynomial import chebyshev as C
+    from oracle.solvers import chebyshev_precond
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((12, 12)))
+    lams = np.linspace(0.05, 2.0, 12)
+    A = Q @ np.diag(lams) @ Q.T
+    lmin, lmax = 0.1, 2.2
+    theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    for k in (1, 2, 3, 5):
+        for j in (0, 4, 11):
+            v = Q[:, j]
+            z = chebyshev_precond(A, np.ones(12), v, lmin, lmax, k)
+            Tk = lambda t: C.chebval(t, [0] * k + [1])
+            p = (1.0 - Tk((theta - lams[j]) / delta) / Tk(theta / delta)) / lams[j]
+            assert np.allclose(z, p * v, rtol=1e-12, atol=1e-14), (k, j)
