@@ -338,9 +338,14 @@ k_multidot2(const T* __restrict__ V, int64_t ld, int nk, const T* __restrict__ w
   for (int k = 0; k <= NK; ++k) acc[k] = T(0);
   GRID_LOOP(i, n) {
     const T wi = w[i];
+    // every load is issued unconditionally (rows past nk re-read row nk - 1 from L1 and are
+    // discarded), so all of them are in flight at once instead of one per branch
+    T vk[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) vk[k] = V[(int64_t)(k < nk ? k : nk - 1) * ld + i];
 #pragma unroll
     for (int k = 0; k < NK; ++k)
-      if (k < nk) acc[k] += V[(int64_t)k * ld + i] * wi;
+      if (k < nk) acc[k] += vk[k] * wi;
     acc[NK] += wi * wi;
   }
 #pragma unroll
@@ -366,7 +371,7 @@ k_multidot2(const T* __restrict__ V, int64_t ld, int nk, const T* __restrict__ w
 // (h[nk] = w.w from the same multi-dot: Pythagoras for the classical Gram-Schmidt step). The
 // update runs in the vector type (FP32 for FP32 vectors: FP64 arithmetic per element and basis
 // vector would bound this kernel on GB300), the coefficients from shared memory.
-template <class T, bool NORMALISE>
+template <class T, bool NORMALISE, int NK>
 __global__ void k_orth_update_scale(const T* __restrict__ V, int64_t ld, int nk,
                                     const double* __restrict__ h, T* __restrict__ w, int64_t n) {
   __shared__ T hs[CHNS_GMRES_MAX_RESTART + 1];
@@ -385,10 +390,32 @@ __global__ void k_orth_update_scale(const T* __restrict__ V, int64_t ld, int nk,
   __syncthreads();
   const T sc = s_scale;
   GRID_LOOP(i, n) {
+    T vk[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) vk[k] = V[(int64_t)(k < nk ? k : nk - 1) * ld + i];
     T acc = w[i];
-    for (int k = 0; k < nk; ++k) acc -= hs[k] * V[(int64_t)k * ld + i];
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+      if (k < nk) acc -= hs[k] * vk[k];
     w[i] = acc * sc;
   }
+}
+
+template <class T, bool NORMALISE>
+void orth_update(const T* V, int64_t ld, int nk, const double* h, T* w, int64_t n, unsigned grid,
+                 cudaStream_t s) {
+  note_launch();
+  if (nk <= 8)
+    k_orth_update_scale<T, NORMALISE, 8><<<grid, kVecThreads, 0, s>>>(V, ld, nk, h, w, n);
+  else if (nk <= 16)
+    k_orth_update_scale<T, NORMALISE, 16><<<grid, kVecThreads, 0, s>>>(V, ld, nk, h, w, n);
+  else if (nk <= 24)
+    k_orth_update_scale<T, NORMALISE, 24><<<grid, kVecThreads, 0, s>>>(V, ld, nk, h, w, n);
+  else if (nk <= 32)
+    k_orth_update_scale<T, NORMALISE, 32><<<grid, kVecThreads, 0, s>>>(V, ld, nk, h, w, n);
+  else
+    k_orth_update_scale<T, NORMALISE, CHNS_GMRES_MAX_RESTART + 1>
+        <<<grid, kVecThreads, 0, s>>>(V, ld, nk, h, w, n);
 }
 
 template <class T>
@@ -966,8 +993,7 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, do
       double hn2 = ww - hh;
       if (!(hn2 > 0.5 * ww)) {
         // re-orthogonalise: w -= V h, then a second multi-dot on the updated vector
-        note_launch();
-        k_orth_update_scale<T, false><<<vg, kVecThreads, 0, c.s>>>(V, ld, nk, hdev, w, n);
+        orth_update<T, false>(V, ld, nk, hdev, w, n, vg, c.s);
         multidot(V, ld, nk, w, n, md2, c.m->ws.md_part, c.s);
         note_launch();
         k_multidot_final<<<nk + 1, kVecThreads, 0, c.s>>>(c.m->ws.md_part, (int)md2, hdev);
@@ -990,8 +1016,7 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, do
         return CHNS_ENAN;
       }
       if (hn > 0.0) {
-        note_launch();
-        k_orth_update_scale<T, true><<<vg, kVecThreads, 0, c.s>>>(V, ld, nk, hdev, w, n);
+        orth_update<T, true>(V, ld, nk, hdev, w, n, vg, c.s);
       }
       // Givens rotations
       for (int i = 0; i < j; ++i) {
