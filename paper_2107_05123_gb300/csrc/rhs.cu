@@ -93,17 +93,22 @@ k_rhs_momentum(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 uk,
   gather<double, false>(m, idx, cf.mu, me);
   gather<double, false>(m, idx, pk, pp);
   const double J = g.detJ, cw = p.d.cw;
-  for (int i = 0; i < 3; ++i) {
-    double ui[8], r[8] = {0};
-    gather<double, false>(m, idx, uk.c[i], ui);
-    for_qp([&](auto QC) {
-      constexpr int Q = decltype(QC)::value;
-      VmsQ<double> c = vms_at<Q>(pe, ue, me, g, p);
-      double F[3];
-      forcing_at<Q>(pe, g, c.gphi, F);
-      double pv, pg[3], v, vg[3];
-      vg_at<Q>(pp, g, pv, pg);
-      vg_at<Q>(ui, g, v, vg);
+  // the quadrature-point coefficients (tau_m, the advection and stabilisation vectors, the
+  // forcing) are the same for the three components: computed once per point
+  double ui[3][8], r[3][8] = {{0}};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) gather<double, false>(m, idx, uk.c[i], ui[i]);
+  for_qp([&](auto QC) {
+    constexpr int Q = decltype(QC)::value;
+    VmsQ<double> c = vms_at<Q>(pe, ue, me, g, p);
+    double F[3];
+    forcing_at<Q>(pe, g, c.gphi, F);
+    double pv, pg[3];
+    vg_at<Q>(pp, g, pv, pg);
+#pragma unroll 1
+    for (int i = 0; i < 3; ++i) {
+      double v, vg[3];
+      vg_at<Q>(ui[i], g, v, vg);
       const double grav = c.rho * ghat(i) * p.d.inv_fr;
       double bdot = c.b[0] * vg[0] + c.b[1] * vg[1] + c.b[2] * vg[2];
       double bpdot = c.bp[0] * vg[0] + c.bp[1] * vg[1] + c.bp[2] * vg[2];
@@ -112,10 +117,11 @@ k_rhs_momentum(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 uk,
       double V[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) V[d] = J * (-c.e * vg[d] + cw * c.gphi[i] * c.gphi[d] - c.t[d] * r0);
-      add_test<Q>(r, J * fn, V, g);
-    });
-    scatter<double, true>(m, idx, r, b + i * m.n_nodes);
-  }
+      add_test<Q>(r[i], J * fn, V, g);
+    }
+  });
+#pragma unroll
+  for (int i = 0; i < 3; ++i) scatter<double, true>(m, idx, r[i], b + i * m.n_nodes);
 }
 
 // Full R_m,i(v) at Q (Def. of R_m) with v~ = (v + u_k)/2.
