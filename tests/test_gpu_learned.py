@@ -254,3 +254,27 @@ def test_trained_network_reduces_iterations(capi):
     capi.chns_learned_destroy(net)
     print("Jacobi-PCG", its_j, "FCG + learned", its_l)
     assert np.mean(its_l) < 0.8 * np.mean(its_j), (its_j, its_l)
+
+
+def test_step_collection_adds_pairs_and_leaves_the_step_unchanged(capi):
+    """chns_step with chns_step_params.collect: every pressure solve adds its pairs, and the
+    fields after the step equal those of the same step without collection."""
+    from paper_2107_05123_gb300.session import DeviceState, default_step_params
+    w = configs.rising_drop(3, 5, Cn=0.04)
+    om, gm = meshes("drop_l3_5")
+    f0 = w.init(gm.node_xyz)
+    prm = capi.make_params(w.params.as_dict())
+    net = capi.chns_learned_create(16, 64, 2)
+    out = {}
+    for collect in (False, True):
+        ds = DeviceState(dict(phi=f0["phi"], mu=f0["mu"], u=f0["u"], p=f0["p"]))
+        sp = default_step_params(1e-10, capi.FP64, 8)
+        if collect:
+            sp.collect, sp.collect_every, sp.collect_max = net, 4, 5
+        capi.chns_step(gm.handle, ds.c, prm, sp)
+        out[collect] = ds.host()
+    n_pairs = capi.chns_learned_num_samples(net)
+    capi.chns_learned_destroy(net)
+    assert 2 <= n_pairs <= 10, n_pairs
+    for k in ("phi", "mu", "u", "p"):
+        assert relerr(out[True][k], out[False][k]) < 1e-9, k
