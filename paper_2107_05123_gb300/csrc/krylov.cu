@@ -322,56 +322,32 @@ __global__ void k_gmres_update_b2(const T* __restrict__ V, int64_t ld, int nk,
 // shared memory once and sweeps all rows over it (the rows are read once, w once); per-warp sums
 // accumulate in shared memory across the block's slices; partials land in part[k][blockIdx.x].
 constexpr int kMd2Threads = 256;
-// GMRES multi-dot: h_k = V_k . w for k < nk and h_nk = w.w in one pass over w. Every thread
-// keeps all nk + 1 running sums in registers over its few elements (FP32 products, one element
-// per vector per iteration, so each warp reads 128 contiguous bytes of every basis vector), then
-// the sums go through double-float warp reductions and FP64 across warps; block partials land
-// in part[k * gridDim.x + block] for k_multidot_final.
-template <class T, int NK>
+// GMRES multi-dot: h_k = V_k . w for k < nk and h_nk = w.w. Block (c, k) of the 2D grid sums
+// the products of row k (w itself for k = nk) with w over chunk c of the elements: one
+// accumulator per thread (double-float for FP32 vectors), all loads coalesced and independent,
+// full occupancy; w is re-read per row from L2. part[k * gridDim.x + c] -> k_multidot_final.
+template <class T>
 __global__ void __launch_bounds__(kMd2Threads)
 k_multidot2(const T* __restrict__ V, int64_t ld, int nk, const T* __restrict__ w, int64_t n,
             double* __restrict__ part) {
-  __shared__ double accs[NK + 1][kMd2Threads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T acc[NK + 1];
-#pragma unroll
-  for (int k = 0; k <= NK; ++k) acc[k] = T(0);
-  GRID_LOOP(i, n) {
-    const T wi = w[i];
-    // every load is issued unconditionally (rows past nk re-read row nk - 1 from L1 and are
-    // discarded), so all of them are in flight at once instead of one per branch
-    T vk[NK];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) vk[k] = V[(int64_t)(k < nk ? k : nk - 1) * ld + i];
-#pragma unroll
-    for (int k = 0; k < NK; ++k)
-      if (k < nk) acc[k] += vk[k] * wi;
-    acc[NK] += wi * wi;
-  }
-#pragma unroll
-  for (int k = 0; k <= NK; ++k) {
-    if (k < nk || k == NK) {
-      typename Acc<T>::type a = Acc<T>::zero();
-      Acc<T>::add(a, acc[k]);
-      const auto d = warp_sum(a);
-      if (lane == 0) accs[k][warp] = acc_value(d);
-    }
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k <= nk; k += kMd2Threads) {
-    const int src = k < nk ? k : NK;
-    double t = 0.0;
-#pragma unroll
-    for (int q = 0; q < kMd2Threads / 32; ++q) t += accs[src][q];
-    part[(int64_t)k * gridDim.x + blockIdx.x] = t;
-  }
+  const int k = blockIdx.y;
+  const T* __restrict__ a = k < nk ? V + (int64_t)k * ld : w;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * chunk;
+  const int64_t i1 = i0 + chunk < n ? i0 + chunk : n;
+  typename Acc<T>::type acc = Acc<T>::zero();
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += kMd2Threads) Acc<T>::fma(acc, a[i], w[i]);
+  typename Acc<T>::type v[1] = {acc};
+  double tot[1];
+  block_sum<1, kMd2Threads>(v, tot);
+  if (threadIdx.x == 0) part[(int64_t)k * gridDim.x + blockIdx.x] = tot[0];
 }
 
 // w = (w - sum_k h_k V_k) * scale, with scale = 1/sqrt(h[nk] - sum_k h_k^2) when NORMALISE
 // (h[nk] = w.w from the same multi-dot: Pythagoras for the classical Gram-Schmidt step). The
 // update runs in the vector type (FP32 for FP32 vectors: FP64 arithmetic per element and basis
 // vector would bound this kernel on GB300), the coefficients from shared memory.
-template <class T, bool NORMALISE, int NK>
+template <class T, bool NORMALISE>
 __global__ void k_orth_update_scale(const T* __restrict__ V, int64_t ld, int nk,
                                     const double* __restrict__ h, T* __restrict__ w, int64_t n) {
   __shared__ T hs[CHNS_GMRES_MAX_RESTART + 1];
@@ -390,13 +366,8 @@ __global__ void k_orth_update_scale(const T* __restrict__ V, int64_t ld, int nk,
   __syncthreads();
   const T sc = s_scale;
   GRID_LOOP(i, n) {
-    T vk[NK];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) vk[k] = V[(int64_t)(k < nk ? k : nk - 1) * ld + i];
     T acc = w[i];
-#pragma unroll
-    for (int k = 0; k < NK; ++k)
-      if (k < nk) acc -= hs[k] * vk[k];
+    for (int k = 0; k < nk; ++k) acc -= hs[k] * V[(int64_t)k * ld + i];
     w[i] = acc * sc;
   }
 }
@@ -405,17 +376,7 @@ template <class T, bool NORMALISE>
 void orth_update(const T* V, int64_t ld, int nk, const double* h, T* w, int64_t n, unsigned grid,
                  cudaStream_t s) {
   note_launch();
-  if (nk <= 8)
-    k_orth_update_scale<T, NORMALISE, 8><<<grid, kVecThreads, 0, s>>>(V, ld, nk, h, w, n);
-  else if (nk <= 16)
-    k_orth_update_scale<T, NORMALISE, 16><<<grid, kVecThreads, 0, s>>>(V, ld, nk, h, w, n);
-  else if (nk <= 24)
-    k_orth_update_scale<T, NORMALISE, 24><<<grid, kVecThreads, 0, s>>>(V, ld, nk, h, w, n);
-  else if (nk <= 32)
-    k_orth_update_scale<T, NORMALISE, 32><<<grid, kVecThreads, 0, s>>>(V, ld, nk, h, w, n);
-  else
-    k_orth_update_scale<T, NORMALISE, CHNS_GMRES_MAX_RESTART + 1>
-        <<<grid, kVecThreads, 0, s>>>(V, ld, nk, h, w, n);
+  k_orth_update_scale<T, NORMALISE><<<grid, kVecThreads, 0, s>>>(V, ld, nk, h, w, n);
 }
 
 template <class T>
@@ -909,21 +870,17 @@ chns_status fcg(const Ctx& c, const T* b, T* x, const T* dinv, chns_learned* L, 
   return iterate<T>(c, step, x, tol_abs, max_it, chunk, rr, iters, rnorm, snap, stall);
 }
 
-// multi-dot launch with the register count fitted to the number of basis vectors
+// multi-dot launch: (chunks, nk + 1) blocks, about four per SM in total; returns the chunk count
 template <class T>
-void multidot(const T* V, int64_t ld, int nk, const T* w, int64_t n, unsigned grid, double* part,
-              cudaStream_t s) {
+unsigned multidot(const chns_mesh* m, const T* V, int64_t ld, int nk, const T* w, int64_t n,
+                  double* part, cudaStream_t s) {
+  const int64_t want = 4 * (int64_t)m->sm_count / (nk + 1);
+  const unsigned chunks = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>({std::max<int64_t>(want, 8), (n + kMd2Threads - 1) / kMd2Threads,
+                            (int64_t)kMdMaxBlocks}));
   note_launch();
-  if (nk <= 8)
-    k_multidot2<T, 8><<<grid, kMd2Threads, 0, s>>>(V, ld, nk, w, n, part);
-  else if (nk <= 16)
-    k_multidot2<T, 16><<<grid, kMd2Threads, 0, s>>>(V, ld, nk, w, n, part);
-  else if (nk <= 24)
-    k_multidot2<T, 24><<<grid, kMd2Threads, 0, s>>>(V, ld, nk, w, n, part);
-  else if (nk <= 32)
-    k_multidot2<T, 32><<<grid, kMd2Threads, 0, s>>>(V, ld, nk, w, n, part);
-  else
-    k_multidot2<T, CHNS_GMRES_MAX_RESTART + 1><<<grid, kMd2Threads, 0, s>>>(V, ld, nk, w, n, part);
+  k_multidot2<T><<<dim3(chunks, nk + 1), kMd2Threads, 0, s>>>(V, ld, nk, w, n, part);
+  return chunks;
 }
 
 // Right-preconditioned restarted GMRES with classical Gram-Schmidt and one re-orthogonalisation
@@ -974,11 +931,8 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, do
       if (st != CHNS_OK) return st;
       // classical Gram-Schmidt: h = V^T w and w.w in one pass; a second pass only when the
       // new vector lost more than half its norm to the projection (cancellation)
-      const unsigned md2 = (unsigned)std::max<int64_t>(
-          1, std::min<int64_t>((n + 2 * kMd2Threads - 1) / (2 * kMd2Threads),
-                               std::min<int64_t>(kMdMaxBlocks, 4 * (int64_t)c.m->sm_count)));
       int nk = j + 1;
-      multidot(V, ld, nk, w, n, md2, c.m->ws.md_part, c.s);
+      const unsigned md2 = multidot(c.m, V, ld, nk, w, n, c.m->ws.md_part, c.s);
       note_launch();
       k_multidot_final<<<nk + 1, kVecThreads, 0, c.s>>>(c.m->ws.md_part, (int)md2, hdev);
       CHNS_CUDA(cudaGetLastError());
@@ -994,7 +948,7 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, do
       if (!(hn2 > 0.5 * ww)) {
         // re-orthogonalise: w -= V h, then a second multi-dot on the updated vector
         orth_update<T, false>(V, ld, nk, hdev, w, n, vg, c.s);
-        multidot(V, ld, nk, w, n, md2, c.m->ws.md_part, c.s);
+        multidot(c.m, V, ld, nk, w, n, c.m->ws.md_part, c.s);
         note_launch();
         k_multidot_final<<<nk + 1, kVecThreads, 0, c.s>>>(c.m->ws.md_part, (int)md2, hdev);
         CHNS_CUDA(cudaGetLastError());
