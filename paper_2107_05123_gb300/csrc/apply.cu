@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(MeshDev m, DevParams p,
 // With PQ the block sums of the element energies x_e . A_e x_e (summing to x^T A x) are added to
 // S_cg[kCgPq0 + par] with an FP64 atomic.
 template <class K, class T, class S, class C, bool PQ, bool CGP>
-__global__ void __launch_bounds__(kPatchThreads, K::MIN_CTAS)
+__global__ void __launch_bounds__(kPatchElems, K::MIN_CTAS)
 k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S* __restrict__ y,
               double* __restrict__ S_cg, int par, int fcg, const S* __restrict__ zcg,
               S* __restrict__ pout) {
@@ -75,27 +75,20 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
       S_cg[kCgRr0 + (par ^ 1)] = 0.0;
     }
   }
-  // the elements' local corner slots and levels are loaded first, so that their latency
-  // overlaps the gather of the patch's nodes
-  constexpr int EPT = kPatchElems / kPatchThreads;
-  const int64_t e0 = (int64_t)m.patch_elem[pidx] + threadIdx.x;
-  const int64_t e_end = m.patch_elem[pidx + 1];
-  uint4 lp[EPT];
-  int lev[EPT];
-#pragma unroll
-  for (int t = 0; t < EPT; ++t) {
-    const int64_t e = e0 + t * kPatchThreads;
-    lp[t] = make_uint4(0, 0, 0, 0);
-    lev[t] = 0;
-    if (e < e_end) {
-      lp[t] = __ldg(m.eloc + e);
-      lev[t] = __ldg(m.level + e);
-    }
+  // the element's local corner slots and level are loaded first, so that their latency overlaps
+  // the gather of the patch's nodes
+  const int64_t e = (int64_t)m.patch_elem[pidx] + threadIdx.x;
+  const bool has_elem = e < m.patch_elem[pidx + 1];
+  uint4 lp = make_uint4(0, 0, 0, 0);
+  int lev = 0;
+  if (has_elem) {
+    lp = __ldg(m.eloc + e);
+    lev = __ldg(m.level + e);
   }
   if (CGP) __syncthreads();
   // 1. regular slots
   {
-    for (int i = threadIdx.x; i < nreg; i += kPatchThreads) {
+    for (int i = threadIdx.x; i < nreg; i += kPatchElems) {
       const int32_t v = m.slot_node[s0 + i];
       const int64_t g = v & kNodeMask;
       const bool dir = K::DIR && (v & kDirBit);
@@ -145,14 +138,11 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
   __syncthreads();
   // 3. elements
   typename Acc<T>::type en[1] = {Acc<T>::zero()};
-#pragma unroll 1
-  for (int t = 0; t < EPT; ++t) {
-    if (e0 + t * kPatchThreads >= e_end) break;
-    const uint4 lq = lp[t];
-    const int sl[8] = {(int)(lq.x & 0xffff), (int)(lq.x >> 16), (int)(lq.y & 0xffff),
-                       (int)(lq.y >> 16),    (int)(lq.z & 0xffff), (int)(lq.z >> 16),
-                       (int)(lq.w & 0xffff), (int)(lq.w >> 16)};
-    const Geo<T> g = level_geometry<T>(m, lev[t]);
+  if (has_elem) {
+    const int sl[8] = {(int)(lp.x & 0xffff), (int)(lp.x >> 16), (int)(lp.y & 0xffff),
+                       (int)(lp.y >> 16),    (int)(lp.z & 0xffff), (int)(lp.z >> 16),
+                       (int)(lp.w & 0xffff), (int)(lp.w >> 16)};
+    const Geo<T> g = level_geometry<T>(m, lev);
     T fe[NF][8];
 #pragma unroll
     for (int f = 0; f < NF; ++f)
@@ -178,7 +168,7 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
   // p.Ap
   if (PQ) {
     double tot[1];
-    block_sum<1, kPatchThreads>(en, tot);
+    block_sum<1, kPatchElems>(en, tot);
     if (threadIdx.x == 0) atomicAdd(S_cg + kCgPq0 + par, tot[0]);
   }
   __syncthreads();
@@ -234,7 +224,7 @@ static void launch_patch(const chns_mesh* m, const DevParams& p, const CoefArgs<
     configured = true;
   }
   note_launch();
-  k_apply_patch<K, T, S, C, PQ, CGP><<<(unsigned)m->d.n_patch, kPatchThreads, smem, s>>>(
+  k_apply_patch<K, T, S, C, PQ, CGP><<<(unsigned)m->d.n_patch, kPatchElems, smem, s>>>(
       m->d, p, cf, x, y, S_cg, par, fcg, z, pout);
 }
 

@@ -18,14 +18,10 @@ constexpr int32_t kIdxMask = kDirBit - 1;
 // Patch slot entries: node id (< 2^29) | kOwnBit (only this patch touches the node) | kDirBit.
 constexpr int32_t kOwnBit = 1 << 29;
 constexpr int32_t kNodeMask = kOwnBit - 1;
-// A patch is a run of Morton-consecutive elements processed by one CTA of kPatchThreads threads
-// (kPatchElems / kPatchThreads elements per thread) whose distinct nodes (regular nodes and
-// hanging corners) fit in kPatchSlots shared slots. Two elements per thread: the rising-drop
-// mesh (314,672 leaves) then needs 615 CTAs, which all fit on the 152 SMs at once; with one
-// element per thread no launch of it fits in a single wave (152 x 2,048 threads < 314,672).
-constexpr int kPatchThreads = 256;
-constexpr int kPatchElems = 512;
-constexpr int kPatchSlots = 2048;
+// A patch is a run of Morton-consecutive elements processed by one CTA (one thread per element)
+// whose distinct nodes (regular nodes and hanging corners) fit in kPatchSlots shared slots.
+constexpr int kPatchElems = 256;
+constexpr int kPatchSlots = 1024;
 
 // Element geometry of one octant level on the box [0,L]^3 scaled per axis: h_d = L_d 2^-level,
 // 1/h_d and det J = h_x h_y h_z / 8, in FP64 and FP32 (looked up, never recomputed per element).

@@ -64,9 +64,9 @@ __device__ __forceinline__ void stiff_local(const T c[8], const Geo<T>& g, const
 
 template <class T, class C>
 struct PoissonK {
-  // CTAs of the patch apply resident per SM that the register allocation must allow (FP32: 5,
-  // i.e. at most 51 registers, 24 KB of shared memory each; FP64: 3)
-  static constexpr int MIN_CTAS = sizeof(T) == 4 ? 5 : 3;
+  // CTAs of the patch apply resident per SM that the register allocation must allow (FP32: 6,
+  // i.e. at most 42 registers; FP64: 3)
+  static constexpr int MIN_CTAS = sizeof(T) == 4 ? 6 : 3;
   static constexpr int NC = 1;
   static constexpr bool DIR = false;
   static constexpr bool DIAG_PER_COMP = false;
@@ -91,7 +91,7 @@ struct PoissonK {
 // (w, rho~ u) per component (Def. weak_VMS_disc_vel_update); Dirichlet rows are identity.
 template <class T, class C>
 struct MassK {
-  static constexpr int MIN_CTAS = sizeof(T) == 4 ? 3 : 1;
+  static constexpr int MIN_CTAS = sizeof(T) == 4 ? 5 : 3;
   static constexpr int NC = 3;
   static constexpr bool DIR = true;
   static constexpr bool DIAG_PER_COMP = false;
@@ -132,7 +132,7 @@ struct MassK {
 //   row mu : -1/2 (q, dmu) + 1/2 (q, psi''(phi~) dphi) + Cn^2/2 (grad q, grad dphi)
 template <class T, class C>
 struct ChK {
-  static constexpr int MIN_CTAS = sizeof(T) == 4 ? 3 : 1;
+  static constexpr int MIN_CTAS = sizeof(T) == 4 ? 4 : 1;
   static constexpr int NC = 2;
   static constexpr bool DIR = false;
   static constexpr bool DIAG_PER_COMP = true;
@@ -243,7 +243,7 @@ __device__ __forceinline__ VmsQ<T> vms_at(const T pe[8], const T ue[3][8], const
 
 template <class T, class C>
 struct MomK {
-  // FP32: two CTAs per SM (at most 128 registers; 90 KB of shared memory each)
+  // FP32: two CTAs per SM (at most 128 registers) instead of the one that 217 registers allow
   static constexpr int MIN_CTAS = sizeof(T) == 4 ? 2 : 1;
   static constexpr int NC = 3;
   static constexpr bool DIR = true;
