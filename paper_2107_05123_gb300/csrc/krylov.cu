@@ -1049,8 +1049,8 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, do
     it += jend;
     // H (upper triangle of the first jend columns) and the rotated right-hand side
     std::vector<double> Gh((size_t)kGmSize);
-    CHNS_CUDA(cudaMemcpyAsync(Gh.data(), G, kGmSize * sizeof(double), cudaMemcpyDeviceToHost, c.s));
-    CHNS_CUDA(cudaStreamSynchronize(c.s));
+    st = read_dev(c.m, G, Gh.data(), kGmSize, c.s);
+    if (st != CHNS_OK) return st;
     for (int jj = 0; jj < jend; ++jj)
       for (int i = 0; i <= jj; ++i) Hij(i, jj) = Gh[(size_t)jj * kGmLd + i];
     for (int i = 0; i < jend; ++i) g[i] = Gh[kGmG + i];
