@@ -65,7 +65,6 @@ struct Workspace {
   double* coef64 = nullptr;    // FP64 step coefficients (phi~, u_hat x3, mu~ + scratch)
   double* part_big = nullptr;  // per-block partials of element-level reductions (n_elem/64+64)
   double* md_part = nullptr;   // GMRES multi-dot partials: [restart + 2][kMdMaxBlocks]
-  double* gm_small = nullptr;  // GMRES device state (Hessenberg columns, rotations): kGmSmallSize
 };
 
 }  // namespace chns
@@ -129,7 +128,6 @@ constexpr int kNumVec64 = 16;
 constexpr int kNumVec32 = 10;
 constexpr int kRedSlots = 4096;   // partial sums per reduction
 constexpr int kMdMaxBlocks = 1024; // blocks of the GMRES multi-dot
-constexpr int kGmSmallSize = 4096; // doubles of GMRES device state
 constexpr int kScalarBase = 3 * 4096;  // scalars stored after three partial arrays
 
 // ---- apply dispatch (apply.cu)

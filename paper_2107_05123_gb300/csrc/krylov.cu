@@ -19,6 +19,7 @@
 namespace chns {
 
 constexpr int kVecThreads = 256;
+constexpr int kMdBlocks = 256;  // blocks per multi-dot row (partials: rows x kMdBlocks)
 
 // device scalar slots (offsets from ws.red + kScalarBase)
 enum Slot { S_RZ0 = 0, S_RZ1 = 1, S_PQ = 2, S_RR = 3, S_TMP = 8, S_AUX = 16, S_MD = 64 };
@@ -280,9 +281,7 @@ __global__ void k_smooth(T* __restrict__ z, const T* __restrict__ r, const T* __
 
 // ---- GMRES
 __global__ void __launch_bounds__(kVecThreads)
-k_multidot_final(const double* __restrict__ part, int nb, double* __restrict__ out,
-                 const double* __restrict__ run) {
-  if (run && *run == 0.0) return;
+k_multidot_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
   double s[1] = {0.0};
   for (int b = threadIdx.x; b < nb; b += kVecThreads) s[0] += part[(int64_t)blockIdx.x * nb + b];
   double t[1];
@@ -330,8 +329,7 @@ constexpr int kMd2Threads = 256;
 template <class T>
 __global__ void __launch_bounds__(kMd2Threads)
 k_multidot2(const T* __restrict__ V, int64_t ld, int nk, const T* __restrict__ w, int64_t n,
-            double* __restrict__ part, const double* __restrict__ run) {
-  if (run && *run == 0.0) return;  // conditional pass (GMRES re-orthogonalisation)
+            double* __restrict__ part) {
   const int k = blockIdx.y;
   const T* __restrict__ a = k < nk ? V + (int64_t)k * ld : w;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -345,17 +343,28 @@ k_multidot2(const T* __restrict__ V, int64_t ld, int nk, const T* __restrict__ w
   if (threadIdx.x == 0) part[(int64_t)k * gridDim.x + blockIdx.x] = tot[0];
 }
 
-// w = (w - sum_k c_k V_k) * scale with c and scale in device memory (scale null: 1); with run
-// set, only when *run != 0
-template <class T>
-__global__ void k_orth_apply(const T* __restrict__ V, int64_t ld, int nk,
-                             const double* __restrict__ c, const double* __restrict__ scale,
-                             const double* __restrict__ run, T* __restrict__ w, int64_t n) {
-  if (run && *run == 0.0) return;
+// w = (w - sum_k h_k V_k) * scale, with scale = 1/sqrt(h[nk] - sum_k h_k^2) when NORMALISE
+// (h[nk] = w.w from the same multi-dot: Pythagoras for the classical Gram-Schmidt step). The
+// update runs in the vector type (FP32 for FP32 vectors: FP64 arithmetic per element and basis
+// vector would bound this kernel on GB300), the coefficients from shared memory.
+template <class T, bool NORMALISE>
+__global__ void k_orth_update_scale(const T* __restrict__ V, int64_t ld, int nk,
+                                    const double* __restrict__ h, T* __restrict__ w, int64_t n) {
   __shared__ T hs[CHNS_GMRES_MAX_RESTART + 1];
-  if (threadIdx.x < nk) hs[threadIdx.x] = (T)c[threadIdx.x];
+  __shared__ T s_scale;
+  if (threadIdx.x < nk) hs[threadIdx.x] = (T)h[threadIdx.x];
+  if (threadIdx.x == 0) {
+    double sc = 1.0;
+    if (NORMALISE) {
+      double hh = 0.0;
+      for (int k = 0; k < nk; ++k) hh += h[k] * h[k];
+      const double r = h[nk] - hh;
+      sc = r > 0.0 ? rsqrt(r) : 1.0;
+    }
+    s_scale = (T)sc;
+  }
   __syncthreads();
-  const T sc = scale ? (T)*scale : T(1);
+  const T sc = s_scale;
   GRID_LOOP(i, n) {
     T acc = w[i];
     for (int k = 0; k < nk; ++k) acc -= hs[k] * V[(int64_t)k * ld + i];
@@ -363,78 +372,11 @@ __global__ void k_orth_apply(const T* __restrict__ V, int64_t ld, int nk,
   }
 }
 
-// ---- device side of one Arnoldi step (single thread). Layout of the GMRES state g:
-// H column j at g + j * kGmLd (rows 0..j+1), cs, sn, rhs (Givens-rotated beta e_1), scalars.
-constexpr int kGmLd = CHNS_GMRES_MAX_RESTART + 1;
-constexpr int kGmCs = CHNS_GMRES_MAX_RESTART * kGmLd;
-constexpr int kGmSn = kGmCs + CHNS_GMRES_MAX_RESTART;
-constexpr int kGmG = kGmSn + CHNS_GMRES_MAX_RESTART;
-constexpr int kGmFlag = kGmG + kGmLd;   // 1: re-orthogonalise this step
-constexpr int kGmScale = kGmFlag + 1;   // 1 / |w| for the normalisation
-constexpr int kGmHn = kGmScale + 1;     // |w| after orthogonalisation (H(j+1, j))
-constexpr int kGmBreak = kGmHn + 1;     // breakdown (|w| = 0 or not finite)
-constexpr int kGmCoef = kGmBreak + 1;   // coefficients of the normalisation pass (kGmLd)
-constexpr int kGmRes = kGmCoef + kGmLd; // |rotated rhs(j+1)| per step (CHNS_GMRES_MAX_RESTART)
-constexpr int kGmSize = kGmRes + CHNS_GMRES_MAX_RESTART;
-static_assert(kGmSize <= kGmSmallSize, "GMRES device state exceeds its workspace array");
-
-// First Gram-Schmidt pass done (h = V^T w, ww = w.w in h[nk]): store H(:, j); decide on a second
-// pass (cancellation: the new vector kept less than half its norm)
-__global__ void k_gs_first(const double* __restrict__ h, int j, double* __restrict__ G) {
-  const int nk = j + 1;
-  double hh = 0.0;
-  for (int k = 0; k < nk; ++k) {
-    G[j * kGmLd + k] = h[k];
-    G[kGmCoef + k] = h[k];
-    hh += h[k] * h[k];
-  }
-  const double ww = h[nk], hn2 = ww - hh;
-  const bool again = !(hn2 > 0.5 * ww);
-  G[kGmFlag] = again ? 1.0 : 0.0;
-  const double hn = std::sqrt(hn2 > 0.0 ? hn2 : 0.0);
-  G[kGmHn] = hn;
-  G[kGmScale] = hn > 0.0 ? 1.0 / hn : 1.0;
-}
-
-// Second pass (when flagged): H(:, j) += h2, |w| from Pythagoras on the re-orthogonalised vector
-__global__ void k_gs_second(const double* __restrict__ h2, int j, double* __restrict__ G) {
-  if (G[kGmFlag] == 0.0) return;
-  const int nk = j + 1;
-  double hh = 0.0;
-  for (int k = 0; k < nk; ++k) {
-    G[j * kGmLd + k] += h2[k];
-    G[kGmCoef + k] = h2[k];
-    hh += h2[k] * h2[k];
-  }
-  const double hn2 = h2[nk] - hh;
-  const double hn = std::sqrt(hn2 > 0.0 ? hn2 : 0.0);
-  G[kGmHn] = hn;
-  G[kGmScale] = hn > 0.0 ? 1.0 / hn : 1.0;
-}
-
-// Givens rotations of H(:, j), new rotation, rotated right-hand side and its last entry
-__global__ void k_gmres_givens(int j, double* __restrict__ G) {
-  double* col = G + j * kGmLd;
-  const double hn = G[kGmHn];
-  col[j + 1] = hn;
-  double* cs = G + kGmCs;
-  double* sn = G + kGmSn;
-  double* g = G + kGmG;
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-    col[i] = t;
-  }
-  const double a = col[j], b = col[j + 1];
-  const double r = hypot(a, b);
-  cs[j] = r > 0.0 ? a / r : 1.0;
-  sn[j] = r > 0.0 ? b / r : 0.0;
-  col[j] = r;
-  col[j + 1] = 0.0;
-  g[j + 1] = -sn[j] * g[j];
-  g[j] = cs[j] * g[j];
-  G[kGmRes + j] = fabs(g[j + 1]);
-  if (!(hn > 0.0) || !isfinite(hn) || !isfinite(r)) G[kGmBreak] = 1.0;
+template <class T, bool NORMALISE>
+void orth_update(const T* V, int64_t ld, int nk, const double* h, T* w, int64_t n, unsigned grid,
+                 cudaStream_t s) {
+  note_launch();
+  k_orth_update_scale<T, NORMALISE><<<grid, kVecThreads, 0, s>>>(V, ld, nk, h, w, n);
 }
 
 template <class T>
@@ -532,8 +474,6 @@ namespace {
 constexpr int kLearnedStall = 100;
 // damping of the Jacobi step that follows the learned correction
 constexpr double kLearnedOmega = 2.0 / 3.0;
-// GMRES: Arnoldi steps between host checks of the residual estimate
-constexpr int kGmCheck = 5;
 
 struct Ctx {
   const chns_mesh* m;
@@ -933,13 +873,13 @@ chns_status fcg(const Ctx& c, const T* b, T* x, const T* dinv, chns_learned* L, 
 // multi-dot launch: (chunks, nk + 1) blocks, about four per SM in total; returns the chunk count
 template <class T>
 unsigned multidot(const chns_mesh* m, const T* V, int64_t ld, int nk, const T* w, int64_t n,
-                  double* part, cudaStream_t s, const double* run = nullptr) {
+                  double* part, cudaStream_t s) {
   const int64_t want = 4 * (int64_t)m->sm_count / (nk + 1);
   const unsigned chunks = (unsigned)std::max<int64_t>(
       1, std::min<int64_t>({std::max<int64_t>(want, 8), (n + kMd2Threads - 1) / kMd2Threads,
                             (int64_t)kMdMaxBlocks}));
   note_launch();
-  k_multidot2<T><<<dim3(chunks, nk + 1), kMd2Threads, 0, s>>>(V, ld, nk, w, n, part, run);
+  k_multidot2<T><<<dim3(chunks, nk + 1), kMd2Threads, 0, s>>>(V, ld, nk, w, n, part);
   return chunks;
 }
 
@@ -950,11 +890,10 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, do
                   int max_it, int restart, T* V, T* z, int* iters, double* rnorm) {
   const int64_t n = c.n, ld = n;
   const unsigned vg = vgrid(c.m, n);
+  const unsigned mdb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(kMdBlocks, (n + 255) / 256));
   double* hdev = c.S + S_MD;
-  double* hdev2 = c.S + S_MD + 48;
-  double* G = c.m->ws.gm_small;
-  std::vector<double> res((size_t)restart + 1, 0.0);
-  std::vector<double> H((size_t)(restart + 1) * restart, 0.0), g(restart + 1), y(restart);
+  std::vector<double> H((size_t)(restart + 1) * restart, 0.0), cs(restart), sn(restart),
+      g(restart + 1), y(restart), h(restart + 2);
   int it = 0;
   double beta = 0.0;
   chns_status st;
@@ -977,16 +916,10 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, do
     if (beta <= tol_abs || it >= max_it) break;
     note_launch();
     k_scale<T><<<vg, kVecThreads, 0, c.s>>>(V, 1.0 / beta, n);
-    // device-side Arnoldi: the host only looks at the residual estimates every kGmCheck steps
-    // (and at the end of the cycle); steps past convergence are computed and discarded
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
-    CHNS_CUDA(cudaMemsetAsync(G, 0, kGmSize * sizeof(double), c.s));
-    CHNS_CUDA(cudaMemcpyAsync(G + kGmG, g.data(), sizeof(double), cudaMemcpyHostToDevice, c.s));
     int jend = 0;
-    bool stop = false, broke = false;
-    const int jmax = std::min(restart, max_it - it);
-    for (int j = 0; j < jmax && !stop; ++j) {
+    for (int j = 0; j < restart; ++j) {
       T* vj = V + (int64_t)j * ld;
       T* w = V + (int64_t)(j + 1) * ld;
       note_launch();
@@ -996,64 +929,67 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, do
         k_mul<T><<<vg, kVecThreads, 0, c.s>>>(dinv, vj, z, n);
       st = apply_T<T>(c, z, w);
       if (st != CHNS_OK) return st;
-      // classical Gram-Schmidt: h = V^T w and w.w in one pass; a second pass only when the new
-      // vector lost more than half its norm to the projection (decided on the device)
-      const int nk = j + 1;
+      // classical Gram-Schmidt: h = V^T w and w.w in one pass; a second pass only when the
+      // new vector lost more than half its norm to the projection (cancellation)
+      int nk = j + 1;
       const unsigned md2 = multidot(c.m, V, ld, nk, w, n, c.m->ws.md_part, c.s);
       note_launch();
-      k_multidot_final<<<nk + 1, kVecThreads, 0, c.s>>>(c.m->ws.md_part, (int)md2, hdev, nullptr);
-      note_launch();
-      k_gs_first<<<1, 1, 0, c.s>>>(hdev, j, G);
-      note_launch();
-      k_orth_apply<T><<<vg, kVecThreads, 0, c.s>>>(V, ld, nk, G + kGmCoef, nullptr, G + kGmFlag,
-                                                   w, n);
-      multidot(c.m, V, ld, nk, w, n, c.m->ws.md_part, c.s, G + kGmFlag);
-      note_launch();
-      k_multidot_final<<<nk + 1, kVecThreads, 0, c.s>>>(c.m->ws.md_part, (int)md2, hdev2,
-                                                         G + kGmFlag);
-      note_launch();
-      k_gs_second<<<1, 1, 0, c.s>>>(hdev2, j, G);
-      note_launch();
-      k_orth_apply<T><<<vg, kVecThreads, 0, c.s>>>(V, ld, nk, G + kGmCoef, G + kGmScale,
-                                                   nullptr, w, n);
-      note_launch();
-      k_gmres_givens<<<1, 1, 0, c.s>>>(j, G);
+      k_multidot_final<<<nk + 1, kVecThreads, 0, c.s>>>(c.m->ws.md_part, (int)md2, hdev);
       CHNS_CUDA(cudaGetLastError());
-      if ((j + 1) % kGmCheck == 0 || j + 1 == jmax) {
-        st = read_dev(c.m, G + kGmRes, res.data(), j + 1, c.s);
-        if (st != CHNS_OK) return st;
-        double brk = 0.0;
-        st = read_dev(c.m, G + kGmBreak, &brk, 1, c.s);
-        if (st != CHNS_OK) return st;
-        for (int i = jend; i <= j; ++i) {
-          jend = i + 1;
-          if (!std::isfinite(res[i])) {
-            set_error("krylov: NaN/Inf in GMRES");
-            *iters = it + jend;
-            *rnorm = res[i];
-            return CHNS_ENAN;
-          }
-          if (res[i] <= tol_abs) {
-            stop = true;
-            break;
-          }
-        }
-        if (brk != 0.0) {
-          // breakdown: |w| = 0 (the Krylov space holds the solution) or a non-finite value
-          broke = true;
-          stop = true;
-        }
+      st = read_dev(c.m, hdev, h.data(), nk + 1, c.s);
+      if (st != CHNS_OK) return st;
+      double hh = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        Hij(i, j) = h[i];
+        hh += h[i] * h[i];
       }
+      double ww = h[nk];
+      double hn2 = ww - hh;
+      if (!(hn2 > 0.5 * ww)) {
+        // re-orthogonalise: w -= V h, then a second multi-dot on the updated vector
+        orth_update<T, false>(V, ld, nk, hdev, w, n, vg, c.s);
+        multidot(c.m, V, ld, nk, w, n, c.m->ws.md_part, c.s);
+        note_launch();
+        k_multidot_final<<<nk + 1, kVecThreads, 0, c.s>>>(c.m->ws.md_part, (int)md2, hdev);
+        CHNS_CUDA(cudaGetLastError());
+        st = read_dev(c.m, hdev, h.data(), nk + 1, c.s);
+        if (st != CHNS_OK) return st;
+        double h2 = 0.0;
+        for (int i = 0; i <= j; ++i) {
+          Hij(i, j) += h[i];
+          h2 += h[i] * h[i];
+        }
+        hn2 = h[nk] - h2;
+      }
+      const double hn = std::sqrt(std::max(0.0, hn2));
+      Hij(j + 1, j) = hn;
+      if (!std::isfinite(hn)) {
+        set_error("krylov: NaN/Inf in GMRES");
+        *iters = it;
+        *rnorm = hn;
+        return CHNS_ENAN;
+      }
+      if (hn > 0.0) {
+        orth_update<T, true>(V, ld, nk, hdev, w, n, vg, c.s);
+      }
+      // Givens rotations
+      for (int i = 0; i < j; ++i) {
+        double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+        Hij(i, j) = t;
+      }
+      double a = Hij(j, j), bb = Hij(j + 1, j);
+      double rden = std::hypot(a, bb);
+      cs[j] = rden > 0.0 ? a / rden : 1.0;
+      sn[j] = rden > 0.0 ? bb / rden : 0.0;
+      Hij(j, j) = rden;
+      Hij(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      jend = j + 1;
+      if (std::fabs(g[j + 1]) <= tol_abs || it >= max_it || hn == 0.0) break;
     }
-    (void)broke;  // a zero |w| ends the cycle with a zero residual estimate (lucky breakdown)
-    it += jend;
-    // H (upper triangle of the first jend columns) and the rotated right-hand side
-    std::vector<double> Gh((size_t)kGmSize);
-    st = read_dev(c.m, G, Gh.data(), kGmSize, c.s);
-    if (st != CHNS_OK) return st;
-    for (int jj = 0; jj < jend; ++jj)
-      for (int i = 0; i <= jj; ++i) Hij(i, jj) = Gh[(size_t)jj * kGmLd + i];
-    for (int i = 0; i < jend; ++i) g[i] = Gh[kGmG + i];
     // back substitution and update x += M^-1 V y
     for (int i = jend - 1; i >= 0; --i) {
       double acc = g[i];

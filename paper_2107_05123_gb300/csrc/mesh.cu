@@ -129,7 +129,6 @@ static chns_status alloc_workspace(chns_mesh* m) {
   CHNS_CUDA(cudaMalloc(&w.coef16, (size_t)8 * N * sizeof(__nv_bfloat16)));
   CHNS_CUDA(cudaMalloc(&w.coef64, (size_t)16 * N * sizeof(double)));
   CHNS_CUDA(cudaMalloc(&w.part_big, (size_t)(m->d.n_elem / 64 + 64) * sizeof(double)));
-  CHNS_CUDA(cudaMalloc(&w.gm_small, (size_t)kGmSmallSize * sizeof(double)));
   CHNS_CUDA(cudaMalloc(&w.md_part,
                        (size_t)(CHNS_GMRES_MAX_RESTART + 2) * kMdMaxBlocks * sizeof(double)));
   CHNS_CUDA(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
@@ -168,7 +167,6 @@ static void free_mesh(chns_mesh* m) {
   dfree(w.coef64);
   dfree(w.part_big);
   dfree(w.md_part);
-  dfree(w.gm_small);
   if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
   delete m;
 }
