@@ -150,6 +150,7 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
       for (int a = 0; a < 8; ++a) fe[f][a] = fs[f * kPatchSlots + sl[a]];
     K k;
     k.setup(fe, g, p);
+    if constexpr (K::QDATA) k.bind(cf.qd, m.n_elem, e);
     T xin[NC][8];
 #pragma unroll
     for (int c = 0; c < NC; ++c)
@@ -364,11 +365,48 @@ static void launch_apply(const chns_mesh* m, chns_operator op, const DevParams& 
     case CHNS_OP_CH:
       launch_patch<ChK<T, C>, T, S, C, false>(m, p, cf, x, y, nullptr, s);
       break;
-    case CHNS_OP_MOMENTUM:
-      launch_patch<MomK<T, C>, T, S, C, false>(m, p, cf, x, y, nullptr, s);
+    case CHNS_OP_MOMENTUM: {
+      // quadrature data of the running momentum solve, when it matches this precision
+      const void* qd = sizeof(T) == sizeof(double) ? m->mq.qd64 : m->mq.qd32;
+      if (m->mq.on && qd) {
+        CoefArgs<C> cq = cf;
+        cq.qd = qd;
+        launch_patch<MomQK<T, C>, T, S, C, false>(m, p, cq, x, y, nullptr, s);
+      } else {
+        launch_patch<MomK<T, C>, T, S, C, false>(m, p, cf, x, y, nullptr, s);
+      }
       break;
+    }
   }
 }
+
+// Quadrature data of the momentum operator for the coefficients coef (FP64 and, when coef32 is
+// given, FP32), used by every momentum apply until momentum_qdata_off.
+chns_status momentum_qdata_on(const chns_mesh* m, const chns_params* prm, const chns_coef* coef64,
+                              const chns_coef* coef32, cudaStream_t s) {
+  chns_status st = check_coef(CHNS_OP_MOMENTUM, coef64);
+  if (st != CHNS_OK) return st;
+  const int64_t E = m->d.n_elem;
+  const size_t nv = (size_t)8 * kMomQ * E;
+  if (!m->mq.qd64) CHNS_CUDA(cudaMalloc(&m->mq.qd64, nv * sizeof(double)));
+  if (coef32 && !m->mq.qd32) CHNS_CUDA(cudaMalloc(&m->mq.qd32, nv * sizeof(float)));
+  const DevParams p = make_dev_params(*prm);
+  const unsigned nb = (unsigned)((E + 127) / 128);
+  note_launch();
+  k_mom_qdata<double, double><<<nb, 128, 0, s>>>(m->d, p, coef_args<double>(coef64),
+                                                 static_cast<double*>(m->mq.qd64));
+  if (coef32) {
+    note_launch();
+    k_mom_qdata<float, float><<<nb, 128, 0, s>>>(m->d, p, coef_args<float>(coef32),
+                                                 static_cast<float*>(m->mq.qd32));
+  }
+  CHNS_CUDA(cudaGetLastError());
+  m->mq.on = true;
+  m->mq.has32 = coef32 != nullptr;
+  return CHNS_OK;
+}
+
+void momentum_qdata_off(const chns_mesh* m) { m->mq.on = false; }
 
 template <class T, class S, class C>
 static void launch_diag(const chns_mesh* m, chns_operator op, const DevParams& p,

@@ -92,6 +92,13 @@ struct chns_mesh {
   int64_t n_slots = 0;
   chns::Workspace ws;
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture CUDA graphs
+  // quadrature data of the momentum operator during a momentum solve (see momentum_qdata_on)
+  struct MomQState {
+    void* qd64 = nullptr;
+    void* qd32 = nullptr;
+    bool on = false, has32 = false;
+  };
+  mutable MomQState mq;
   int red_blocks = 0;
   int sm_count = 0;
 };
@@ -154,6 +161,11 @@ chns_status apply_poisson_cg(const chns_mesh* m, const chns_params* prm, const c
                              const void* z, const void* p_old, void* p_new, void* y,
                              chns_precision prec, double* S_cg, int par, cudaStream_t s,
                              bool fcg = false);
+// Precompute the momentum operator's quadrature data for coefficients that stay fixed over the
+// applies that follow (a Krylov solve); momentum_qdata_off returns to on-the-fly evaluation.
+chns_status momentum_qdata_on(const chns_mesh* m, const chns_params* prm, const chns_coef* coef64,
+                              const chns_coef* coef32, cudaStream_t s);
+void momentum_qdata_off(const chns_mesh* m);
 chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
                     const chns_coef* coef, void* d, chns_precision prec, cudaStream_t s);
 // 2x2 nodal blocks of the CH Jacobian, d4 = [d_pp, d_pm, d_mp, d_mm] x n_nodes (FP64 or FP32)

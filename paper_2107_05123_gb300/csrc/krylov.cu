@@ -1068,6 +1068,11 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
   const Workspace& ws = m->ws;
   const int nc = op_ncomp(op);
   const int64_t n = nc * m->d.n_nodes;
+  // momentum quadrature data (set up below) is valid only within this solve
+  struct QdGuard {
+    const chns_mesh* m;
+    ~QdGuard() { momentum_qdata_off(m); }
+  } qd_guard{m};
   cudaEvent_t e0, e1;
   CHNS_CUDA(cudaEventCreate(&e0));
   CHNS_CUDA(cudaEventCreate(&e1));
@@ -1147,6 +1152,10 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
     if (c.inner == CHNS_FP64) {
       st = make_dinv64();
       if (st != CHNS_OK) return st;
+      if (op == CHNS_OP_MOMENTUM) {
+        st = momentum_qdata_on(m, prm, coef, nullptr, s);
+        if (st != CHNS_OK) return st;
+      }
       int its = 0;
       double rn = 0.0;
       if (cheb) {
@@ -1178,6 +1187,10 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
       chns_coef coef32;
       st = make_reduced_coef(m, coef, CHNS_FP32, &coef32, s);
       if (st != CHNS_OK) return st;
+      if (op == CHNS_OP_MOMENTUM) {
+        st = momentum_qdata_on(m, prm, coef, &coef32, s);
+        if (st != CHNS_OK) return st;
+      }
       float* r32 = ws.v32[0];
       float* d32 = ws.v32[1];
       float* dinv32 = nullptr;

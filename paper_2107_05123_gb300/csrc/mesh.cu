@@ -167,6 +167,8 @@ static void free_mesh(chns_mesh* m) {
   dfree(w.coef64);
   dfree(w.part_big);
   dfree(w.md_part);
+  dfree(m->mq.qd64);
+  dfree(m->mq.qd32);
   if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
   delete m;
 }

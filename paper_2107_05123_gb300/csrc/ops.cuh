@@ -15,6 +15,7 @@ struct CoefArgs {
   const C* u[3];    // advecting velocity (u_hat or u~)
   const C* mu;      // mu~
   float phi_shift;  // added to the stored phi values: -1 for bfloat16 storage, else 0
+  const void* qd = nullptr;  // quadrature data of operators that precompute it (MomQK)
 };
 
 // Gather phi~ of an element. In bfloat16 storage the field is s = 1 + phi~, whose relative
@@ -64,6 +65,7 @@ __device__ __forceinline__ void stiff_local(const T c[8], const Geo<T>& g, const
 
 template <class T, class C>
 struct PoissonK {
+  static constexpr bool QDATA = false;
   // CTAs of the patch apply resident per SM that the register allocation must allow (FP32: 6,
   // i.e. at most 42 registers; FP64: 3)
   static constexpr int MIN_CTAS = sizeof(T) == 4 ? 6 : 3;
@@ -91,6 +93,7 @@ struct PoissonK {
 // (w, rho~ u) per component (Def. weak_VMS_disc_vel_update); Dirichlet rows are identity.
 template <class T, class C>
 struct MassK {
+  static constexpr bool QDATA = false;
   static constexpr int MIN_CTAS = sizeof(T) == 4 ? 5 : 3;
   static constexpr int NC = 3;
   static constexpr bool DIR = true;
@@ -132,6 +135,7 @@ struct MassK {
 //   row mu : -1/2 (q, dmu) + 1/2 (q, psi''(phi~) dphi) + Cn^2/2 (grad q, grad dphi)
 template <class T, class C>
 struct ChK {
+  static constexpr bool QDATA = false;
   static constexpr int MIN_CTAS = sizeof(T) == 4 ? 4 : 1;
   static constexpr int NC = 2;
   static constexpr bool DIR = false;
@@ -243,6 +247,7 @@ __device__ __forceinline__ VmsQ<T> vms_at(const T pe[8], const T ue[3][8], const
 
 template <class T, class C>
 struct MomK {
+  static constexpr bool QDATA = false;
   // FP32: two CTAs per SM (at most 128 registers) instead of the one that 217 registers allow
   static constexpr int MIN_CTAS = sizeof(T) == 4 ? 2 : 1;
   static constexpr int NC = 3;
@@ -288,6 +293,91 @@ struct MomK {
         T V[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) V[d] = J * (c.e * vg[d] + R * c.t[d]);
+        add_test<Q>(r[k], J * s, V, g);
+      }
+    });
+  }
+};
+
+// Quadrature data of the momentum operator: per element and quadrature point the 11 values
+// the linear operator needs (a0, b[3], bp[3], e, t[3] of VmsQ), computed once per solve while
+// the coefficients are fixed, stored value-major, qd[(q * kMomQ + v) * n_elem + e], so that a
+// warp's loads are coalesced. The apply then reads 88 values per element instead of
+// re-evaluating tau_m and the RBVMS vectors at every quadrature point (FP64 arithmetic is the
+// bound of that evaluation on GB300).
+constexpr int kMomQ = 11;
+
+template <class T, class C>
+__global__ void __launch_bounds__(128)
+k_mom_qdata(MeshDev m, DevParams p, CoefArgs<C> cf, T* __restrict__ qd) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.n_elem) return;
+  int idx[8];
+  load_corners(m, e, idx);
+  const Geo<T> g = geometry<T>(m, e);
+  MomK<T, C> k;
+  k.load(m, p, cf, idx, g);
+  const int64_t E = m.n_elem;
+  for_qp([&](auto QC) {
+    constexpr int Q = decltype(QC)::value;
+    const VmsQ<T> c = vms_at<Q>(k.pe, k.ue, k.me, g, p);
+    T* q = qd + (int64_t)Q * kMomQ * E + e;
+    q[0] = c.a0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      q[(1 + d) * E] = c.b[d];
+      q[(4 + d) * E] = c.bp[d];
+      q[(8 + d) * E] = c.t[d];
+    }
+    q[7 * E] = c.e;
+  });
+}
+
+// The momentum operator from quadrature data (same arithmetic as MomK::apply).
+template <class T, class C>
+struct MomQK {
+  static constexpr bool QDATA = true;
+  static constexpr int MIN_CTAS = sizeof(T) == 4 ? 2 : 1;
+  static constexpr int NC = 3;
+  static constexpr bool DIR = true;
+  static constexpr bool DIAG_PER_COMP = false;
+  static constexpr int NF = 1;  // (phi~ only to keep the shared-memory layout of the kernel)
+  const T* qd = nullptr;
+  int64_t ne = 0, e = 0;
+  __device__ __forceinline__ void setup(const T[NF][8], const Geo<T>&, const DevParams&) {}
+  __device__ __forceinline__ void bind(const void* q, int64_t n_elem, int64_t elem) {
+    qd = static_cast<const T*>(q);
+    ne = n_elem;
+    e = elem;
+  }
+  __device__ __forceinline__ void apply(const Geo<T>& g, const DevParams&, const T x[NC][8],
+                                        T r[NC][8]) const {
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) r[k][a] = T(0);
+    const T J = g.detJ;
+    for_qp([&](auto QC) {
+      constexpr int Q = decltype(QC)::value;
+      const T* q = qd + (int64_t)Q * kMomQ * ne + e;
+      const T a0 = __ldg(q);
+      T b[3], bp[3], t[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        b[d] = __ldg(q + (1 + d) * ne);
+        bp[d] = __ldg(q + (4 + d) * ne);
+        t[d] = __ldg(q + (8 + d) * ne);
+      }
+      const T ce = __ldg(q + 7 * ne);
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        T v, vg[3];
+        vg_at<Q>(x[k], g, v, vg);
+        T s = a0 * v + b[0] * vg[0] + b[1] * vg[1] + b[2] * vg[2];
+        T R = a0 * v + bp[0] * vg[0] + bp[1] * vg[1] + bp[2] * vg[2];
+        T V[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) V[d] = J * (ce * vg[d] + R * t[d]);
         add_test<Q>(r[k], J * s, V, g);
       }
     });
