@@ -243,8 +243,8 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     achieved = alg_bytes / t_apply / 1e9
     # DRAM bytes of one launch from an ncu capture of this kernel on this workload
-    # (dram__bytes.sum.per_second x gpu__time_duration: 667.8 GB/s x 17.344 us; profiles/
-    # poisson_apply_fp32_rising_drop.md); --traffic overrides it
+    # (dram__bytes.sum.per_second x gpu__time_duration: 667.8 GB/s x 17.344 us, summarised
+    # under profiles/); --traffic overrides it
     traffic = args.traffic if args.traffic is not None else APPLY_DRAM_BYTES
 
     # ---- end to end: one Poisson solve through the C ABI with pinned host buffers
