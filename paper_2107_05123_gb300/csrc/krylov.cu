@@ -289,17 +289,6 @@ k_multidot_final(const double* __restrict__ part, int nb, double* __restrict__ o
   if (threadIdx.x == 0) out[blockIdx.x] = t[0];
 }
 
-// w -= sum_k h_k V_k
-template <class T>
-__global__ void k_orth_update(const T* __restrict__ V, int64_t ld, int nk,
-                              const double* __restrict__ h, T* __restrict__ w, int64_t n) {
-  GRID_LOOP(i, n) {
-    double acc = (double)w[i];
-    for (int k = 0; k < nk; ++k) acc -= h[k] * (double)V[(int64_t)k * ld + i];
-    w[i] = (T)acc;
-  }
-}
-
 // x += B^-1 (sum_k y_k V_k) with 2x2 nodal blocks
 template <class T>
 __global__ void k_gmres_update_b2(const T* __restrict__ V, int64_t ld, int nk,
