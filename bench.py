@@ -403,8 +403,9 @@ def run_learned(args):
     0.05-0.12, Cn 0.01, density ratio 1000): training pairs from the pressure-Poisson solves of
     `--learned-steps` time steps (iterates of FP64 Jacobi-PCG, every 8th, at most 24 per solve),
     energy-norm training on the GPU, then the pressure-Poisson solves of one more step from the
-    same state with Jacobi-PCG (FP32 + FP64 refinement), FCG + learned correction (same
-    precision) and plain FP64 Jacobi-PCG. Returns the summary object of the bench line."""
+    same state in mixed precision with Jacobi-PCG, Chebyshev-PCG (degree 3) and FCG + learned
+    correction, and the same step on the all-FP64 path (Jacobi). Returns the summary object of the
+    bench line."""
     import torch
 
     from chns_workloads import configs
@@ -452,23 +453,29 @@ def run_learned(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     res = {}
-    solvers = {
-        "jacobi_fp32": capi.make_solver(capi.KSP_CG, capi.PC_JACOBI, 1e-8, 20000, 30, capi.FP32,
-                                        1e-6, 30, check_every=8),
-        "learned_fp32": capi.make_solver(capi.KSP_FCG, capi.PC_LEARNED, 1e-8, 20000, 30,
-                                         capi.FP32, 1e-6, 30, check_every=8, learned=net),
-        "jacobi_fp64": capi.make_solver(capi.KSP_CG, capi.PC_JACOBI, 1e-8, 20000, 30, capi.FP64,
-                                        check_every=8),
+    # one more step from the same state: mixed precision (FP32 Krylov + FP32 applies + FP64
+    # refinement) with three pressure preconditioners, and the all-FP64 path with Jacobi
+    runs = {
+        "mixed_jacobi": params(pp=capi.make_solver(
+            capi.KSP_CG, capi.PC_JACOBI, 1e-8, 20000, 30, capi.FP32, 1e-6, 30, check_every=8)),
+        "mixed_chebyshev3": params(pp=capi.make_solver(
+            capi.KSP_CG, capi.PC_CHEBYSHEV, 1e-8, 20000, 3, capi.FP32, 1e-6, 30, check_every=8)),
+        "mixed_learned": params(pp=capi.make_solver(
+            capi.KSP_FCG, capi.PC_LEARNED, 1e-8, 20000, 30, capi.FP32, 1e-6, 30, check_every=8,
+            learned=net)),
+        "plain_fp64_jacobi": default_step_params(rtol=1e-8, inner=capi.FP64, pp_check_every=8),
     }
-    for name, sol in solvers.items():
+    runs["plain_fp64_jacobi"].vp.max_it = 20000
+    for name, sp in runs.items():
         try:
-            st = capi.chns_step(mesh.handle, DeviceState(snap).c, prm, params(pp=sol))
+            st = capi.chns_step(mesh.handle, DeviceState(snap).c, prm, sp)
         except capi.ChnsError as e:
             st = getattr(e, "stats", None)
             res[name] = {"error": str(e)}
             if st is None:
                 continue
         res.setdefault(name, {}).update(
+            ms_step=round(st.ms_total, 2),
             pp_iters=[st.pp[l].iterations for l in range(2)],
             pp_ms=[round(st.pp[l].ms, 3) for l in range(2)],
             fallbacks=[st.pp[l].fallbacks for l in range(2)],
@@ -483,7 +490,7 @@ def run_learned(args):
             "train_ms_per_iteration": round(1e3 * t_train / max(args.learned_iters, 1), 3),
             "energy_loss_first_100": float(loss[:100].mean()) if len(loss) else None,
             "energy_loss_last_500": float(loss[-500:].mean()) if len(loss) else None,
-            "pp_solves_next_step": res, "small_drops": small,
+            "next_step": res, "small_drops": small,
             "wall_s": round(time.perf_counter() - t_all, 1)}
 
 
@@ -697,9 +704,9 @@ def main():
     ap.add_argument("--learned-iters", type=int, default=6000, help="training iterations")
     ap.add_argument("--learned-lr", type=float, default=3e-4)
     ap.add_argument("--learned-grid", type=int, default=64, help="grid size D of the network")
-    ap.add_argument("--mode", choices=["bench", "apply", "pp", "large"], default="bench",
+    ap.add_argument("--mode", choices=["bench", "apply", "pp", "large", "learned"], default="bench",
                     help="apply / pp: time only the roofline kernel / the Poisson solve "
-                         "(profiling); large: only the Rayleigh-Taylor workload")
+                         "(profiling); large / learned: only that part of the bench line")
     args = ap.parse_args()
     if args.mode == "apply":
         run_apply_only(args)
@@ -707,6 +714,8 @@ def main():
         run_pp_only(args)
     elif args.mode == "large":
         print(json.dumps(run_large(args)))
+    elif args.mode == "learned":
+        print(json.dumps(run_learned(args)))
     elif args.impl == "reference":
         run_reference(args)
     else:
