@@ -133,6 +133,22 @@ chns_status chns_mesh_node_coords(const chns_mesh* mesh, uint32_t* coords);
 chns_status chns_mesh_boundary(const chns_mesh* mesh, uint8_t* flags);
 void chns_mesh_destroy(chns_mesh* mesh);
 
+/* Launch configuration of the operator applies on this mesh (performance only: results agree
+ * to rounding, since the order of floating-point additions into shared nodes differs).
+ *   CHNS_APPLY_PATCH:  one CTA per patch (a run of <= 256 Morton-consecutive elements whose
+ *                      nodes are gathered once into shared memory).
+ *   CHNS_APPLY_STREAM: persistent CTAs, each walking the patches blockIdx, blockIdx + grid, ...
+ *                      and gathering the next patch's node values into shared memory (cp.async)
+ *                      while the current patch is computed. Used by the FP32 Poisson and mass
+ *                      applies (including the apply fused into CG); the other operators and
+ *                      precisions keep CHNS_APPLY_PATCH.
+ *   CHNS_APPLY_AUTO:   CHNS_APPLY_STREAM when the mesh has at least 16 patches per SM.
+ * max_ctas bounds the persistent grid (0: as many CTAs as the device holds at once). Errors:
+ * EINVAL for a null mesh, an unknown kernel or max_ctas < 0. Not thread-safe against applies
+ * running on the same mesh from other host threads. */
+typedef enum { CHNS_APPLY_AUTO = 0, CHNS_APPLY_PATCH = 1, CHNS_APPLY_STREAM = 2 } chns_apply_kernel;
+chns_status chns_mesh_set_apply_config(chns_mesh* mesh, chns_apply_kernel kernel, int64_t max_ctas);
+
 /* ---------------------------------------------------------------- operator applies (Sec. 4.1)
  * y = A x, matrix-free: gather (with hanging interpolation) -> element quadrature -> scatter-add
  * (transpose incl. hanging). x and y must not alias. */

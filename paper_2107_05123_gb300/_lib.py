@@ -29,6 +29,7 @@ OP_POISSON, OP_MASS, OP_CH, OP_MOMENTUM = 0, 1, 2, 3
 OP_NCOMP = {OP_POISSON: 1, OP_MASS: 3, OP_CH: 2, OP_MOMENTUM: 3}
 # chns_ksp / chns_pc
 KSP_CG, KSP_GMRES, KSP_FCG = 0, 1, 2
+APPLY_AUTO, APPLY_PATCH, APPLY_STREAM = 0, 1, 2
 PC_NONE, PC_JACOBI, PC_LEARNED, PC_CHEBYSHEV = 0, 1, 2, 3
 
 
@@ -97,6 +98,7 @@ _SIGS = {
     "chns_mesh_node_coords": ([_P, _P], C.c_int),
     "chns_mesh_boundary": ([_P, _P], C.c_int),
     "chns_mesh_destroy": ([_P], None),
+    "chns_mesh_set_apply_config": ([_P, C.c_int, C.c_int64], C.c_int),
     "chns_apply_poisson": ([_P, C.POINTER(chns_params), C.POINTER(chns_coef), _P, _P, C.c_int, _P], C.c_int),
     "chns_apply_mass": ([_P, C.POINTER(chns_params), C.POINTER(chns_coef), _P, _P, C.c_int, _P], C.c_int),
     "chns_apply_ch": ([_P, C.POINTER(chns_params), C.POINTER(chns_coef), _P, _P, C.c_int, _P], C.c_int),
@@ -235,6 +237,11 @@ def chns_mesh_boundary(mesh, n_nodes: int) -> np.ndarray:
     out = np.zeros(n_nodes, dtype=np.uint8)
     _check(LIB.chns_mesh_boundary(mesh, out.ctypes.data), "chns_mesh_boundary")
     return out
+
+
+def chns_mesh_set_apply_config(mesh, kernel: int, max_ctas: int = 0):
+    _check(LIB.chns_mesh_set_apply_config(mesh, int(kernel), int(max_ctas)),
+           "chns_mesh_set_apply_config")
 
 
 def chns_mesh_destroy(mesh):

@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(MeshDev m, DevParams p,
 //  5. each regular slot is written once: a plain store when the patch owns the node, a global
 //     atomic add otherwise (nodes on the patch boundary). y must be zero on entry.
 // With PQ the block sums of the element energies x_e . A_e x_e (summing to x^T A x) are added to
-// S_cg[kCgPq0 + par] with an FP64 atomic.
+// S_cg[kCgPq0 + par] with an FP64 atomic; operators with ENERGY form them from their quadrature
+// data (non-negative terms), the others as x_e . (A_e x_e) in double-float.
 template <class K, class T, class S, class C, bool PQ, bool CGP>
 __global__ void __launch_bounds__(kPatchElems, K::MIN_CTAS)
 k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S* __restrict__ y,
@@ -75,16 +76,12 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
       S_cg[kCgRr0 + (par ^ 1)] = 0.0;
     }
   }
-  // the element's local corner slots and level are loaded first, so that their latency overlaps
-  // the gather of the patch's nodes
+  // the element's local corner slots (with its level) are loaded first, so that their latency
+  // overlaps the gather of the patch's nodes
   const int64_t e = (int64_t)m.patch_elem[pidx] + threadIdx.x;
   const bool has_elem = e < m.patch_elem[pidx + 1];
   uint4 lp = make_uint4(0, 0, 0, 0);
-  int lev = 0;
-  if (has_elem) {
-    lp = __ldg(m.eloc + e);
-    lev = __ldg(m.level + e);
-  }
+  if (has_elem) lp = __ldg(m.eloc + e);
   if (CGP) __syncthreads();
   // 1. regular slots
   {
@@ -139,7 +136,8 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
   // 3. elements
   typename Acc<T>::type en[1] = {Acc<T>::zero()};
   if (has_elem) {
-    const int sl[8] = {(int)(lp.x & 0xffff), (int)(lp.x >> 16), (int)(lp.y & 0xffff),
+    const int lev = (int)(lp.x >> kElocLevelShift) & kElocLevelMask;
+    const int sl[8] = {(int)(lp.x & kElocSlotMask), (int)(lp.x >> 16), (int)(lp.y & 0xffff),
                        (int)(lp.y >> 16),    (int)(lp.z & 0xffff), (int)(lp.z >> 16),
                        (int)(lp.w & 0xffff), (int)(lp.w >> 16)};
     const Geo<T> g = level_geometry<T>(m, lev);
@@ -157,12 +155,16 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
 #pragma unroll
       for (int a = 0; a < 8; ++a) xin[c][a] = xs[c * kPatchSlots + sl[a]];
     T r[NC][8];
-    k.apply(g, p, xin, r);
+    constexpr bool EF = PQ && HasEnergy<K>::value;
+    if constexpr (EF)
+      Acc<T>::add(en[0], k.apply_energy(g, p, xin, r));
+    else
+      k.apply(g, p, xin, r);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
-        if (PQ) Acc<T>::fma(en[0], xin[c][a], r[c][a]);
+        if (PQ && !EF) Acc<T>::fma(en[0], xin[c][a], r[c][a]);
         atomicAdd(ys + c * kPatchSlots + sl[a], r[c][a]);
       }
   }
@@ -227,6 +229,307 @@ static void launch_patch(const chns_mesh* m, const DevParams& p, const CoefArgs<
   note_launch();
   k_apply_patch<K, T, S, C, PQ, CGP><<<(unsigned)m->d.n_patch, kPatchElems, smem, s>>>(
       m->d, p, cf, x, y, S_cg, par, fcg, z, pout);
+}
+
+// ---- persistent, software-pipelined patch apply (FP32/FP64 vectors and coefficients of one type).
+// Each CTA walks the patches blockIdx.x, blockIdx.x + gridDim.x, ... With the patches of one CTA
+// numbered k = 0, 1, ..., iteration k computes patch k (phases 1-5 of k_apply_patch) while
+//   - the node values of patch k+1 (x, z for CGP, coefficient fields), its element slot table
+//     (with the levels) and the parents of its first kPqStage hanging slots are in flight into
+//     the other of two shared-memory stages,
+//   - the slot table of patch k+2 is in flight into the third of three index buffers, and
+//   - the patch-table entries of patch k+3 are in flight into a ring of four,
+// all as cp.async copies, so that no global load of any kind remains in the per-patch chain. The
+// sums of PQ are accumulated over all patches of the CTA and added once.
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+template <int B>
+__device__ __forceinline__ void cp_async_b(void* dst, const void* src) {
+  static_assert(B == 4 || B == 8 || B == 16, "cp.async of 4, 8 or 16 bytes");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (B == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(B) : "memory");
+}
+
+constexpr int kPqStage = 128;  // hanging slots per patch whose parents are staged (rest: global)
+
+template <class K, class T, bool CGP>
+constexpr int stream_stage_arrays() {
+  return (CGP ? 2 : 1) * K::NC + K::NF;
+}
+template <class K, class T, bool CGP>
+constexpr size_t stream_smem() {
+  // two value stages, the accumulators, three slot-index buffers, two stages of element slot
+  // tables and hanging parents, the patch-table ring
+  return (size_t)(2 * stream_stage_arrays<K, T, CGP>() + K::NC) * kPatchSlots * sizeof(T) +
+         (size_t)3 * kPatchSlots * sizeof(int32_t) + (size_t)2 * kPatchElems * sizeof(uint4) +
+         (size_t)2 * kPqStage * sizeof(ushort4) + (size_t)4 * 8 * sizeof(int32_t);
+}
+
+template <class K, class T, bool PQ, bool CGP>
+__global__ void __launch_bounds__(kPatchElems, K::STREAM_CTAS)
+k_apply_stream(MeshDev m, DevParams p, CoefArgs<T> cf, const T* __restrict__ x, T* __restrict__ y,
+               double* __restrict__ S_cg, int par, int fcg, const T* __restrict__ zcg,
+               T* __restrict__ pout) {
+  constexpr int NC = K::NC, NF = K::NF, NA = stream_stage_arrays<K, T, CGP>();
+  static_assert(!K::QDATA, "per-element quadrature data is not staged by this kernel");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* vb = reinterpret_cast<T*>(smem_raw);                             // [2][NA][kPatchSlots]
+  T* ys = vb + 2 * NA * kPatchSlots;                                  // [NC][kPatchSlots]
+  int32_t* ib = reinterpret_cast<int32_t*>(ys + NC * kPatchSlots);    // [3][kPatchSlots]
+  uint4* elb = reinterpret_cast<uint4*>(ib + 3 * kPatchSlots);        // [2][kPatchElems]
+  ushort4* pqb = reinterpret_cast<ushort4*>(elb + 2 * kPatchElems);   // [2][kPqStage]
+  int32_t* mt = reinterpret_cast<int32_t*>(pqb + 2 * kPqStage);
+  // mt: [4][8] = first slot, end slot, regular slots, first element, end element
+  const int np = (int)m.n_patch, G = gridDim.x, tid = threadIdx.x;
+  const int64_t N = m.n_nodes;
+  // the arrays gathered per slot, in stage order: x components, z components (CGP), fields
+  const T* src_arr[NA];
+  {
+    const T* fptr[5] = {cf.phi, cf.u[0], cf.u[1], cf.u[2], cf.mu};
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      src_arr[c] = x + c * N;
+      if (CGP) src_arr[NC + c] = zcg + c * N;
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) src_arr[(CGP ? 2 : 1) * NC + f] = fptr[f];
+  }
+  __shared__ T s_beta;
+  if (CGP && tid == 0) {
+    double bn, bd;
+    if (fcg) {
+      bn = -S_cg[kFcgAlpha] * S_cg[kFcgZq0 + (par ^ 1)];
+      bd = S_cg[kFcgRz0 + (par ^ 1)];
+    } else {
+      bn = S_cg[kCgRz0 + par];
+      bd = S_cg[kCgRzPrev];
+    }
+    s_beta = (T)(bd != 0.0 ? bn / bd : 0.0);
+    if (blockIdx.x == 0) {
+      S_cg[kCgRz0 + (par ^ 1)] = 0.0;
+      S_cg[kCgRr0 + (par ^ 1)] = 0.0;
+    }
+  }
+  // patch-table entries of patch q into ring entry r (threads 0-4, one word each)
+  auto issue_meta = [&](int q, int r) {
+    if (tid < 5) {
+      const int32_t* src = tid < 2 ? m.patch_slot + q + tid
+                                   : tid == 2 ? m.patch_nreg + q : m.patch_elem + q + (tid - 3);
+      cp_async_b<4>(mt + 8 * r + tid, src);
+    }
+  };
+  // slot table of patch q (ring entry r landed) into index buffer bi
+  auto issue_idx = [&](int r, int bi) {
+    const int s0 = mt[8 * r], nr = mt[8 * r + 2];
+    int32_t* dst = ib + bi * kPatchSlots;
+    for (int i = tid; i < nr; i += kPatchElems) cp_async_b<4>(dst + i, m.slot_node + s0 + i);
+  };
+  // everything patch q (ring entry r) needs besides its slot table, into stage st: node values
+  // (from index buffer bi: each thread reads only entries its own copies wrote), element slot
+  // tables, parents of the first kPqStage hanging slots
+  auto issue_stage = [&](int r, int st, int bi) {
+    const int s0 = mt[8 * r], s1 = mt[8 * r + 1], nr = mt[8 * r + 2];
+    const int e0 = mt[8 * r + 3], e1 = mt[8 * r + 4];
+    const int32_t* src = ib + bi * kPatchSlots;
+    T* dst = vb + st * NA * kPatchSlots;
+    for (int i = tid; i < nr; i += kPatchElems) {
+      const int g = src[i] & kNodeMask;
+#pragma unroll
+      for (int a = 0; a < NA; ++a) cp_async_b<sizeof(T)>(dst + a * kPatchSlots + i, src_arr[a] + g);
+    }
+    if (e0 + tid < e1) cp_async_b<16>(elb + st * kPatchElems + tid, m.eloc + e0 + tid);
+    if (tid < kPqStage && nr + tid < s1 - s0)
+      cp_async_b<8>(pqb + st * kPqStage + tid, m.slot_par + s0 + nr + tid);
+  };
+  // prologue: ring entries of patches 0-2, slot tables of patches 0-1, stage 0 of patch 0
+  int pid = blockIdx.x;
+  for (int j = 0; j < 3; ++j)
+    if (pid + j * G < np) issue_meta(pid + j * G, j);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  for (int j = 0; j < 2; ++j)
+    if (pid + j * G < np) issue_idx(j, j);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  if (pid < np) issue_stage(0, 0, 0);
+  cp_async_commit();
+  typename Acc<T>::type en[1] = {Acc<T>::zero()};
+  for (int k = 0; pid < np; pid += G, ++k) {
+    const int st = k & 1, bc = k % 3, rc = k & 3;
+    cp_async_wait_all();
+    __syncthreads();  // stage k, slot table k+1 and ring entry k+2 have landed for every thread
+    if (pid + G < np) issue_stage((k + 1) & 3, st ^ 1, (k + 1) % 3);
+    if (pid + 2 * G < np) issue_idx((k + 2) & 3, (k + 2) % 3);
+    if (pid + 3 * G < np) issue_meta(pid + 3 * G, (k + 3) & 3);
+    cp_async_commit();
+    const int s0 = mt[8 * rc], ns = mt[8 * rc + 1] - s0, nreg = mt[8 * rc + 2];
+    const int e0 = mt[8 * rc + 3], ne = mt[8 * rc + 4] - e0;
+    T* xs = vb + st * NA * kPatchSlots;
+    const T* zs = xs + NC * kPatchSlots;
+    T* fs = xs + (CGP ? 2 : 1) * NC * kPatchSlots;
+    const int32_t* ic = ib + bc * kPatchSlots;
+    const ushort4* pq = pqb + st * kPqStage;
+    auto parents = [&](int i) { return i - nreg < kPqStage ? pq[i - nreg] : m.slot_par[s0 + i]; };
+    // 1. regular slots: CG direction update, Dirichlet zeros, accumulators cleared
+    for (int i = tid; i < nreg; i += kPatchElems) {
+      const int32_t v = ic[i];
+      const bool dir = K::DIR && (v & kDirBit);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        T xv = xs[c * kPatchSlots + i];
+        if (CGP) {
+          xv = zs[c * kPatchSlots + i] + s_beta * xv;
+          (pout + c * N)[v & kNodeMask] = xv;  // patches sharing the node store the same value
+        }
+        xs[c * kPatchSlots + i] = dir ? T(0) : xv;
+        ys[c * kPatchSlots + i] = T(0);
+      }
+    }
+    __syncthreads();
+    // 2. hanging slots
+    for (int i = nreg + tid; i < ns; i += kPatchElems) {
+      const ushort4 q = parents(i);
+      const bool four = q.z != 0xffff;
+      const T w = four ? T(0.25) : T(0.5);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T* a = xs + c * kPatchSlots;
+        T v = a[q.x] + a[q.y];
+        if (four) v += a[q.z] + a[q.w];
+        xs[c * kPatchSlots + i] = w * v;
+        ys[c * kPatchSlots + i] = T(0);
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const T* a = fs + f * kPatchSlots;
+        T v = a[q.x] + a[q.y];
+        if (four) v += a[q.z] + a[q.w];
+        fs[f * kPatchSlots + i] = w * v;
+      }
+    }
+    __syncthreads();
+    // 3. elements
+    if (tid < ne) {
+      const uint4 lp = elb[st * kPatchElems + tid];
+      const int lev = (int)(lp.x >> kElocLevelShift) & kElocLevelMask;
+      const int sl[8] = {(int)(lp.x & kElocSlotMask), (int)(lp.x >> 16), (int)(lp.y & 0xffff),
+                         (int)(lp.y >> 16),    (int)(lp.z & 0xffff), (int)(lp.z >> 16),
+                         (int)(lp.w & 0xffff), (int)(lp.w >> 16)};
+      const Geo<T> g = level_geometry<T>(m, lev);
+      T fe[NF][8];
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int a = 0; a < 8; ++a) fe[f][a] = fs[f * kPatchSlots + sl[a]];
+      K kk;
+      kk.setup(fe, g, p);
+      T xin[NC][8];
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int a = 0; a < 8; ++a) xin[c][a] = xs[c * kPatchSlots + sl[a]];
+      T r[NC][8];
+      constexpr bool EF = PQ && HasEnergy<K>::value;
+      if constexpr (EF)
+        Acc<T>::add(en[0], kk.apply_energy(g, p, xin, r));
+      else
+        kk.apply(g, p, xin, r);
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          if (PQ && !EF) Acc<T>::fma(en[0], xin[c][a], r[c][a]);
+          atomicAdd(ys + c * kPatchSlots + sl[a], r[c][a]);
+        }
+    }
+    __syncthreads();
+    // 4. hanging slots -> parents
+    for (int i = nreg + tid; i < ns; i += kPatchElems) {
+      const ushort4 q = parents(i);
+      const bool four = q.z != 0xffff;
+      const T w = four ? T(0.25) : T(0.5);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        T* a = ys + c * kPatchSlots;
+        const T v = w * a[i];
+        atomicAdd(a + q.x, v);
+        atomicAdd(a + q.y, v);
+        if (four) {
+          atomicAdd(a + q.z, v);
+          atomicAdd(a + q.w, v);
+        }
+      }
+    }
+    __syncthreads();
+    // 5. regular slots -> global (owned: store; shared with other patches: atomic add)
+    for (int i = tid; i < nreg; i += kPatchElems) {
+      const int32_t v = ic[i];
+      if (K::DIR && (v & kDirBit)) continue;
+      const int g = v & kNodeMask;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T val = ys[c * kPatchSlots + i];
+        T* yc = y + c * N;
+        if (v & kOwnBit)
+          yc[g] = val;
+        else
+          atomic_add(yc + g, val);
+      }
+    }
+    // the next iteration's first barrier orders these reads before the buffers are refilled
+  }
+  cp_async_wait_all();
+  if (PQ) {
+    double tot[1];
+    block_sum<1, kPatchElems>(en, tot);
+    if (tid == 0) atomicAdd(S_cg + kCgPq0 + par, tot[0]);
+  }
+}
+
+// Resident CTAs of one instantiation on this device (queried once per instantiation).
+template <class Fn>
+static int resident_ctas(Fn fn, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPatchElems, smem) != cudaSuccess)
+    per_sm = 1;
+  return std::max(per_sm, 1);
+}
+
+template <class K, class T, bool PQ, bool CGP>
+static void launch_stream(const chns_mesh* m, const DevParams& p, const CoefArgs<T>& cf,
+                          const T* x, T* y, double* S_cg, cudaStream_t s, const T* z = nullptr,
+                          T* pout = nullptr, int par = 0, int fcg = 0) {
+  constexpr size_t smem = stream_smem<K, T, CGP>();
+  static int per_sm = 0;  // per instantiation
+  if (per_sm == 0) {
+    cudaFuncSetAttribute(k_apply_stream<K, T, PQ, CGP>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    per_sm = resident_ctas(k_apply_stream<K, T, PQ, CGP>, smem);
+  }
+  int64_t grid = (int64_t)per_sm * std::max(m->sm_count, 1);
+  if (m->apply_max_ctas > 0) grid = std::min(grid, m->apply_max_ctas);
+  grid = std::max<int64_t>(1, std::min(grid, m->d.n_patch));
+  note_launch();
+  k_apply_stream<K, T, PQ, CGP><<<(unsigned)grid, kPatchElems, smem, s>>>(m->d, p, cf, x, y, S_cg,
+                                                                           par, fcg, z, pout);
+}
+
+// The persistent kernel pays off once every resident CTA has several patches to walk; operators
+// with per-element quadrature data, BF16 coefficients (2-byte copies) and FP64 (ALU bound) keep
+// one CTA per patch.
+template <class K, class T, class S, class C>
+static bool use_stream(const chns_mesh* m) {
+  if (!(std::is_same<T, float>::value && std::is_same<S, T>::value && std::is_same<C, T>::value))
+    return false;
+  if (K::QDATA || K::STREAM_CTAS == 0) return false;
+  if (m->apply_kernel == CHNS_APPLY_PATCH) return false;
+  if (m->apply_kernel == CHNS_APPLY_STREAM) return true;
+  return m->d.n_patch >= (int64_t)kStreamMinPatchesPerSm * std::max(m->sm_count, 1);
 }
 
 // Reference (corner a, slot k) -> node reference with Dirichlet bit and its weight, or -1.
@@ -357,9 +660,23 @@ static void launch_apply(const chns_mesh* m, chns_operator op, const DevParams& 
                          const CoefArgs<C>& cf, const S* x, S* y, cudaStream_t s) {
   switch (op) {
     case CHNS_OP_POISSON:
+      if constexpr (std::is_same<T, float>::value && std::is_same<S, T>::value &&
+                    std::is_same<C, T>::value) {
+        if (use_stream<PoissonK<T, C>, T, S, C>(m)) {
+          launch_stream<PoissonK<T, C>, T, false, false>(m, p, cf, x, y, nullptr, s);
+          break;
+        }
+      }
       launch_patch<PoissonK<T, C>, T, S, C, false>(m, p, cf, x, y, nullptr, s);
       break;
     case CHNS_OP_MASS:
+      if constexpr (std::is_same<T, float>::value && std::is_same<S, T>::value &&
+                    std::is_same<C, T>::value) {
+        if (use_stream<MassK<T, C>, T, S, C>(m)) {
+          launch_stream<MassK<T, C>, T, false, false>(m, p, cf, x, y, nullptr, s);
+          break;
+        }
+      }
       launch_patch<MassK<T, C>, T, S, C, false>(m, p, cf, x, y, nullptr, s);
       break;
     case CHNS_OP_CH:
@@ -538,6 +855,12 @@ chns_status apply_poisson_cg(const chns_mesh* m, const chns_params* prm, const c
           static_cast<double*>(p_new), par, fcg);
       break;
     case CHNS_FP32:
+      if (use_stream<PoissonK<float, float>, float, float, float>(m)) {
+        launch_stream<PoissonK<float, float>, float, true, true>(
+            m, p, coef_args<float>(coef), static_cast<const float*>(p_old), static_cast<float*>(y),
+            S_cg, s, static_cast<const float*>(z), static_cast<float*>(p_new), par, fcg);
+        break;
+      }
       launch_patch<PoissonK<float, float>, float, float, float, true, true>(
           m, p, coef_args<float>(coef), static_cast<const float*>(p_old), static_cast<float*>(y),
           S_cg, s, static_cast<const float*>(z), static_cast<float*>(p_new), par, fcg);

@@ -22,6 +22,14 @@ constexpr int32_t kNodeMask = kOwnBit - 1;
 // whose distinct nodes (regular nodes and hanging corners) fit in kPatchSlots shared slots.
 constexpr int kPatchElems = 256;
 constexpr int kPatchSlots = 1024;
+// Per element of a patch, eloc holds its 8 corner slots as uint16; slots are < kPatchSlots, so the
+// first entry also carries the element's level in bits 10-14.
+constexpr uint32_t kElocSlotMask = 0x3ff;
+constexpr int kElocLevelShift = 10;
+constexpr uint32_t kElocLevelMask = 0x1f;
+// The persistent, pipelined apply is chosen automatically once the mesh has at least this many
+// patches per SM.
+constexpr int kStreamMinPatchesPerSm = 16;
 
 // Element geometry of one octant level on the box [0,L]^3 scaled per axis: h_d = L_d 2^-level,
 // 1/h_d and det J = h_x h_y h_z / 8, in FP64 and FP32 (looked up, never recomputed per element).
@@ -47,7 +55,7 @@ struct MeshDev {
   const int32_t* patch_nreg;  // [n_patch] regular slots of each patch
   const int32_t* slot_node;   // [slots] regular slot: node id | kOwnBit | kDirBit
   const ushort4* slot_par;    // [slots] hanging slot: local parent slots (0xffff = none)
-  const uint4* eloc;          // [n_elem] 8 local slot indices (uint16) per element
+  const uint4* eloc;          // [n_elem] 8 local slot indices (uint16) per element + level
   const LevelGeo* geo;        // [CHNS_MAXD] per-level geometry
 };
 
@@ -101,6 +109,9 @@ struct chns_mesh {
   mutable MomQState mq;
   int red_blocks = 0;
   int sm_count = 0;
+  // launch configuration of the operator applies (chns_mesh_set_apply_config)
+  chns_apply_kernel apply_kernel = CHNS_APPLY_AUTO;
+  int64_t apply_max_ctas = 0;
 };
 
 namespace chns {

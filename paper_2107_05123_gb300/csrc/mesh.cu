@@ -182,8 +182,12 @@ struct PatchTables {
   std::vector<uint4> eloc;
 };
 
+static_assert(kPatchSlots - 1 <= (int)kElocSlotMask && CHNS_MAXD - 1 <= (int)kElocLevelMask &&
+                  kElocLevelShift + 5 <= 16,
+              "patch slot and level must fit the first uint16 of eloc");
+
 static void build_patches(int64_t n, int64_t N, const std::vector<int32_t>& enode,
-                          const std::vector<int4>& hang, PatchTables& P) {
+                          const std::vector<int4>& hang, const uint8_t* levels, PatchTables& P) {
   std::vector<int32_t> stamp_n(N, -1), slot_n(N, 0), stamp_h(hang.size(), -1), slot_h(hang.size(), 0);
   std::vector<int32_t> count(N, 0);
   std::vector<int32_t> reg, hg;                    // current patch: node ids, hanging ids
@@ -216,6 +220,7 @@ static void build_patches(int64_t n, int64_t N, const std::vector<int32_t>& enod
         int32_t v = ecorner[e - e0][c];
         l[c] = (unsigned short)(v >= 0 ? v : nr + ~v);
       }
+      l[0] = (unsigned short)(l[0] | ((uint32_t)levels[e] << kElocLevelShift));
       P.eloc[e] = make_uint4(l[0] | (l[1] << 16), l[2] | (l[3] << 16), l[4] | (l[5] << 16),
                              l[6] | (l[7] << 16));
     }
@@ -451,7 +456,7 @@ static chns_status build(const uint32_t* anchors, const uint8_t* levels, int64_t
 
   // ---- patches (CTA-level gather / scatter)
   PatchTables P;
-  build_patches(n, N, enode, hang, P);
+  build_patches(n, N, enode, hang, levels, P);
 
   // ---- upload
   m->d.n_elem = n;
@@ -583,6 +588,18 @@ extern "C" chns_status chns_mesh_get_info(const chns_mesh* m, chns_mesh_info* in
   info->min_level = m->min_level;
   info->max_level = m->max_level;
   for (int d = 0; d < 3; ++d) info->extent[d] = m->d.ext[d];
+  return CHNS_OK;
+}
+
+extern "C" chns_status chns_mesh_set_apply_config(chns_mesh* m, chns_apply_kernel kernel,
+                                                  int64_t max_ctas) {
+  if (!m || max_ctas < 0 || (kernel != CHNS_APPLY_AUTO && kernel != CHNS_APPLY_PATCH &&
+                             kernel != CHNS_APPLY_STREAM)) {
+    chns::set_error("chns_mesh_set_apply_config: null mesh, unknown kernel or max_ctas < 0");
+    return CHNS_EINVAL;
+  }
+  m->apply_kernel = kernel;
+  m->apply_max_ctas = max_ctas;
   return CHNS_OK;
 }
 

@@ -5,6 +5,8 @@
 // The same structs drive the matrix-free apply kernel and the exact diagonal kernel.
 #pragma once
 
+#include <type_traits>
+
 #include "elem.cuh"
 
 namespace chns {
@@ -39,13 +41,22 @@ __device__ __forceinline__ void poisson_coef(const T pe[8], const Geo<T>& g, con
 #pragma unroll
   const PrmT<T>& k = p.get<T>();
 #pragma unroll
-  for (int q = 0; q < 8; ++q) c[q] = g.detJ / (k.alpha * clamp1(pq[q]) + k.beta);
+  for (int q = 0; q < 8; ++q) {
+    const T den = k.alpha * clamp1(pq[q]) + k.beta;  // rho in [rho_-, rho_+], far from 0
+    if constexpr (std::is_same<T, float>::value)
+      c[q] = __fdividef(g.detJ, den);  // a few ulp; the FP32 applies feed FP64-refined solves
+    else
+      c[q] = g.detJ / den;
+  }
 }
 
 // Sum-factorised local stiffness apply with a per-quadrature-point coefficient c[q]:
-// r_a = sum_q c_q grad N_a(q) . grad u(q).
-template <class T>
-__device__ __forceinline__ void stiff_local(const T c[8], const Geo<T>& g, const T u[8], T r[8]) {
+// r_a = sum_q c_q grad N_a(q) . grad u(q). With E, *e = u . r = sum_q c_q |grad u(q)|^2, formed
+// from the per-axis gradient data (a sum of non-negative terms for c >= 0, so it is accurate in
+// the working precision; u . r itself cancels).
+template <class T, bool E = false>
+__device__ __forceinline__ void stiff_local(const T c[8], const Geo<T>& g, const T u[8], T r[8],
+                                            T* e = nullptr) {
   T gx[4], gy[4], gz[4];
   grad_compact(u, gx, gy, gz);
   T sx[4], sy[4], sz[4];
@@ -61,6 +72,16 @@ __device__ __forceinline__ void stiff_local(const T c[8], const Geo<T>& g, const
 #pragma unroll
   for (int a = 0; a < 8; ++a) r[a] = T(0);
   grad_compact_T(sx, sy, sz, sc, r);
+  if constexpr (E) {
+    T ex = T(0), ey = T(0), ez = T(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      ex += gx[j] * sx[j];
+      ey += gy[j] * sy[j];
+      ez += gz[j] * sz[j];
+    }
+    *e = sc[0] * ex + sc[1] * ey + sc[2] * ez;
+  }
 }
 
 template <class T, class C>
@@ -69,6 +90,7 @@ struct PoissonK {
   // CTAs of the patch apply resident per SM that the register allocation must allow (FP32: 6,
   // i.e. at most 42 registers; FP64: 3)
   static constexpr int MIN_CTAS = sizeof(T) == 4 ? 6 : 3;
+  static constexpr int STREAM_CTAS = sizeof(T) == 4 ? 5 : 0;  // persistent apply (0: not used)
   static constexpr int NC = 1;
   static constexpr bool DIR = false;
   static constexpr bool DIAG_PER_COMP = false;
@@ -87,6 +109,14 @@ struct PoissonK {
                                         T r[NC][8]) const {
     stiff_local(c, g, x[0], r[0]);
   }
+  // apply and the element energy x . A_e x (see stiff_local)
+  static constexpr bool ENERGY = true;
+  __device__ __forceinline__ T apply_energy(const Geo<T>& g, const DevParams&, const T x[NC][8],
+                                            T r[NC][8]) const {
+    T e;
+    stiff_local<T, true>(c, g, x[0], r[0], &e);
+    return e;
+  }
 };
 
 // ---------------------------------------------------------------- velocity update mass
@@ -95,6 +125,7 @@ template <class T, class C>
 struct MassK {
   static constexpr bool QDATA = false;
   static constexpr int MIN_CTAS = sizeof(T) == 4 ? 5 : 3;
+  static constexpr int STREAM_CTAS = sizeof(T) == 4 ? 3 : 0;  // persistent apply (0: not used)
   static constexpr int NC = 3;
   static constexpr bool DIR = true;
   static constexpr bool DIAG_PER_COMP = false;
@@ -137,6 +168,7 @@ template <class T, class C>
 struct ChK {
   static constexpr bool QDATA = false;
   static constexpr int MIN_CTAS = sizeof(T) == 4 ? 4 : 1;
+  static constexpr int STREAM_CTAS = 0;  // persistent apply (0: not used)
   static constexpr int NC = 2;
   static constexpr bool DIR = false;
   static constexpr bool DIAG_PER_COMP = true;
@@ -250,6 +282,7 @@ struct MomK {
   static constexpr bool QDATA = false;
   // FP32: two CTAs per SM (at most 128 registers) instead of the one that 217 registers allow
   static constexpr int MIN_CTAS = sizeof(T) == 4 ? 2 : 1;
+  static constexpr int STREAM_CTAS = 0;  // persistent apply (0: not used)
   static constexpr int NC = 3;
   static constexpr bool DIR = true;
   static constexpr bool DIAG_PER_COMP = false;
@@ -338,6 +371,7 @@ template <class T, class C>
 struct MomQK {
   static constexpr bool QDATA = true;
   static constexpr int MIN_CTAS = sizeof(T) == 4 ? 2 : 1;
+  static constexpr int STREAM_CTAS = 0;  // persistent apply (0: not used)
   static constexpr int NC = 3;
   static constexpr bool DIR = true;
   static constexpr bool DIAG_PER_COMP = false;
@@ -383,5 +417,11 @@ struct MomQK {
     });
   }
 };
+
+// Operators that form the element energy x . A_e x alongside the apply (ENERGY = true).
+template <class K, class = void>
+struct HasEnergy : std::false_type {};
+template <class K>
+struct HasEnergy<K, std::void_t<decltype(K::ENERGY)>> : std::bool_constant<K::ENERGY> {};
 
 }  // namespace chns
