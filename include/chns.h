@@ -82,11 +82,22 @@ typedef enum { CHNS_KSP_CG = 0, CHNS_KSP_GMRES = 1, CHNS_KSP_FCG = 2 } chns_ksp;
  * from 15 power iterations at the start of the solve (in the precision of the iteration);
  * restart - 1 extra applies per iteration. A fixed SPD preconditioner (as long as lmax bounds
  * the spectrum), run through the flexible-CG driver. */
+/* SCHUR (CH with GMRES): block upper-triangular preconditioner of the Newton Jacobian
+ * [A B; C D] (rows phi, mu; B = k K, D = -M/2, k = 1/(2 Pe Cn)) built on the Schur complement of
+ * D, S = A - B D^-1 C, approximated by H M^-1 H with H = M/sqrt(dt) + Cn sqrt(k) K (which keeps
+ * the M/dt and Cn^2 k K M^-1 K terms of S and drops advection and psi''):
+ *   z_mu = -2 M^-1 r_mu,  z_phi = H^-1 M H^-1 (r_phi - k K z_mu).
+ * The inner solves are fixed numbers of Jacobi-CG iterations (inner_its with H, a quarter of
+ * them, at least 4, with M) from zero, so the preconditioner varies with r and GMRES runs in
+ * its flexible form (the preconditioned vectors are kept: restart <= 30). For meshes and
+ * parameters where the biharmonic term dominates (small Cn h^-1), where the 2x2 nodal
+ * block-Jacobi preconditioner stalls. */
 typedef enum {
   CHNS_PC_NONE = 0,
   CHNS_PC_JACOBI = 1,
   CHNS_PC_LEARNED = 2,
-  CHNS_PC_CHEBYSHEV = 3
+  CHNS_PC_CHEBYSHEV = 3,
+  CHNS_PC_SCHUR = 4
 } chns_pc;
 
 typedef struct chns_mesh chns_mesh;   /* opaque; owns device tables and workspace */
@@ -231,6 +242,7 @@ typedef struct {
   int32_t max_refine;       /* FP32 modes: maximum refinement cycles */
   int32_t check_every;      /* CG/FCG: iterations between host convergence checks (>= 1) */
   chns_learned* learned;    /* CHNS_PC_LEARNED: the network (not owned); else ignored */
+  int32_t inner_its;        /* CHNS_PC_SCHUR: CG iterations of each inner solve with H (0: 20) */
 } chns_solver_params;
 
 typedef struct {

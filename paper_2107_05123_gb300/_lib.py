@@ -30,7 +30,7 @@ OP_NCOMP = {OP_POISSON: 1, OP_MASS: 3, OP_CH: 2, OP_MOMENTUM: 3}
 # chns_ksp / chns_pc
 KSP_CG, KSP_GMRES, KSP_FCG = 0, 1, 2
 APPLY_AUTO, APPLY_PATCH, APPLY_STREAM = 0, 1, 2
-PC_NONE, PC_JACOBI, PC_LEARNED, PC_CHEBYSHEV = 0, 1, 2, 3
+PC_NONE, PC_JACOBI, PC_LEARNED, PC_CHEBYSHEV, PC_SCHUR = 0, 1, 2, 3, 4
 
 
 class ChnsError(RuntimeError):
@@ -58,7 +58,7 @@ class chns_solver_params(C.Structure):
     _fields_ = [("ksp", C.c_int32), ("pc", C.c_int32), ("rtol", C.c_double),
                 ("max_it", C.c_int32), ("restart", C.c_int32), ("inner_precision", C.c_int32),
                 ("inner_rtol", C.c_double), ("max_refine", C.c_int32),
-                ("check_every", C.c_int32), ("learned", C.c_void_p)]
+                ("check_every", C.c_int32), ("learned", C.c_void_p), ("inner_its", C.c_int32)]
 
 
 class chns_solve_stats(C.Structure):
@@ -205,9 +205,9 @@ def make_coef(phi=None, u=(None, None, None), mu=None) -> chns_coef:
 
 def make_solver(ksp=KSP_CG, pc=PC_JACOBI, rtol=1e-8, max_it=10000, restart=30,
                 inner_precision=FP64, inner_rtol=1e-3, max_refine=20, check_every=1,
-                learned=None):
+                learned=None, inner_its=0):
     return chns_solver_params(ksp, pc, rtol, max_it, restart, inner_precision, inner_rtol,
-                              max_refine, check_every, learned)
+                              max_refine, check_every, learned, inner_its)
 
 
 # ------------------------------------------------------------------ mesh

@@ -879,6 +879,67 @@ chns_status apply_poisson_cg(const chns_mesh* m, const chns_params* prm, const c
   return CHNS_OK;
 }
 
+// y = sa M x + sb K x and its exact diagonal (shifted Laplacian, constant coefficients); phi is
+// any coefficient array of the precision (gathered by the patch kernel, not used).
+static DevParams shift_params(const chns_params* prm, double sa, double sb) {
+  DevParams p = make_dev_params(*prm);
+  p.d.sa = sa;
+  p.d.sb = sb;
+  p.f.sa = (float)sa;
+  p.f.sb = (float)sb;
+  return p;
+}
+
+chns_status apply_shift(const chns_mesh* m, const chns_params* prm, const void* phi, double sa,
+                        double sb, const void* x, void* y, chns_precision prec, cudaStream_t s) {
+  CHNS_CHECK(m && prm && phi && x && y && x != y, CHNS_EINVAL, "shifted apply: bad argument");
+  const DevParams p = shift_params(prm, sa, sb);
+  chns_coef c{};
+  c.phi_tilde = phi;
+  const int64_t N = m->d.n_nodes;
+  if (prec == CHNS_FP64) {
+    CHNS_CUDA(cudaMemsetAsync(y, 0, N * sizeof(double), s));
+    launch_patch<ShiftK<double, double>, double, double, double, false>(
+        m, p, coef_args<double>(&c), static_cast<const double*>(x), static_cast<double*>(y),
+        nullptr, s);
+  } else if (prec == CHNS_FP32) {
+    CHNS_CUDA(cudaMemsetAsync(y, 0, N * sizeof(float), s));
+    launch_patch<ShiftK<float, float>, float, float, float, false>(
+        m, p, coef_args<float>(&c), static_cast<const float*>(x), static_cast<float*>(y), nullptr,
+        s);
+  } else {
+    set_error("shifted apply: bad precision");
+    return CHNS_EINVAL;
+  }
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
+chns_status diag_shift(const chns_mesh* m, const chns_params* prm, const void* phi, double sa,
+                       double sb, void* d, chns_precision prec, cudaStream_t s) {
+  CHNS_CHECK(m && prm && phi && d, CHNS_EINVAL, "shifted diagonal: bad argument");
+  const DevParams p = shift_params(prm, sa, sb);
+  chns_coef c{};
+  c.phi_tilde = phi;
+  const int64_t N = m->d.n_nodes;
+  const unsigned nb = (unsigned)((m->d.n_elem + kApplyThreads - 1) / kApplyThreads);
+  note_launch();
+  if (prec == CHNS_FP64) {
+    CHNS_CUDA(cudaMemsetAsync(d, 0, N * sizeof(double), s));
+    k_diag<ShiftK<double, double>, double, double, double><<<nb, kApplyThreads, 0, s>>>(
+        m->d, p, coef_args<double>(&c), static_cast<double*>(d));
+  } else if (prec == CHNS_FP32) {
+    CHNS_CUDA(cudaMemsetAsync(d, 0, N * sizeof(float), s));
+    k_diag<ShiftK<float, float>, float, float, float><<<nb, kApplyThreads, 0, s>>>(
+        m->d, p, coef_args<float>(&c), static_cast<float*>(d));
+  } else {
+    set_error("shifted diagonal: bad precision");
+    return CHNS_EINVAL;
+  }
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
 // 2x2 nodal blocks of the CH Jacobian, d4 = [d_pp, d_pm, d_mp, d_mm] x N, in FP64 or FP32.
 chns_status block_diag_ch(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
                           void* d4, chns_precision prec, cudaStream_t s) {

@@ -27,6 +27,7 @@ struct PrmT {
   T inv_re, h2re, inv_pe, h2pe;         // 1/Re, 1/(2Re), 1/Pe, 1/(2Pe)
   T inv_pecn, kmu, kphi, cn2;           // 1/(Pe Cn), 1/(2 Pe Cn), Cn^2/2, Cn^2
   T ka, cw, inv_fr;                     // -alpha/Cn, Cn/We, 1/Fr
+  T sa, sb;  // constant-coefficient operator sa M + sb K (set per call by its apply, else 0)
 };
 
 struct DevParams {
@@ -67,6 +68,7 @@ inline PrmT<T> make_prm(const chns_params& p) {
   q.ka = (T)(-alpha / p.Cn);
   q.cw = (T)(p.Cn / p.We);
   q.inv_fr = (T)(1.0 / p.Fr);
+  q.sa = q.sb = (T)0;
   return q;
 }
 

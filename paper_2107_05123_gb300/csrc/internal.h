@@ -177,6 +177,12 @@ chns_status apply_poisson_cg(const chns_mesh* m, const chns_params* prm, const c
 chns_status momentum_qdata_on(const chns_mesh* m, const chns_params* prm, const chns_coef* coef64,
                               const chns_coef* coef32, cudaStream_t s);
 void momentum_qdata_off(const chns_mesh* m);
+// y = sa M x + sb K x (shifted Laplacian, constant sa, sb) and its exact diagonal; phi is any
+// coefficient array of the precision (FP64 or FP32), read but unused.
+chns_status apply_shift(const chns_mesh* m, const chns_params* prm, const void* phi, double sa,
+                        double sb, const void* x, void* y, chns_precision prec, cudaStream_t s);
+chns_status diag_shift(const chns_mesh* m, const chns_params* prm, const void* phi, double sa,
+                       double sb, void* d, chns_precision prec, cudaStream_t s);
 chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
                     const chns_coef* coef, void* d, chns_precision prec, cudaStream_t s);
 // 2x2 nodal blocks of the CH Jacobian, d4 = [d_pp, d_pm, d_mp, d_mm] x n_nodes (FP64 or FP32)
@@ -184,6 +190,8 @@ chns_status block_diag_ch(const chns_mesh* m, const chns_params* prm, const chns
                           void* d4, chns_precision prec, cudaStream_t s);
 int op_ncomp(chns_operator op);
 bool op_dirichlet(chns_operator op);
+// internal operator code of the Krylov context: y = sa M x + sb K x (apply_shift)
+constexpr chns_operator kOpShift = static_cast<chns_operator>(100);
 
 // ---- vector kernels (krylov.cu)
 void vec_convert_f64_f32(const double* a, float* b, int64_t n, cudaStream_t s);

@@ -474,10 +474,14 @@ struct Ctx {
   cudaStream_t s;
   int64_t n;                // vector length (components * n_nodes)
   double* S;                // device scalars
+  double sa = 0.0, sb = 0.0;  // op == kOpShift: y = sa M x + sb K x
 };
 
 template <class T>
 chns_status apply_T(const Ctx& c, const T* x, T* y) {
+  if (c.op == kOpShift)
+    return apply_shift(c.m, c.prm, sizeof(T) == sizeof(double) ? c.coef64->phi_tilde : c.coefR.phi_tilde,
+                       c.sa, c.sb, x, y, sizeof(T) == sizeof(double) ? CHNS_FP64 : CHNS_FP32, c.s);
   if (sizeof(T) == sizeof(double)) return apply_op(c.m, c.op, c.prm, c.coef64, x, y, CHNS_FP64, c.s);
   return apply_op(c.m, c.op, c.prm, &c.coefR, x, y, c.inner, c.s);
 }
@@ -788,6 +792,111 @@ chns_status pcg(const Ctx& c, const T* b, T* x, const T* dinv, double tol_abs, i
   return iterate<T>(c, step, x, tol_abs, max_it, chunk, rr, iters, rnorm, snap);
 }
 
+// `iters` Jacobi-CG iterations on A x = b from x = 0 with no host synchronisation (the scalars
+// stay in the parity slots; see cg_iteration); an inexact inner solve.
+template <class T>
+chns_status cg_fixed(const Ctx& c, const T* b, T* x, const T* dinv, int iters, T* r, T* z, T* p,
+                     T* q, T* p2) {
+  T* pb[2] = {p, p2};
+  const int64_t n = c.n;
+  const unsigned rg = red_grid(c.m, n), vg = vgrid(c.m, n);
+  CHNS_CUDA(cudaMemsetAsync(x, 0, n * sizeof(T), c.s));
+  CHNS_CUDA(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, c.s));
+  note_launch();
+  k_mul<T><<<vg, kVecThreads, 0, c.s>>>(dinv, r, z, n);
+  CHNS_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), c.s));
+  note_launch();
+  k_dot<T, T><<<rg, kVecThreads, 0, c.s>>>(r, z, n, c.m->ws.red, c.m->ws.counter, c.S + kCgRz0);
+  CHNS_CUDA(cudaMemcpyAsync(c.S + kCgRzPrev, c.S + kCgRz0, sizeof(double),
+                            cudaMemcpyDeviceToDevice, c.s));
+  CHNS_CUDA(cudaMemsetAsync(c.S + kCgPq0, 0, sizeof(double), c.s));
+  for (int it = 0; it < iters; ++it) {
+    chns_status st = cg_iteration<T>(c, c.s, x, r, z, pb[it & 1], pb[(it & 1) ^ 1], q, dinv, it & 1);
+    if (st != CHNS_OK) return st;
+  }
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
+// Block upper-triangular preconditioner of the CH Newton Jacobian J = [A B; C D] (rows phi, mu;
+// B = kmu K, C = (psi'' M + Cn^2 K)/2, D = -M/2): P = [S~ B; 0 D] with the Schur complement
+// S = A - B D^-1 C = M/dt - adv + kmu K M^-1 M_psi'' + 2 kmu kphi K M^-1 K approximated by
+// S~ = H M^-1 H, H = sqrt(1/dt) M + sqrt(2 kmu kphi) K (= M/dt + 2 kmu kphi K M^-1 K + a cross
+// term 2 sqrt(2 kmu kphi / dt) K). J P^-1 is similar to a unit lower-triangular matrix when
+// S~ = S. Applying P^-1 to (r_phi, r_mu):
+//   z_mu = D^-1 r_mu = -2 M^-1 r_mu;  z_phi = S~^-1 (r_phi - B z_mu) = H^-1 M H^-1 (...),
+// with the M and H inverses replaced by fixed numbers of Jacobi-CG iterations.
+template <class T>
+struct SchurPC {
+  Ctx cM, cH, cK;        // N-vector contexts: M, H, kmu K
+  T* dM = nullptr;       // inverse diagonals of M and H
+  T* dH = nullptr;
+  T* t[8] = {};          // scratch N-vectors: CG r, z, p, q, p2; t, w, u
+  int itH = 20, itM = 5;
+
+  // contexts and diagonals; vec: >= 10 scratch N-vectors
+  chns_status setup(const Ctx& c, T* const* vec, int inner_its) {
+    const int64_t N = c.m->d.n_nodes;
+    const double dt = c.prm->dt, Pe = c.prm->Pe, Cn = c.prm->Cn;
+    const double kmu = 0.5 / (Pe * Cn), kphi = 0.5 * Cn * Cn;
+    itH = inner_its > 0 ? inner_its : 20;
+    itM = std::max(4, itH / 4);
+    cM = c;
+    cM.op = kOpShift;
+    cM.n = N;
+    cM.sa = 1.0;
+    cM.sb = 0.0;
+    cH = cM;
+    cH.sa = std::sqrt(1.0 / dt);
+    cH.sb = std::sqrt(2.0 * kmu * kphi);
+    cK = cM;
+    cK.sa = 0.0;
+    cK.sb = kmu;
+    dM = vec[0];
+    dH = vec[1];
+    for (int k = 0; k < 8; ++k) t[k] = vec[2 + k];
+    const chns_precision pr = sizeof(T) == sizeof(double) ? CHNS_FP64 : CHNS_FP32;
+    const void* phi = sizeof(T) == sizeof(double) ? c.coef64->phi_tilde : c.coefR.phi_tilde;
+    chns_status st = diag_shift(c.m, c.prm, phi, cM.sa, cM.sb, dM, pr, c.s);
+    if (st != CHNS_OK) return st;
+    st = diag_shift(c.m, c.prm, phi, cH.sa, cH.sb, dH, pr, c.s);
+    if (st != CHNS_OK) return st;
+    note_launch();
+    k_invert<T, T><<<vgrid(c.m, N), kVecThreads, 0, c.s>>>(dM, dM, N);
+    note_launch();
+    k_invert<T, T><<<vgrid(c.m, N), kVecThreads, 0, c.s>>>(dH, dH, N);
+    CHNS_CUDA(cudaGetLastError());
+    return CHNS_OK;
+  }
+
+  // z = P^-1 v for the pair [phi; mu] (2N each; z must not alias v)
+  chns_status apply(const T* v, T* z) {
+    const int64_t N = cM.n;
+    const unsigned vg = vgrid(cM.m, N);
+    const T* vphi = v;
+    const T* vmu = v + N;
+    T* zphi = z;
+    T* zmu = z + N;
+    T *r = t[0], *zz = t[1], *p = t[2], *q = t[3], *p2 = t[4], *tt = t[5], *w = t[6], *u = t[7];
+    chns_status st = cg_fixed<T>(cM, vmu, zmu, dM, itM, r, zz, p, q, p2);
+    if (st != CHNS_OK) return st;
+    note_launch();
+    k_scale<T><<<vg, kVecThreads, 0, cM.s>>>(zmu, -2.0, N);
+    st = apply_T<T>(cK, zmu, tt);
+    if (st != CHNS_OK) return st;
+    note_launch();
+    k_axpby<T><<<vg, kVecThreads, 0, cM.s>>>(1.0, vphi, -1.0, tt, u, N);
+    st = cg_fixed<T>(cH, u, w, dH, itH, r, zz, p, q, p2);
+    if (st != CHNS_OK) return st;
+    st = apply_T<T>(cM, w, tt);
+    if (st != CHNS_OK) return st;
+    st = cg_fixed<T>(cH, tt, zphi, dH, itH, r, zz, p, q, p2);
+    if (st != CHNS_OK) return st;
+    CHNS_CUDA(cudaGetLastError());
+    return CHNS_OK;
+  }
+};
+
 // Flexible CG on the Poisson operator with the preconditioner z = M(r): with L the learned
 // correction c followed by one damped Jacobi step, z = c + omega dinv (r - A c) (w: scratch
 // vector); with cheb the Chebyshev polynomial (scratch w, dcheb); else Jacobi (dinv) or the
@@ -876,8 +985,12 @@ unsigned multidot(const chns_mesh* m, const T* V, int64_t ld, int nk, const T* w
 // pass; the second pass also returns w.w so that the new norm needs no extra reduction.
 template <class T>
 chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, double tol_abs,
-                  int max_it, int restart, T* V, T* z, int* iters, double* rnorm) {
+                  int max_it, int restart, T* V, T* z, int* iters, double* rnorm,
+                  SchurPC<T>* spc = nullptr) {
   const int64_t n = c.n, ld = n;
+  // flexible form (spc): the preconditioned vectors Z_j = P^-1 V_j follow the restart + 1 basis
+  // vectors in the same buffer, and the update is x += Z y
+  T* Zb = V + (int64_t)(restart + 1) * ld;
   const unsigned vg = vgrid(c.m, n);
   const unsigned mdb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(kMdBlocks, (n + 255) / 256));
   double* hdev = c.S + S_MD;
@@ -911,12 +1024,18 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, do
     for (int j = 0; j < restart; ++j) {
       T* vj = V + (int64_t)j * ld;
       T* w = V + (int64_t)(j + 1) * ld;
-      note_launch();
-      if (block2)
-        k_mul_b2<T><<<vg, kVecThreads, 0, c.s>>>(dinv, vj, z, n / 2);
-      else
-        k_mul<T><<<vg, kVecThreads, 0, c.s>>>(dinv, vj, z, n);
-      st = apply_T<T>(c, z, w);
+      T* zj = spc ? Zb + (int64_t)j * ld : z;
+      if (spc) {
+        st = spc->apply(vj, zj);
+        if (st != CHNS_OK) return st;
+      } else {
+        note_launch();
+        if (block2)
+          k_mul_b2<T><<<vg, kVecThreads, 0, c.s>>>(dinv, vj, z, n / 2);
+        else
+          k_mul<T><<<vg, kVecThreads, 0, c.s>>>(dinv, vj, z, n);
+      }
+      st = apply_T<T>(c, zj, w);
       if (st != CHNS_OK) return st;
       // classical Gram-Schmidt: h = V^T w and w.w in one pass; a second pass only when the
       // new vector lost more than half its norm to the projection (cancellation)
@@ -987,7 +1106,9 @@ chns_status gmres(const Ctx& c, const T* b, T* x, const T* dinv, bool block2, do
     }
     CHNS_CUDA(cudaMemcpyAsync(hdev, y.data(), jend * sizeof(double), cudaMemcpyHostToDevice, c.s));
     note_launch();
-    if (block2)
+    if (spc)
+      k_gmres_update<T><<<vg, kVecThreads, 0, c.s>>>(Zb, ld, jend, hdev, nullptr, x, n);
+    else if (block2)
       k_gmres_update_b2<T><<<vg, kVecThreads, 0, c.s>>>(V, ld, jend, hdev, dinv, x, n / 2);
     else
       k_gmres_update<T><<<vg, kVecThreads, 0, c.s>>>(V, ld, jend, hdev, dinv, x, n);
@@ -1038,8 +1159,14 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
   CHNS_CHECK(sp->ksp == CHNS_KSP_CG || sp->ksp == CHNS_KSP_GMRES || sp->ksp == CHNS_KSP_FCG,
              CHNS_EINVAL, "bad ksp");
   CHNS_CHECK(sp->pc == CHNS_PC_NONE || sp->pc == CHNS_PC_JACOBI || sp->pc == CHNS_PC_LEARNED ||
-                 sp->pc == CHNS_PC_CHEBYSHEV,
+                 sp->pc == CHNS_PC_CHEBYSHEV || sp->pc == CHNS_PC_SCHUR,
              CHNS_EINVAL, "bad preconditioner");
+  // flexible GMRES keeps restart preconditioned vectors beside the restart + 1 basis vectors of
+  // 2 n_nodes in the basis buffer of (CHNS_GMRES_MAX_RESTART + 1) x 3 n_nodes
+  CHNS_CHECK(sp->pc != CHNS_PC_SCHUR ||
+                 (op == CHNS_OP_CH && sp->ksp == CHNS_KSP_GMRES && sp->inner_its >= 0 &&
+                  2 * (2 * sp->restart + 1) <= 3 * (CHNS_GMRES_MAX_RESTART + 1)),
+             CHNS_EINVAL, "Schur preconditioner: CH operator, GMRES, restart <= 30, inner_its >= 0");
   CHNS_CHECK(sp->pc != CHNS_PC_CHEBYSHEV ||
                  (op == CHNS_OP_POISSON && sp->ksp != CHNS_KSP_GMRES && sp->restart >= 1 &&
                   sp->restart <= 16),
@@ -1116,6 +1243,22 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
     }
     const bool block2 = (op == CHNS_OP_CH && jac);
     const int64_t Nn = m->d.n_nodes;
+    // Schur-complement preconditioner of the CH pair, per precision on first use (scratch:
+    // workspace vectors 3..6, twelve node vectors, free during GMRES)
+    const bool schur = sp->pc == CHNS_PC_SCHUR;
+    SchurPC<double> spc64;
+    SchurPC<float> spc32;
+    bool spc64_ok = false, spc32_ok = false;
+    auto schur64 = [&]() -> SchurPC<double>* {
+      if (!schur) return nullptr;
+      if (!spc64_ok) {
+        double* vec[12];
+        for (int k = 0; k < 12; ++k) vec[k] = ws.v64[3 + k / 3] + (k % 3) * Nn;
+        if (spc64.setup(c, vec, sp->inner_its) != CHNS_OK) return nullptr;
+        spc64_ok = true;
+      }
+      return &spc64;
+    };
     const double* dinv64 = nullptr;
     auto make_dinv64 = [&]() -> chns_status {
       if (!jac || dinv64) return CHNS_OK;
@@ -1167,9 +1310,12 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
           its += its2;
         }
       }
-      else
+      else {
+        SchurPC<double>* pc64 = schur64();
+        if (schur && !pc64) return CHNS_ECUDA;
         st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it, sp->restart, ws.gm_V,
-                           ws.v64[7], &its, &rn);
+                           ws.v64[7], &its, &rn, pc64);
+      }
       out.iterations = its;
     } else {
       // FP32 coefficient copies; the preconditioner is computed from them in FP32.
@@ -1275,9 +1421,12 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
                                sp->check_every, r64, ws.v64[3], ws.v64[4], ws.v64[5], ws.v64[6],
                                ws.v64[7], &its, &frn, 0, nullptr, cheb ? &cheb64 : nullptr,
                                ws.v64[14]);
-            else
-              st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it - total, sp->restart, ws.gm_V,
-                                 ws.v64[7], &its, &frn);
+            else {
+              SchurPC<double>* pc64 = schur64();
+              if (schur && !pc64) return CHNS_ECUDA;
+              st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it - total, sp->restart,
+                                 ws.gm_V, ws.v64[7], &its, &frn, pc64);
+            }
             total += its;
             cur = CHNS_FP64;
             last_rn = -1.0;
@@ -1317,9 +1466,17 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
             ++out.fallbacks;
           }
         }
-        else
+        else {
+          if (schur && !spc32_ok) {
+            float* vec[12];
+            for (int k = 0; k < 12; ++k) vec[k] = ws.v32[3 + k / 3] + (k % 3) * Nn;
+            st = spc32.setup(c, vec, sp->inner_its);
+            if (st != CHNS_OK) return st;
+            spc32_ok = true;
+          }
           ist = gmres<float>(c, r32, d32, dinv32, block2, itol, budget, sp->restart, ws.gm_V32,
-                             ws.v32[7], &its, &irn);
+                             ws.v32[7], &its, &irn, schur ? &spc32 : nullptr);
+        }
         if (ist != CHNS_OK && ist != CHNS_ENOTCONV) return ist;
         total += its;
         ++refine;

@@ -38,7 +38,6 @@ __device__ __forceinline__ void poisson_coef(const T pe[8], const Geo<T>& g, con
                                              T c[8]) {
   T pq[8];
   interp3(pe, pq);
-#pragma unroll
   const PrmT<T>& k = p.get<T>();
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -156,6 +155,43 @@ struct MassK {
       for (int q = 0; q < 8; ++q) v[q] *= c[q];
       interp3(v, r[k]);
     }
+  }
+};
+
+// ---------------------------------------------------------------- shifted Laplacian
+// sa (q, u) + sb (grad q, grad u) with constant sa, sb >= 0 (DevParams sa, sb): the operator of
+// the inner solves of the Cahn-Hilliard Schur-complement preconditioner. No Dirichlet rows.
+template <class T, class C>
+struct ShiftK {
+  static constexpr bool QDATA = false;
+  static constexpr int MIN_CTAS = sizeof(T) == 4 ? 6 : 3;
+  static constexpr int STREAM_CTAS = 0;
+  static constexpr int NC = 1;
+  static constexpr bool DIR = false;
+  static constexpr bool DIAG_PER_COMP = false;
+  static constexpr int NF = 1;  // (phi~ gathered but unused: the patch kernel's layout)
+  T cm, ck[8];
+  __device__ __forceinline__ void setup(const T[NF][8], const Geo<T>& g, const DevParams& p) {
+    const PrmT<T>& k = p.get<T>();
+    cm = k.sa * g.detJ;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ck[q] = k.sb * g.detJ;
+  }
+  __device__ __forceinline__ void load(const MeshDev&, const DevParams& p, const CoefArgs<C>&,
+                                       const int[8], const Geo<T>& g) {
+    const T f[NF][8] = {};
+    setup(f, g, p);
+  }
+  __device__ __forceinline__ void apply(const Geo<T>& g, const DevParams&, const T x[NC][8],
+                                        T r[NC][8]) const {
+    stiff_local(ck, g, x[0], r[0]);
+    T v[8], t[8];
+    interp3(x[0], v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] *= cm;
+    interp3(v, t);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) r[0][a] += t[a];
   }
 };
 
