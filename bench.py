@@ -14,8 +14,9 @@ e2e         = one Poisson solve through the C ABI from pinned host buffers (copi
 roofline    = the dominant apply kernel timed alone from a cold L2 (algorithmic bytes / time);
 cpu_baseline= the FP64 CPU oracle (assembled matrix + Jacobi-PCG) on a bounded sample;
 large_interface = the Rayleigh-Taylor workload at scale (~7e6 leaves): its pressure-Poisson
-              solve in the three precisions, their difference, and the Poisson apply alone
-              (see run_large);
+              solve in the three precisions, their difference, the Poisson apply alone, and
+              full time steps (CH with the Schur-complement preconditioner) in mixed precision
+              and in FP64 (see run_large);
 learned     = the learned coarse correction for the pressure-Poisson solve on the 8-drop
               workload: pairs from time steps, training, and the solves of one more step with
               and without it (untimed setup; see run_learned).
@@ -40,7 +41,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Poisson+PCG DOFs/s and time/step vs plain FP64 GPU at 1e-8 residual; HBM frac"
 UNIT = "DOFs/s"
 WORKLOAD = "rising_drop_levels5-8"
-APPLY_DRAM_BYTES = 11.58e6
+APPLY_DRAM_BYTES = 11.27e6  # DRAM bytes of one launch of the roofline kernel (ncu, see below)
 
 
 def _peaks():
@@ -243,8 +244,8 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     achieved = alg_bytes / t_apply / 1e9
     # DRAM bytes of one launch from an ncu capture of this kernel on this workload
-    # (dram__bytes.sum.per_second x gpu__time_duration: 667.8 GB/s x 17.344 us, summarised
-    # under profiles/); --traffic overrides it
+    # (dram__bytes_read.sum 11.27 MB + dram__bytes_write.sum 0, summarised under profiles/);
+    # --traffic overrides it
     traffic = args.traffic if args.traffic is not None else APPLY_DRAM_BYTES
 
     # ---- end to end: one Poisson solve through the C ABI with pinned host buffers
@@ -332,8 +333,9 @@ def run_large(args):
     1e-8 with Jacobi-PCG in the three precisions (BF16 coefficients + FP32 Krylov + FP64
     refinement, FP32 + FP64 refinement, all FP64), the difference of the reduced-precision
     solutions from the FP64 one, and the Poisson apply timed alone from a cold L2 (HBM regime).
-    The full time step is not run here: its Cahn-Hilliard GMRES with the 2x2 block-Jacobi
-    preconditioner does not reach 1e-8 within 4,000 iterations at this resolution."""
+    Then full time steps from the initial state: the Cahn-Hilliard GMRES uses the
+    Schur-complement preconditioner, since the 2x2 block-Jacobi one does not reach 1e-8 within
+    4,000 iterations at this resolution."""
     import numpy as np
     import torch
 
@@ -394,6 +396,57 @@ def run_large(args):
     out["poisson_apply_fp32"] = {"ms": round(statistics.mean(ts) * 1e3, 4), "alg_bytes": int(alg),
                                  "achieved_gbs": ach, "peak_gbs": peak, "peak_kind": kind,
                                  "frac": ach / peak}
+    del flush, x32, y32
+    # full time steps from the initial state: CH Newton with GMRES and the Schur-complement
+    # preconditioner (the nodal block-Jacobi one stalls at this resolution), velocity
+    # prediction, pressure Poisson, velocity update; mixed precision (FP32 Krylov + FP64
+    # refinement) for args.large_steps steps and the all-FP64 path for one
+    from paper_2107_05123_gb300.session import DeviceState, default_step_params
+
+    def step_params(inner):
+        sp = default_step_params(rtol=1e-8, inner=inner, pp_check_every=8)
+        sp.ch.pc = capi.PC_SCHUR
+        sp.ch.inner_its = 20
+        sp.ch.max_it = 400
+        return sp
+
+    def timed_steps(inner, n):
+        ds = DeviceState(dict(phi=f0["phi"], mu=f0["mu"], u=f0["u"], p=f0["p"]))
+        sp = step_params(inner)
+        res, first = [], None
+        for k in range(n):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = capi.chns_step(mesh.handle, ds.c, prm, sp)
+            e1.record()
+            torch.cuda.synchronize()
+            res.append({"ms": round(e0.elapsed_time(e1), 1),
+                        "phases_ms": {"ch": round(st.ms_ch, 1), "vp": round(st.ms_vp, 1),
+                                      "pp": round(st.ms_pp, 1), "vu": round(st.ms_vu, 1)},
+                        "newton_its": list(st.newton_its),
+                        "ch_gmres_its": [st.ch[l].iterations for l in range(2)],
+                        "vp_gmres_its": [st.vp[l].iterations for l in range(2)],
+                        "pp_cg_its": [st.pp[l].iterations for l in range(2)],
+                        "mass_drift": abs(st.phi_mass_after - st.phi_mass_before)})
+            if k == 0:
+                first = ds.host()
+        return res, first
+
+    steps_mixed, f_mixed = timed_steps(capi.FP32, max(1, args.large_steps))
+    steps_fp64, f_fp64 = timed_steps(capi.FP64, 1)
+    err = {}
+    for key in ("phi", "mu", "p", "u"):
+        a, b_ = np.asarray(f_mixed[key]), np.asarray(f_fp64[key])
+        if key == "p":
+            a, b_ = a - a.mean(), b_ - b_.mean()
+        err[key] = float(np.linalg.norm(a - b_) / max(np.linalg.norm(b_), 1e-300))
+    ms_mixed = statistics.mean(r["ms"] for r in steps_mixed)
+    out["time_step"] = {"ch_pc": "schur (inner_its 20), flexible GMRES",
+                        "fp32_fp64refine": {"ms_per_step": round(ms_mixed, 1),
+                                            "steps": steps_mixed},
+                        "fp64": {"ms_per_step": steps_fp64[0]["ms"], "steps": steps_fp64},
+                        "speedup_vs_fp64": round(steps_fp64[0]["ms"] / ms_mixed, 2),
+                        "field_error_vs_fp64_after_1_step": err}
     out["wall_s"] = round(time.perf_counter() - t_all, 1)
     return out
 
@@ -697,6 +750,8 @@ def main():
                     help="DRAM bytes per launch of the roofline kernel from an ncu capture")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the Rayleigh-Taylor workload at scale (~7e6 leaves)")
+    ap.add_argument("--large-steps", type=int, default=2,
+                    help="mixed-precision time steps of the Rayleigh-Taylor workload")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-preconditioner measurement (8-drop workload)")
     ap.add_argument("--learned-steps", type=int, default=3,
