@@ -183,7 +183,7 @@ def test_fcg_with_jacobi_equals_pcg(capi):
 @pytest.mark.parametrize("inner", ["FP64", "FP32"])
 def test_fcg_learned_solution_matches_oracle(capi, inner):
     """Whatever the network, FCG with the learned correction converges to the oracle's solution
-    (the residual tolerance stays the judge)."""
+    (convergence is decided by the unchanged residual tolerance)."""
     import scipy.sparse.linalg as spl
     om, gm = meshes("drop_l3_5")
     phi, A, b = _poisson_system(om, 9)
