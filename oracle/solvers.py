@@ -12,9 +12,16 @@ TEST INFRASTRUCTURE ONLY (see the package header).
   beside Jacobi in the build's Krylov row (not in the paper, whose PETSc solves use AMG/ASM).
 * ``newton``: plain Newton on the CH residual (Appendix A uses Newton; Sec. 6.2 reports one
   iteration at the time steps used).
+* ``ch_schur_precond``: the block upper-triangular preconditioner of the CH Newton Jacobian
+  [A B; C D] (Def. weak_VMS_disc_CH linearised: B = K/(2 Pe Cn), D = -M/2) on the Schur
+  complement of D, approximated by H M^-1 H, H = M/sqrt(dt) + Cn sqrt(k) K, with exact inner
+  inverses (sparse LU); the build's CH preconditioner for fine meshes, not in the paper (whose
+  PETSc solves use algebraic multigrid).
 
-Pins: pcg against sparse LU on SPD systems; dirichlet elimination against a reduced solve
-(tests/test_oracle_solvers.py).
+Pins: pcg against sparse LU on SPD systems; dirichlet elimination against a reduced solve; the
+Chebyshev polynomial against its closed form; the Schur preconditioner with the exact Schur
+complement makes (J P^-1 - I)^2 vanish (tests/test_oracle_solvers_step.py).
+
 """
 from __future__ import annotations
 
@@ -106,3 +113,20 @@ def chebyshev_precond(A, dinv, r, lmin, lmax, degree):
         z = z + d
         rho_old = rho
     return z
+
+
+def ch_schur_precond(M, K, dt, Pe, Cn, r, s_inv=None):
+    """z = P^-1 r for P = [S~ B; 0 D] with B = k K, k = 1/(2 Pe Cn), D = -M/2 and
+    S~^-1 = H^-1 M H^-1, H = M/sqrt(dt) + Cn sqrt(k) K (s_inv, a callable, replaces S~^-1).
+    r and z hold [phi; mu]: z_mu = D^-1 r_mu, z_phi = S~^-1 (r_phi - B z_mu)."""
+    n = M.shape[0]
+    r = np.asarray(r, dtype=np.float64)
+    k = 0.5 / (Pe * Cn)
+    z_mu = -2.0 * spla.spsolve(M.tocsc(), r[n:])
+    t = r[:n] - k * (K @ z_mu)
+    if s_inv is None:
+        H = (M / np.sqrt(dt) + Cn * np.sqrt(k) * K).tocsc()
+        z_phi = spla.spsolve(H, M @ spla.spsolve(H, t))
+    else:
+        z_phi = s_inv(t)
+    return np.concatenate([z_phi, z_mu])

@@ -99,3 +99,74 @@ def test_chebyshev_preconditioner_is_the_scaled_chebyshev_polynomial():
             Tk = lambda t: C.chebval(t, [0] * k + [1])
             p = (1.0 - Tk((theta - lams[j]) / delta) / Tk(theta / delta)) / lams[j]
             assert np.allclose(z, p * v, rtol=1e-12, atol=1e-14), (k, j)
+
+
+_CH_PRM = dict(Re=35.0, We=2.0, Cn=0.05, Pe=50.0, Fr=1.0, rho_ratio=20.0, eta_ratio=5.0,
+               dt=1e-3, C_I=6.0)
+
+
+def _ch_system(level, prm, seed):
+    from chns_workloads import octree
+    a, l = octree.uniform(level)
+    om = Mesh(a, l, (1.0, 1.0, 1.0))
+    el, co = fem.Elem(om), fem.Coeffs(prm)
+    rng = np.random.default_rng(seed)
+    n = om.n_nodes
+    phi = np.tanh(1.5 * rng.standard_normal(n))
+    u = 0.3 * rng.standard_normal((3, n))
+    J = fem.ch_jacobian(el, co, phi, u)
+    ones = np.ones((om.n_elem, 8))
+    return n, J.tocsr(), fem.mass(el, ones).tocsr(), fem.stiffness(el, ones).tocsr()
+
+
+def test_schur_preconditioner_blocks_and_exact_factor():
+    """The preconditioner's reading of the CH Jacobian (B = K/(2 Pe Cn), D = -M/2) is the oracle's
+    Jacobian, and with the exact Schur complement S = A - B D^-1 C in place of H M^-1 H,
+    J P^-1 - I is nilpotent of index 2 (J P^-1 is similar to a unit block-lower-triangular
+    matrix), so a sign or scale error in B, D or the factor order breaks the identity."""
+    n, J, M, K = _ch_system(2, _CH_PRM, 5)
+    k = 0.5 / (_CH_PRM["Pe"] * _CH_PRM["Cn"])
+    Jd = J.toarray()
+    A, B, C, D = Jd[:n, :n], Jd[:n, n:], Jd[n:, :n], Jd[n:, n:]
+    assert np.allclose(B, k * K.toarray(), rtol=0, atol=1e-14 * np.abs(B).max())
+    assert np.allclose(D, -0.5 * M.toarray(), rtol=0, atol=1e-14 * np.abs(D).max())
+    S = A - B @ np.linalg.solve(D, C)
+    s_inv = lambda t: np.linalg.solve(S, t)
+    P_inv = np.column_stack([
+        solvers.ch_schur_precond(M, K, _CH_PRM["dt"], _CH_PRM["Pe"], _CH_PRM["Cn"], e, s_inv)
+        for e in np.eye(2 * n)])
+    E = Jd @ P_inv - np.eye(2 * n)
+    assert np.linalg.norm(E) > 1e-3                    # the factor is not the inverse ...
+    assert np.linalg.norm(E @ E) <= 1e-9 * max(1.0, np.linalg.norm(E) ** 2)  # ... but E^2 = 0
+
+
+def test_schur_preconditioner_where_the_biharmonic_term_dominates():
+    """With H M^-1 H for S and exact inner inverses, GMRES on the CH Newton system of a 16^3 mesh
+    with Cn = 0.02, Pe = 1/(3 Cn^2), dt = 2e-2 needs far fewer iterations than with the inverse
+    2x2 nodal blocks, and reaches the same solution."""
+    import scipy.sparse.linalg as spla
+    prm = dict(_CH_PRM, Cn=0.02, Pe=1.0 / (3 * 0.02 ** 2), dt=2e-2)
+    n, J, M, K = _ch_system(4, prm, 6)
+    b = np.random.default_rng(7).standard_normal(2 * n)
+    ref = spla.spsolve(J.tocsc(), b)
+    schur = spla.LinearOperator(
+        J.shape, matvec=lambda r: solvers.ch_schur_precond(M, K, prm["dt"], prm["Pe"], prm["Cn"], r))
+    Jd = J.tocsr()
+    diag = Jd.diagonal()
+    app, amm, apm, amp = diag[:n], diag[n:], Jd.diagonal(n), Jd.diagonal(-n)
+    det = app * amm - apm * amp
+
+    def bj(r):
+        x, y = r[:n], r[n:]
+        return np.concatenate([(amm * x - apm * y) / det, (-amp * x + app * y) / det])
+
+    jac = spla.LinearOperator(J.shape, matvec=bj)
+    its = {}
+    for name, P in (("schur", schur), ("block_jacobi", jac)):
+        count = [0]
+        x, info = spla.gmres(J, b, M=P, rtol=1e-10, restart=30, maxiter=100,
+                             callback=lambda _: count.__setitem__(0, count[0] + 1),
+                             callback_type="pr_norm")
+        its[name] = (count[0], info, np.linalg.norm(x - ref) / np.linalg.norm(ref))
+    assert its["schur"][1] == 0 and its["schur"][2] < 1e-7, its
+    assert 2 * its["schur"][0] < its["block_jacobi"][0], its  # 28 against 103 here
