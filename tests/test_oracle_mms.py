@@ -160,3 +160,29 @@ def test_momentum_at_rest_second_order():
     errs = [_momentum_error(L) for L in (2, 3, 4)]
     r = _rates(errs)
     assert r[-1] > 1.8, (errs, r)
+
+
+def test_ch_block_second_order_in_time():
+    """The CH block of the step (Crank-Nicolson: phi~, mu~ and psi'(phi~) at the midpoint,
+    Def. variational_form_sem_disc) is second order in time: with the fluid at rest and no
+    gravity or capillary forcing the velocity stays zero, and the step's phi, mu at T = 0.016
+    converge to a dt = 2.5e-4 reference at rate 2 on a fixed mesh (self-convergence)."""
+    from oracle import step
+    w = configs.smooth_uniform(2, seed=0)
+    m = Mesh(w.anchors, w.levels, w.extent)
+    f = w.init(m.node_xyz)
+    prm = dict(w.params.as_dict(), Fr=1e12, We=1e12)
+    z = np.zeros_like(f["u"])
+    T, res = 0.016, {}
+    for dt in (4e-3, 2e-3, 1e-3, 2.5e-4):
+        st = step.State(phi=f["phi"].copy(), mu=f["mu"].copy(), u=z.copy(), u_old=z.copy(),
+                        p=f["p"].copy())
+        for _ in range(int(round(T / dt))):
+            st = step.chns_step(m, dict(prm, dt=dt), st)
+        res[dt] = st
+    ref = res[2.5e-4]
+    assert np.abs(ref.u).max() < 1e-12
+    for key in ("phi", "mu"):
+        errs = [np.linalg.norm(getattr(res[dt], key) - getattr(ref, key)) for dt in (4e-3, 2e-3, 1e-3)]
+        r = _rates(errs)
+        assert r.min() > 1.85, (key, errs, r)
