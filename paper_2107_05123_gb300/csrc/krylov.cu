@@ -58,8 +58,8 @@ k_sum(const A* __restrict__ a, int64_t n, double* part, unsigned* counter, doubl
 
 // out = a x + b y
 template <class T>
-__global__ void k_axpby(double a, const T* __restrict__ x, double b, const T* __restrict__ y,
-                        T* __restrict__ out, int64_t n) {
+__global__ void k_axpby(double a, const T* __restrict__ x, double b, const T* y, T* out,
+                        int64_t n) {  // out may alias y (in-place residual updates)
   const T ta = (T)a, tb = (T)b;
   GRID_LOOP(i, n) out[i] = ta * x[i] + tb * y[i];
 }

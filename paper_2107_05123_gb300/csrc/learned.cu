@@ -1009,12 +1009,6 @@ static void restrict_to(chns_learned* L, const chns_mesh* m, const T* r, float* 
                                                  grid, nullptr, false, 0.f, 0.f);
 }
 
-static chns_status read_scalar(const double* d, double* h, cudaStream_t s) {
-  CHNS_CUDA(cudaMemcpyAsync(h, d, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CHNS_CUDA(cudaStreamSynchronize(s));
-  return CHNS_OK;
-}
-
 // host value of sum a^2 (FP32 grid or FP64 nodal via dot_host)
 static chns_status grid_sq(chns_learned* L, const float* a, double* out, cudaStream_t s) {
   const unsigned nb = std::min<unsigned>(grid_for(L->nv), 1024);
