@@ -109,6 +109,22 @@ def _dist():
     return ws, rank, local
 
 
+def replica_max(pg, values, device):
+    """Max over ranks of per-rank times (one all-reduce; identity without a process group)."""
+    if not pg:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def whole_job_value(ws, n_nodes, solves_per_rank, ms_max):
+    """DOFs/s of the whole job: every replica solves the same number of systems of n_nodes
+    unknowns; the slowest rank's time counts."""
+    return ws * n_nodes * solves_per_rank / (ms_max * 1e-3)
+
+
 # --------------------------------------------------------------------------- our arm
 def field_errors(final_fields, n_steps):
     """Relative L2 difference per field between the reduced-precision paths and the all-FP64
@@ -186,16 +202,11 @@ def run_ours(args):
                 pp_it += st.pp[l].iterations
             stats.append(st)
         launches = capi.chns_kernel_launches() - l0
-        tot_ms = sum(step_ms)
-        tmax = tot_ms
-        if pg:
-            t = torch.tensor([tot_ms, pp_ms], device="cuda", dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            tmax, pp_ms = float(t[0]), float(t[1])
+        tmax, pp_ms = replica_max(pg, [sum(step_ms), pp_ms], "cuda")
         last = stats[-1]
         final_fields[label] = ds.host()
         return dict(label=label, ms_per_step=tmax / args.steps,
-                    value=ws * N * pp_n / (pp_ms * 1e-3),
+                    value=whole_job_value(ws, N, pp_n, pp_ms),
                     pp_ms_per_solve=pp_ms / pp_n, pp_iters_per_solve=pp_it / pp_n,
                     launches=launches,
                     phases_ms=dict(ch=last.ms_ch, vp=last.ms_vp, pp=last.ms_pp, vu=last.ms_vu),
@@ -273,7 +284,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_val = ws * N / (statistics.mean(e2e_ms) * 1e-3)
+    e2e_val = whole_job_value(ws, N, 1, replica_max(pg, [statistics.mean(e2e_ms)], "cuda")[0])
 
     large = None
     if rank == 0 and not args.no_large:
