@@ -1249,12 +1249,15 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
     SchurPC<double> spc64;
     SchurPC<float> spc32;
     bool spc64_ok = false, spc32_ok = false;
-    auto schur64 = [&]() -> SchurPC<double>* {
+    // the FP64 preconditioner (nullptr when not used); *err receives a setup failure
+    auto schur64 = [&](chns_status* err) -> SchurPC<double>* {
+      *err = CHNS_OK;
       if (!schur) return nullptr;
       if (!spc64_ok) {
         double* vec[12];
         for (int k = 0; k < 12; ++k) vec[k] = ws.v64[3 + k / 3] + (k % 3) * Nn;
-        if (spc64.setup(c, vec, sp->inner_its) != CHNS_OK) return nullptr;
+        *err = spc64.setup(c, vec, sp->inner_its);
+        if (*err != CHNS_OK) return nullptr;
         spc64_ok = true;
       }
       return &spc64;
@@ -1311,8 +1314,8 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
         }
       }
       else {
-        SchurPC<double>* pc64 = schur64();
-        if (schur && !pc64) return CHNS_ECUDA;
+        SchurPC<double>* pc64 = schur64(&st);
+        if (st != CHNS_OK) return st;
         st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it, sp->restart, ws.gm_V,
                            ws.v64[7], &its, &rn, pc64);
       }
@@ -1422,8 +1425,8 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
                                ws.v64[7], &its, &frn, 0, nullptr, cheb ? &cheb64 : nullptr,
                                ws.v64[14]);
             else {
-              SchurPC<double>* pc64 = schur64();
-              if (schur && !pc64) return CHNS_ECUDA;
+              SchurPC<double>* pc64 = schur64(&st);
+              if (st != CHNS_OK) return st;
               st = gmres<double>(c, b, x, dinv64, block2, tol, sp->max_it - total, sp->restart,
                                  ws.gm_V, ws.v64[7], &its, &frn, pc64);
             }
