@@ -210,7 +210,8 @@ chns_status chns_phi_mass(const chns_mesh* mesh, const double* phi, double* out_
  * a fixed scratch array inside the library (65,536 partial sums, ~0.5 MB, which every GPU that
  * loads the library keeps until the process exits), and the result is written to `out`, a
  * device double owned by the caller. The call is asynchronous on `stream`.
- * Limits and rules: meshes of more than 8,388,608 elements are rejected with CHNS_EINVAL. The
+ * Limits and rules: meshes of more than 8,388,608 elements are rejected with CHNS_EINVAL, and so
+ * is a call made while another device is current than the one the mesh was created on. The
  * first call on a device looks up the scratch array's device address on the current device;
  * make that first call before any stream capture. Every call shares the one scratch array, so
  * calls that overlap on the GPU (other streams, other threads) race and give wrong results:

@@ -109,6 +109,7 @@ struct chns_mesh {
   mutable MomQState mq;
   int red_blocks = 0;
   int sm_count = 0;
+  int device = 0;  // CUDA device current at chns_mesh_create (holds every device table)
   // launch configuration of the operator applies (chns_mesh_set_apply_config)
   chns_apply_kernel apply_kernel = CHNS_APPLY_AUTO;
   int64_t apply_max_ctas = 0;

@@ -697,7 +697,11 @@ chns_status iterate(const Ctx& c, Step&& step, T* x, double tol_abs, int max_it,
     chns_status rc = CHNS_OK;
     for (int v = 0; v < 2 && rc == CHNS_OK; ++v) {
       cudaGraph_t g = nullptr;
-      CHNS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e0 = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e0 != cudaSuccess) {
+        rc = cuda_fail(e0, "cudaStreamBeginCapture");
+        break;
+      }
       const unsigned long long l0 = chns_launches_now();
       for (int i = 0; i < chunk && rc == CHNS_OK; ++i) rc = step(cs, i);
       // an even chunk ends with an odd iteration, which leaves r.r in slot 0
@@ -708,30 +712,49 @@ chns_status iterate(const Ctx& c, Step&& step, T* x, double tol_abs, int max_it,
         if (g) cudaGraphDestroy(g);
         break;
       }
-      if (e1 != cudaSuccess) return cuda_fail(e1, "cudaStreamEndCapture");
+      // on a failure below, fall through to the cleanup loop so that the graph and event of
+      // the other instance are released too
+      if (e1 != cudaSuccess) {
+        rc = cuda_fail(e1, "cudaStreamEndCapture");
+        break;
+      }
       cudaError_t e2 = cudaGraphInstantiate(&ge[v], g, 0);
       cudaGraphDestroy(g);
-      if (e2 != cudaSuccess) return cuda_fail(e2, "cudaGraphInstantiate");
-      CHNS_CUDA(cudaEventCreateWithFlags(&ev[v], cudaEventDisableTiming));
+      if (e2 != cudaSuccess) {
+        ge[v] = nullptr;
+        rc = cuda_fail(e2, "cudaGraphInstantiate");
+        break;
+      }
+      cudaError_t e3 = cudaEventCreateWithFlags(&ev[v], cudaEventDisableTiming);
+      if (e3 != cudaSuccess) {
+        ev[v] = nullptr;
+        rc = cuda_fail(e3, "cudaEventCreateWithFlags");
+        break;
+      }
     }
     note_launches_undo(2 * per_graph);  // captured, not executed
     if (rc == CHNS_OK) {
       int k = 0;
       bool done = false;
+      auto ok = [&](cudaError_t e, const char* what) {
+        if (e == cudaSuccess) return true;
+        rc = cuda_fail(e, what);
+        return false;
+      };
       while (!done) {
         const int v = k & 1;
-        CHNS_CUDA(cudaGraphLaunch(ge[v], c.s));
+        if (!ok(cudaGraphLaunch(ge[v], c.s), "cudaGraphLaunch")) break;
         note_launches(per_graph);
-        CHNS_CUDA(cudaEventRecord(ev[v], c.s));
+        if (!ok(cudaEventRecord(ev[v], c.s), "cudaEventRecord")) break;
         it += chunk;
         // check the previous chunk while this one runs
         if (k >= 1) {
-          CHNS_CUDA(cudaEventSynchronize(ev[v ^ 1]));
+          if (!ok(cudaEventSynchronize(ev[v ^ 1]), "cudaEventSynchronize")) break;
           rr = slot[v ^ 1];
           if (bad(rr) || std::sqrt(rr) <= tol_abs || stalled(it - chunk, rr)) done = true;
         }
         if (done || it >= max_it) {
-          CHNS_CUDA(cudaEventSynchronize(ev[v]));
+          if (!ok(cudaEventSynchronize(ev[v]), "cudaEventSynchronize")) break;
           rr = slot[v];
           done = true;
         }

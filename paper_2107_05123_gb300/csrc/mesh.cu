@@ -539,6 +539,7 @@ static chns_status build(const uint32_t* anchors, const uint8_t* levels, int64_t
   m->d.anchor = m->d_anchor;
   int dev = 0;
   CHNS_CUDA(cudaGetDevice(&dev));
+  m->device = dev;
   CHNS_CUDA(cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev));
   chns_status st = alloc_workspace(m);
   if (st != CHNS_OK) return st;

@@ -75,6 +75,10 @@ extern "C" chns_status chns_phi_mass_noalloc(const chns_mesh* m, const double* p
              "(at most 8388608 elements)");
   int dev = 0;
   CHNS_CUDA(cudaGetDevice(&dev));
+  // the mesh tables live on the device that was current at chns_mesh_create; the scratch array
+  // is looked up on the current one, so both must be the same GPU
+  CHNS_CHECK(dev == m->device, CHNS_EINVAL,
+             "chns_phi_mass_noalloc: the current device is not the mesh's device");
   NaDev* d = nullptr;
   chns_status st = na_setup(dev, &d);
   if (st != CHNS_OK) return st;

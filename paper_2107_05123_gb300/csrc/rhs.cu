@@ -265,7 +265,10 @@ static chns_status need(bool ok, const char* what) {
 
 chns_status phi_mass(const chns_mesh* m, const double* phi, double* out, cudaStream_t s) {
   const unsigned nb = nblk(m);
-  // partials live in the second v64 workspace slot tail-free region (n_elem/128 <= 3N)
+  // The block partials (n_elem/128 <= 3N values) go to the last FP64 workspace vector. The
+  // Chebyshev setup (cheb_bounds) also uses that vector as scratch; sharing it is safe because
+  // this call reads the partials back and synchronises the stream before it returns, and it is
+  // only called between solves (before and after a step), never inside one.
   double* part = m->ws.v64[kNumVec64 - 1];
   note_launch();
   k_phi_mass<<<nb, kRhsThreads, 0, s>>>(m->d, phi, part);
