@@ -92,16 +92,22 @@ typedef enum { CHNS_KSP_CG = 0, CHNS_KSP_GMRES = 1, CHNS_KSP_FCG = 2 } chns_ksp;
  * its flexible form (the preconditioned vectors are kept: restart <= 30). For meshes and
  * parameters where the biharmonic term dominates (small Cn h^-1), where the 2x2 nodal
  * block-Jacobi preconditioner stalls. */
+/* MULTIGRID (POISSON, with CG or FCG): one V-cycle of the geometric multigrid hierarchy
+ * solver_params.mg (chns_mg_create below) per iteration, run through the flexible-CG driver. The
+ * hierarchy's level operators are set up for the solve's coefficient phi~ at the start of the
+ * solve (chns_mg_setup) in the precision of the Krylov iteration. */
 typedef enum {
   CHNS_PC_NONE = 0,
   CHNS_PC_JACOBI = 1,
   CHNS_PC_LEARNED = 2,
   CHNS_PC_CHEBYSHEV = 3,
-  CHNS_PC_SCHUR = 4
+  CHNS_PC_SCHUR = 4,
+  CHNS_PC_MULTIGRID = 5
 } chns_pc;
 
 typedef struct chns_mesh chns_mesh;   /* opaque; owns device tables and workspace */
 typedef struct chns_learned chns_learned;  /* opaque; learned coarse correction (below) */
+typedef struct chns_mg chns_mg;       /* opaque; geometric multigrid hierarchy (below) */
 
 typedef struct {
   int64_t n_elem;
@@ -244,6 +250,7 @@ typedef struct {
   int32_t check_every;      /* CG/FCG: iterations between host convergence checks (>= 1) */
   chns_learned* learned;    /* CHNS_PC_LEARNED: the network (not owned); else ignored */
   int32_t inner_its;        /* CHNS_PC_SCHUR: CG iterations of each inner solve with H (0: 20) */
+  chns_mg* mg;              /* CHNS_PC_MULTIGRID: the hierarchy of this mesh (not owned) */
 } chns_solver_params;
 
 typedef struct {
@@ -303,6 +310,59 @@ typedef struct {
 
 chns_status chns_step(const chns_mesh* mesh, chns_state* state, const chns_params* prm,
                       const chns_step_params* sp, chns_step_stats* stats, void* stream);
+
+/* ---------------------------------------------------------------- geometric multigrid
+ * Not in the paper's solver stack, which preconditions the pressure Poisson system with PETSc's
+ * algebraic multigrid (App. A); the paper names a geometric multigrid on the octree as the
+ * remedy for the AMG setup cost that dominates its solver timings (Sec. 7, Conclusions).
+ * Hierarchy: level 0 is the mesh; level l+1 replaces every leaf of level l's finest octant level
+ *   by its parent (the one-level coarsening of the intergrid transfer, Sec. 5.4), until the
+ *   finest octant level is at most coarsest_level; the coarsest level must have <= 1024 nodes.
+ * Transfers: P_l (level l+1 -> l) evaluates the coarse finite-element function, hanging
+ *   constraints included, at the level-l nodes (child interpolation, Sec. 5.4); R_l = P_l^T.
+ * Level operators: the Poisson operator of each level with phi~ injected from the finer level.
+ * V-cycle: `degree` Chebyshev steps on D^-1 A over [lmax / smooth_range, lmax], lmax =
+ *   lmax_factor x the estimate of the largest eigenvalue of D^-1 A from `power_its` power
+ *   iterations started at v_i = dinv_i (h(i) / 2^32 - 1/2), h(i) = i * 2654435761 mod 2^32;
+ *   restriction of the residual; the cycle on the next level; prolongation; `degree`
+ *   Chebyshev steps from the corrected iterate. Coarsest level: z = (A + 1 1^T / n)^-1 r.
+ * The object owns its level meshes, transfer tables and vectors; it stays tied to the mesh it
+ * was built from (which must outlive it). Defaults (params NULL): coarsest_level 2, degree 3,
+ * power_its 12, smooth_range 15, lmax_factor 1.1. */
+typedef struct {
+  int32_t coarsest_level;   /* 0..CHNS_MAXD-1 */
+  int32_t degree;           /* Chebyshev steps before and after the coarse correction, 1..8 */
+  int32_t power_its;        /* 1..100 */
+  double smooth_range;      /* > 1 */
+  double lmax_factor;       /* >= 1 */
+} chns_mg_params;
+
+chns_status chns_mg_create(const chns_mesh* mesh, const chns_mg_params* params, void* stream,
+                           chns_mg** out);
+void chns_mg_destroy(chns_mg* mg);
+/* number of levels; n_nodes / n_elem (optional, host arrays of n_levels) per level, fine first */
+chns_status chns_mg_levels(const chns_mg* mg, int32_t* n_levels, int64_t* n_nodes,
+                           int64_t* n_elem);
+/* Level operators for the Poisson coefficient phi~ of level 0 (device array of n_nodes in the
+ * precision prec, CHNS_FP64 or CHNS_FP32; it is read by later V-cycles and must stay valid):
+ * injected coefficients, exact diagonals, Chebyshev intervals and the coarsest dense inverse.
+ * Synchronises the stream. */
+chns_status chns_mg_setup(chns_mg* mg, const chns_params* prm, const void* phi_tilde,
+                          chns_precision prec, void* stream);
+/* lmax[n_levels] of the last setup in precision prec (the coarsest level's entry is 0) */
+chns_status chns_mg_lambda(const chns_mg* mg, chns_precision prec, double* lmax);
+/* z = B r, one V-cycle (device arrays of n_nodes of level 0 in precision prec; r and z must not
+ * alias). Asynchronous; no allocation and no host synchronisation. */
+chns_status chns_mg_vcycle(chns_mg* mg, const void* r, void* z, chns_precision prec,
+                           void* stream);
+/* x_fine = P_level x_coarse and x_coarse = R_level x_fine between levels `level` and level + 1
+ * (FP64 device arrays) */
+chns_status chns_mg_prolong(const chns_mg* mg, int32_t level, const double* x_coarse,
+                            double* x_fine, void* stream);
+chns_status chns_mg_restrict(const chns_mg* mg, int32_t level, const double* x_fine,
+                             double* x_coarse, void* stream);
+/* phi~ of a level after an FP64 setup (FP64 device array of that level's n_nodes) */
+chns_status chns_mg_coefficient(const chns_mg* mg, int32_t level, double* phi, void* stream);
 
 /* ---------------------------------------------------------------- learned preconditioner
  * Not in the paper: a coarse correction for the pressure-Poisson solve, computed by a small

@@ -30,7 +30,7 @@ OP_NCOMP = {OP_POISSON: 1, OP_MASS: 3, OP_CH: 2, OP_MOMENTUM: 3}
 # chns_ksp / chns_pc
 KSP_CG, KSP_GMRES, KSP_FCG = 0, 1, 2
 APPLY_AUTO, APPLY_PATCH, APPLY_STREAM = 0, 1, 2
-PC_NONE, PC_JACOBI, PC_LEARNED, PC_CHEBYSHEV, PC_SCHUR = 0, 1, 2, 3, 4
+PC_NONE, PC_JACOBI, PC_LEARNED, PC_CHEBYSHEV, PC_SCHUR, PC_MULTIGRID = 0, 1, 2, 3, 4, 5
 
 
 class ChnsError(RuntimeError):
@@ -58,7 +58,13 @@ class chns_solver_params(C.Structure):
     _fields_ = [("ksp", C.c_int32), ("pc", C.c_int32), ("rtol", C.c_double),
                 ("max_it", C.c_int32), ("restart", C.c_int32), ("inner_precision", C.c_int32),
                 ("inner_rtol", C.c_double), ("max_refine", C.c_int32),
-                ("check_every", C.c_int32), ("learned", C.c_void_p), ("inner_its", C.c_int32)]
+                ("check_every", C.c_int32), ("learned", C.c_void_p), ("inner_its", C.c_int32),
+                ("mg", C.c_void_p)]
+
+
+class chns_mg_params(C.Structure):
+    _fields_ = [("coarsest_level", C.c_int32), ("degree", C.c_int32), ("power_its", C.c_int32),
+                ("smooth_range", C.c_double), ("lmax_factor", C.c_double)]
 
 
 class chns_solve_stats(C.Structure):
@@ -134,6 +140,15 @@ _SIGS = {
     "chns_learned_num_samples": ([_P], C.c_int32),
     "chns_learned_train": ([_P, _P, C.POINTER(chns_params), C.c_int32, C.c_double, C.c_uint64, _P,
                             _P], C.c_int),
+    "chns_mg_create": ([_P, C.POINTER(chns_mg_params), _P, C.POINTER(_P)], C.c_int),
+    "chns_mg_destroy": ([_P], None),
+    "chns_mg_levels": ([_P, C.POINTER(C.c_int32), _P, _P], C.c_int),
+    "chns_mg_setup": ([_P, C.POINTER(chns_params), _P, C.c_int, _P], C.c_int),
+    "chns_mg_lambda": ([_P, C.c_int, _P], C.c_int),
+    "chns_mg_vcycle": ([_P, _P, _P, C.c_int, _P], C.c_int),
+    "chns_mg_prolong": ([_P, C.c_int32, _P, _P, _P], C.c_int),
+    "chns_mg_restrict": ([_P, C.c_int32, _P, _P, _P], C.c_int),
+    "chns_mg_coefficient": ([_P, C.c_int32, _P, _P], C.c_int),
     "chns_last_error": ([], C.c_char_p),
     "chns_version": ([], C.c_char_p),
     "chns_kernel_launches": ([], C.c_uint64),
@@ -205,9 +220,9 @@ def make_coef(phi=None, u=(None, None, None), mu=None) -> chns_coef:
 
 def make_solver(ksp=KSP_CG, pc=PC_JACOBI, rtol=1e-8, max_it=10000, restart=30,
                 inner_precision=FP64, inner_rtol=1e-3, max_refine=20, check_every=1,
-                learned=None, inner_its=0):
+                learned=None, inner_its=0, mg=None):
     return chns_solver_params(ksp, pc, rtol, max_it, restart, inner_precision, inner_rtol,
-                              max_refine, check_every, learned, inner_its)
+                              max_refine, check_every, learned, inner_its, mg)
 
 
 # ------------------------------------------------------------------ mesh
@@ -336,6 +351,56 @@ def chns_step(mesh, state: chns_state, prm, step_params, stream=None) -> chns_st
 
 
 # ------------------------------------------------------------------ learned preconditioner
+# ------------------------------------------------------------------ geometric multigrid
+def chns_mg_create(mesh, coarsest_level=2, degree=3, power_its=12, smooth_range=15.0,
+                   lmax_factor=1.1, stream=None):
+    p = chns_mg_params(coarsest_level, degree, power_its, smooth_range, lmax_factor)
+    out = C.c_void_p()
+    _check(LIB.chns_mg_create(mesh, C.byref(p), _stream(stream), C.byref(out)), "chns_mg_create")
+    return out.value
+
+
+def chns_mg_destroy(mg):
+    LIB.chns_mg_destroy(mg)
+
+
+def chns_mg_levels(mg):
+    """(n_nodes, n_elem) per level, fine first, as int64 numpy arrays."""
+    n = C.c_int32()
+    _check(LIB.chns_mg_levels(mg, C.byref(n), None, None), "chns_mg_levels")
+    nodes = np.zeros(n.value, dtype=np.int64)
+    elems = np.zeros(n.value, dtype=np.int64)
+    _check(LIB.chns_mg_levels(mg, C.byref(n), _ptr(nodes), _ptr(elems)), "chns_mg_levels")
+    return nodes, elems
+
+
+def chns_mg_setup(mg, prm, phi, prec=FP64, stream=None):
+    _check(LIB.chns_mg_setup(mg, C.byref(prm), _ptr(phi), prec, _stream(stream)), "chns_mg_setup")
+
+
+def chns_mg_lambda(mg, n_levels, prec=FP64) -> np.ndarray:
+    out = np.zeros(n_levels, dtype=np.float64)
+    _check(LIB.chns_mg_lambda(mg, prec, _ptr(out)), "chns_mg_lambda")
+    return out
+
+
+def chns_mg_vcycle(mg, r, z, prec=FP64, stream=None):
+    _check(LIB.chns_mg_vcycle(mg, _ptr(r), _ptr(z), prec, _stream(stream)), "chns_mg_vcycle")
+
+
+def chns_mg_prolong(mg, level, xc, xf, stream=None):
+    _check(LIB.chns_mg_prolong(mg, level, _ptr(xc), _ptr(xf), _stream(stream)), "chns_mg_prolong")
+
+
+def chns_mg_restrict(mg, level, xf, xc, stream=None):
+    _check(LIB.chns_mg_restrict(mg, level, _ptr(xf), _ptr(xc), _stream(stream)),
+           "chns_mg_restrict")
+
+
+def chns_mg_coefficient(mg, level, phi, stream=None):
+    _check(LIB.chns_mg_coefficient(mg, level, _ptr(phi), _stream(stream)), "chns_mg_coefficient")
+
+
 def chns_learned_create(D, capacity=0, seed=0, stream=None):
     out = C.c_void_p()
     _check(LIB.chns_learned_create(int(D), int(capacity), int(seed), _stream(stream),

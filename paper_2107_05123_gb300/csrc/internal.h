@@ -83,6 +83,9 @@ struct chns_mesh {
   int64_t n_boundary = 0;
   std::vector<uint32_t> node_coords;  // host copy, 3*n_nodes
   std::vector<uint8_t> node_bnd;      // host copy
+  // host copies of the element corner and hanging tables (kept for multigrid level meshes)
+  std::vector<int32_t> h_enode;
+  std::vector<int4> h_hang;
   // device allocations
   int4* d_enode = nullptr;
   uint8_t* d_level = nullptr;
@@ -118,6 +121,13 @@ struct chns_mesh {
 namespace chns {
 
 void set_error(const std::string& msg);
+// Mesh construction (mesh.cu). light: no solver workspace (level meshes of a multigrid
+// hierarchy, which are only applied); keep_host: keep host copies of the element and hanging
+// tables. free_mesh releases a mesh built by build_mesh (also after a failed build).
+chns_status build_mesh(const uint32_t* anchors, const uint8_t* levels, int64_t n,
+                       const double extent[3], cudaStream_t stream, chns_mesh* m, bool light,
+                       bool keep_host);
+void free_mesh(chns_mesh* m);
 // count of kernel launches issued by the library (diagnostic); graph launches add the number of
 // kernels they contain, and launches recorded during a stream capture are taken back out
 void note_launch();

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "multigrid.h"
 #include "reduce.cuh"
 
 namespace chns {
@@ -928,7 +929,7 @@ template <class T>
 chns_status fcg(const Ctx& c, const T* b, T* x, const T* dinv, chns_learned* L, double tol_abs,
                 int max_it, int chunk, T* r, T* z, T* p, T* q, T* p2, T* w, int* iters,
                 double* rnorm, int stall = 0, const Snap* snap = nullptr,
-                const Cheb* cheb = nullptr, T* dcheb = nullptr) {
+                const Cheb* cheb = nullptr, T* dcheb = nullptr, chns_mg* mg = nullptr) {
   T* pb[2] = {p, p2};
   const int64_t n = c.n;
   const unsigned rg = red_grid(c.m, n), vg = vgrid(c.m, n);
@@ -946,6 +947,7 @@ chns_status fcg(const Ctx& c, const T* b, T* x, const T* dinv, chns_learned* L, 
       return CHNS_OK;
     }
     if (cheb) return cheb_apply<T>(c, s, *cheb, dinv, r, z, w, dcheb);
+    if (mg) return mg_vcycle<T>(mg, r, z, s);
     note_launch();
     if (dinv) k_mul<T><<<vg, kVecThreads, 0, s>>>(dinv, r, z, n);
     else k_axpby<T><<<vg, kVecThreads, 0, s>>>(1.0, r, 0.0, r, z, n);
@@ -1182,8 +1184,13 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
   CHNS_CHECK(sp->ksp == CHNS_KSP_CG || sp->ksp == CHNS_KSP_GMRES || sp->ksp == CHNS_KSP_FCG,
              CHNS_EINVAL, "bad ksp");
   CHNS_CHECK(sp->pc == CHNS_PC_NONE || sp->pc == CHNS_PC_JACOBI || sp->pc == CHNS_PC_LEARNED ||
-                 sp->pc == CHNS_PC_CHEBYSHEV || sp->pc == CHNS_PC_SCHUR,
+                 sp->pc == CHNS_PC_CHEBYSHEV || sp->pc == CHNS_PC_SCHUR ||
+                 sp->pc == CHNS_PC_MULTIGRID,
              CHNS_EINVAL, "bad preconditioner");
+  CHNS_CHECK(sp->pc != CHNS_PC_MULTIGRID ||
+                 (op == CHNS_OP_POISSON && sp->ksp != CHNS_KSP_GMRES && sp->mg &&
+                  !sp->mg->lv.empty() && sp->mg->lv[0].mesh == m),
+             CHNS_EINVAL, "multigrid: Poisson operator, CG or FCG, and a hierarchy of this mesh");
   // flexible GMRES keeps restart preconditioned vectors beside the restart + 1 basis vectors of
   // 2 n_nodes in the basis buffer of (CHNS_GMRES_MAX_RESTART + 1) x 3 n_nodes
   CHNS_CHECK(sp->pc != CHNS_PC_SCHUR ||
@@ -1257,7 +1264,9 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
     // the Chebyshev preconditioner runs through the flexible-CG driver (with a fixed SPD
     // preconditioner its iterates are those of PCG)
     const bool cheb = sp->pc == CHNS_PC_CHEBYSHEV;
-    const bool use_fcg = sp->ksp == CHNS_KSP_FCG || cheb;
+    // the V-cycle preconditioner also runs through the flexible-CG driver
+    chns_mg* mg = sp->pc == CHNS_PC_MULTIGRID ? sp->mg : nullptr;
+    const bool use_fcg = sp->ksp == CHNS_KSP_FCG || cheb || mg;
     Cheb cheb64, cheb32;
     chns_learned* L = sp->pc == CHNS_PC_LEARNED ? sp->learned : nullptr;
     if (L) {
@@ -1320,13 +1329,18 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
         st = cheb_bounds<double>(c, dinv64, b, ws.v64[14], ws.v64[15], sp->restart, &cheb64);
         if (st != CHNS_OK) return st;
       }
-      if (sp->ksp == CHNS_KSP_CG && !cheb)
+      if (mg) {
+        st = mg_setup(mg, prm, coef->phi_tilde, CHNS_FP64, s);
+        if (st != CHNS_OK) return st;
+      }
+      if (sp->ksp == CHNS_KSP_CG && !cheb && !mg)
         st = pcg<double>(c, b, x, dinv64, tol, sp->max_it, sp->check_every, r64, ws.v64[3],
                          ws.v64[4], ws.v64[5], ws.v64[6], &its, &rn);
       else if (use_fcg) {
         st = fcg<double>(c, b, x, dinv64, L, tol, sp->max_it, sp->check_every, r64, ws.v64[3],
                          ws.v64[4], ws.v64[5], ws.v64[6], ws.v64[7], &its, &rn,
-                         L ? kLearnedStall : 0, nullptr, cheb ? &cheb64 : nullptr, ws.v64[14]);
+                         L ? kLearnedStall : 0, nullptr, cheb ? &cheb64 : nullptr, ws.v64[14],
+                         mg);
         if (L && st == CHNS_ENOTCONV && its < sp->max_it) {
           // the learned correction stalled: Jacobi-PCG from the current iterate
           ++out.fallbacks;
@@ -1379,6 +1393,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
       }
       int total = 0, refine = 0;
       bool learned_ok = true;
+      bool mg32_ready = false;
       last_rn = -1.0;
       double prev_rn = 0.0;
       chns_precision cur = c.inner;
@@ -1439,14 +1454,18 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
                                        &cheb64);
               if (st != CHNS_OK) return st;
             }
-            if (sp->ksp == CHNS_KSP_CG && !cheb)
+            if (mg) {
+              st = mg_setup(mg, prm, coef->phi_tilde, CHNS_FP64, s);
+              if (st != CHNS_OK) return st;
+            }
+            if (sp->ksp == CHNS_KSP_CG && !cheb && !mg)
               st = pcg<double>(c, b, x, dinv64, tol, sp->max_it - total, sp->check_every, r64,
                                ws.v64[3], ws.v64[4], ws.v64[5], ws.v64[6], &its, &frn);
             else if (use_fcg)
               st = fcg<double>(c, b, x, dinv64, nullptr, tol, sp->max_it - total,
                                sp->check_every, r64, ws.v64[3], ws.v64[4], ws.v64[5], ws.v64[6],
                                ws.v64[7], &its, &frn, 0, nullptr, cheb ? &cheb64 : nullptr,
-                               ws.v64[14]);
+                               ws.v64[14], mg);
             else {
               SchurPC<double>* pc64 = schur64(&st);
               if (st != CHNS_OK) return st;
@@ -1477,7 +1496,12 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
           st = cheb_bounds<float>(c, dinv32, r32, ws.v32[9], ws.v32[7], sp->restart, &cheb32);
           if (st != CHNS_OK) return st;
         }
-        if (sp->ksp == CHNS_KSP_CG && !cheb)
+        if (mg && !mg32_ready) {
+          st = mg_setup(mg, prm, coef32.phi_tilde, CHNS_FP32, s);
+          if (st != CHNS_OK) return st;
+          mg32_ready = true;
+        }
+        if (sp->ksp == CHNS_KSP_CG && !cheb && !mg)
           ist = pcg<float>(c, r32, d32, dinv32, itol, budget, sp->check_every, ws.v32[3],
                            ws.v32[4], ws.v32[5], ws.v32[6], ws.v32[8], &its, &irn);
         else if (use_fcg) {
@@ -1485,7 +1509,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
           ist = fcg<float>(c, r32, d32, dinv32, Lc, itol, budget, sp->check_every, ws.v32[3],
                            ws.v32[4], ws.v32[5], ws.v32[6], ws.v32[8], ws.v32[7], &its, &irn,
                            Lc ? kLearnedStall : 0, nullptr, cheb ? &cheb32 : nullptr,
-                           ws.v32[9]);
+                           ws.v32[9], mg);
           if (Lc && ist == CHNS_ENOTCONV && its < budget) {
             // the learned correction stalled: Jacobi only from the next refinement cycle on
             learned_ok = false;

@@ -18,48 +18,15 @@
 #include <thread>
 
 #include "internal.h"
+#include "hostutil.h"
 
 namespace chns {
 namespace {
 
-constexpr uint64_t kFull = 1ull << CHNS_MAXD;
-
-inline uint64_t spread3(uint64_t v) {
-  v &= 0x1FFFFFull;
-  v = (v | (v << 32)) & 0x1F00000000FFFFull;
-  v = (v | (v << 16)) & 0x1F0000FF0000FFull;
-  v = (v | (v << 8)) & 0x100F00F00F00F00Full;
-  v = (v | (v << 4)) & 0x10C30C30C30C30C3ull;
-  v = (v | (v << 2)) & 0x1249249249249249ull;
-  return v;
-}
-inline uint64_t compact3(uint64_t v) {
-  v &= 0x1249249249249249ull;
-  v = (v | (v >> 2)) & 0x10C30C30C30C30C3ull;
-  v = (v | (v >> 4)) & 0x100F00F00F00F00Full;
-  v = (v | (v >> 8)) & 0x1F0000FF0000FFull;
-  v = (v | (v >> 16)) & 0x1F00000000FFFFull;
-  v = (v | (v >> 32)) & 0x1FFFFFull;
-  return v;
-}
-inline uint64_t morton(uint64_t x, uint64_t y, uint64_t z) {
-  return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
-}
-
-// Run f(begin, end) over [0, n) on up to hw threads.
-template <class F>
-void parallel_for(int64_t n, F f) {
-  int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-  if (n < 65536) nt = 1;
-  std::vector<std::thread> th;
-  int64_t chunk = (n + nt - 1) / nt;
-  for (int t = 0; t < nt; ++t) {
-    int64_t b = t * chunk, e = std::min(n, b + chunk);
-    if (b >= e) break;
-    th.emplace_back([=]() { f(b, e); });
-  }
-  for (auto& t : th) t.join();
-}
+using host::compact3;
+using host::kFull;
+using host::morton;
+using host::parallel_for;
 
 struct Cancel {
   uint64_t key;      // Morton key of the midpoint/centre
@@ -110,10 +77,16 @@ inline int cancel_geom(int kind, int par[4], int mid_half[3], int base_bits[3]) 
 
 }  // namespace
 
-static chns_status alloc_workspace(chns_mesh* m) {
+static chns_status alloc_workspace(chns_mesh* m, bool light) {
   const int64_t N = m->d.n_nodes;
   const size_t n3 = (size_t)(3 * N);
   Workspace& w = m->ws;
+  if (light) {
+    // level meshes of a multigrid hierarchy: operator applies and diagonals only (no Krylov
+    // solve runs on them), so no solver vectors
+    CHNS_CUDA(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
+    return CHNS_OK;
+  }
   w.v64.assign(kNumVec64, nullptr);
   w.v32.assign(kNumVec32, nullptr);
   for (auto& p : w.v64) CHNS_CUDA(cudaMalloc(&p, n3 * sizeof(double)));
@@ -139,7 +112,7 @@ static void dfree(void* p) {
   if (p) cudaFree(p);
 }
 
-static void free_mesh(chns_mesh* m) {
+void free_mesh(chns_mesh* m) {
   if (!m) return;
   dfree(m->d_enode);
   dfree(m->d_level);
@@ -291,8 +264,9 @@ static void build_patches(int64_t n, int64_t N, const std::vector<int32_t>& enod
     if (id >= 0 && count[id & kIdxMask & ~kDirBit] == 1) id |= kOwnBit;
 }
 
-static chns_status build(const uint32_t* anchors, const uint8_t* levels, int64_t n,
-                         const double extent[3], cudaStream_t stream, chns_mesh* m) {
+chns_status build_mesh(const uint32_t* anchors, const uint8_t* levels, int64_t n,
+                       const double extent[3], cudaStream_t stream, chns_mesh* m, bool light,
+                       bool keep_host) {
   CHNS_CHECK(n > 0 && n < (int64_t(1) << 28), CHNS_EINVAL, "n_leaves out of range");
   for (int d = 0; d < 3; ++d)
     CHNS_CHECK(extent[d] > 0.0, CHNS_EINVAL, "extent must be positive");
@@ -454,6 +428,11 @@ static chns_status build(const uint32_t* anchors, const uint8_t* levels, int64_t
       }
   });
 
+  if (keep_host) {
+    m->h_enode = enode;
+    m->h_hang.assign(hang.begin(), hang.begin() + H);
+  }
+
   // ---- patches (CTA-level gather / scatter)
   PatchTables P;
   build_patches(n, N, enode, hang, levels, P);
@@ -541,7 +520,7 @@ static chns_status build(const uint32_t* anchors, const uint8_t* levels, int64_t
   CHNS_CUDA(cudaGetDevice(&dev));
   m->device = dev;
   CHNS_CUDA(cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev));
-  chns_status st = alloc_workspace(m);
+  chns_status st = alloc_workspace(m, light);
   if (st != CHNS_OK) return st;
   CHNS_CUDA(cudaStreamSynchronize(stream));
   return CHNS_OK;
@@ -564,7 +543,8 @@ extern "C" chns_status chns_mesh_create(const uint32_t* anchors, const uint8_t* 
   }
   chns_status st;
   try {
-    st = chns::build(anchors, levels, n_leaves, extent, chns::as_stream(stream), m);
+    st = chns::build_mesh(anchors, levels, n_leaves, extent, chns::as_stream(stream), m, false,
+                          false);
   } catch (const std::bad_alloc&) {
     chns::set_error("chns_mesh_create: out of host memory");
     st = CHNS_ENOMEM;

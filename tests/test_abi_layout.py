@@ -13,7 +13,7 @@ from paper_2107_05123_gb300 import _lib as capi
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = ["chns_mesh_info", "chns_params", "chns_coef", "chns_solver_params", "chns_solve_stats",
-           "chns_state", "chns_step_params", "chns_step_stats"]
+           "chns_state", "chns_step_params", "chns_step_stats", "chns_mg_params"]
 
 
 def _c_layout(tmp_path):
