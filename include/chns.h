@@ -95,7 +95,10 @@ typedef enum { CHNS_KSP_CG = 0, CHNS_KSP_GMRES = 1, CHNS_KSP_FCG = 2 } chns_ksp;
 /* MULTIGRID (POISSON, with CG or FCG): one V-cycle of the geometric multigrid hierarchy
  * solver_params.mg (chns_mg_create below) per iteration, run through the flexible-CG driver. The
  * hierarchy's level operators are set up for the solve's coefficient phi~ at the start of the
- * solve (chns_mg_setup) in the precision of the Krylov iteration. */
+ * solve (chns_mg_setup) in the precision of the Krylov iteration.
+ * With SCHUR, a hierarchy in solver_params.mg (optional) replaces each inner CG solve with H by
+ * one V-cycle of H (chns_mg_setup_shifted with sa = 1/sqrt(dt), sb = Cn sqrt(k)), kept set up
+ * from one solve to the next while dt, Pe and Cn do not change. */
 typedef enum {
   CHNS_PC_NONE = 0,
   CHNS_PC_JACOBI = 1,
@@ -349,11 +352,20 @@ chns_status chns_mg_levels(const chns_mg* mg, int32_t* n_levels, int64_t* n_node
  * Synchronises the stream. */
 chns_status chns_mg_setup(chns_mg* mg, const chns_params* prm, const void* phi_tilde,
                           chns_precision prec, void* stream);
-/* lmax[n_levels] of the last setup in precision prec (the coarsest level's entry is 0) */
-chns_status chns_mg_lambda(const chns_mg* mg, chns_precision prec, double* lmax);
-/* z = B r, one V-cycle (device arrays of n_nodes of level 0 in precision prec; r and z must not
- * alias). Asynchronous; no allocation and no host synchronisation. */
-chns_status chns_mg_vcycle(chns_mg* mg, const void* r, void* z, chns_precision prec,
+/* The same for the constant-coefficient operator sa (q, p) + sb (grad q, grad p), sa > 0, sb >= 0
+ * (the inner operator H of the CH Schur-complement preconditioner): no coefficient, the coarsest
+ * inverse without the 1 1^T term. A setup with the sa, sb and precision of the last one returns
+ * at once. The Poisson and the shifted setups are kept side by side. */
+chns_status chns_mg_setup_shifted(chns_mg* mg, const chns_params* prm, double sa, double sb,
+                                  chns_precision prec, void* stream);
+typedef enum { CHNS_MG_POISSON = 0, CHNS_MG_SHIFTED = 1 } chns_mg_operator;
+/* lmax[n_levels] of the last setup of operator op in precision prec (the coarsest level's entry
+ * is 0) */
+chns_status chns_mg_lambda(const chns_mg* mg, int32_t op, chns_precision prec, double* lmax);
+/* z = B r, one V-cycle of operator op (chns_mg_operator; device arrays of n_nodes of level 0 in
+ * precision prec; r and z must not alias). Asynchronous; no allocation and no host
+ * synchronisation. */
+chns_status chns_mg_vcycle(chns_mg* mg, int32_t op, const void* r, void* z, chns_precision prec,
                            void* stream);
 /* x_fine = P_level x_coarse and x_coarse = R_level x_fine between levels `level` and level + 1
  * (FP64 device arrays) */

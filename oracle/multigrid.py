@@ -22,6 +22,9 @@ paper's octree operations and a standard V-cycle:
   [lmax / smooth_range, lmax], lmax = lmax_factor x the power estimate of the largest
   eigenvalue of D^-1 A (`power_its` iterations from a fixed start vector, `start_vector`);
 * coarsest level: the exact mean-zero solution, (A + 1 1^T / n)^-1 r (pure Neumann);
+* the same cycle for the constant-coefficient operator sa (q, p) + sb (grad q, grad p) with
+  sa > 0 (the inner operator H of the Cahn-Hilliard Schur-complement preconditioner,
+  solvers.ch_schur_precond), whose coarsest level is solved exactly without the 1 1^T term;
 * V-cycle: pre-smoothing from zero, residual, restriction, recursion, prolongation, and
   post-smoothing on the new residual with the same polynomial, so that the cycle is a
   symmetric linear operator.
@@ -181,22 +184,28 @@ class VCycle:
     """The V-cycle preconditioner z = B r of the Poisson operator for the coefficient phi~ of
     the fine mesh."""
 
-    def __init__(self, meshes, prm, phi_t, degree=3, power_its=12, smooth_range=15.0,
-                 lmax_factor=1.1, constant_coefficient=False):
+    def __init__(self, meshes, prm, phi_t=None, degree=3, power_its=12, smooth_range=15.0,
+                 lmax_factor=1.1, constant_coefficient=False, shift=None):
+        """shift = (sa, sb): the level operators are sa M + sb K instead of the Poisson
+        operator with coefficient phi_t."""
         self.meshes = meshes
         self.degree = degree
         co = fem.Coeffs(prm)
         self.P = [prolongation(meshes[l], meshes[l + 1]) for l in range(len(meshes) - 1)]
         self.inj = [injection(meshes[l], meshes[l + 1]) for l in range(len(meshes) - 1)]
-        phis = [np.asarray(phi_t, dtype=np.float64)]
-        for l in range(len(meshes) - 1):
-            phis.append(phis[-1][self.inj[l]])
-        self.phi = phis
+        if shift is None:
+            phis = [np.asarray(phi_t, dtype=np.float64)]
+            for l in range(len(meshes) - 1):
+                phis.append(phis[-1][self.inj[l]])
+            self.phi = phis
         self.A, self.dinv, self.lmax, self.lmin = [], [], [], []
         for l, m in enumerate(meshes):
             el = fem.Elem(m)
-            if constant_coefficient:
-                A = fem.stiffness(el, np.ones((m.n_elem, 8)))
+            ones = np.ones((m.n_elem, 8))
+            if shift is not None:
+                A = shift[0] * fem.mass(el, ones) + shift[1] * fem.stiffness(el, ones)
+            elif constant_coefficient:
+                A = fem.stiffness(el, ones)
             else:
                 A = fem.poisson(el, co, phis[l])
             self.A.append(A.tocsr())
@@ -207,7 +216,7 @@ class VCycle:
             self.lmin.append(lmax_factor * lam / smooth_range)
         Ac = self.A[-1].toarray()
         n = Ac.shape[0]
-        self.coarse_reg = Ac + np.full((n, n), 1.0 / n)
+        self.coarse_reg = Ac if shift is not None else Ac + np.full((n, n), 1.0 / n)
 
     def smooth(self, l, r):
         from .solvers import chebyshev_precond

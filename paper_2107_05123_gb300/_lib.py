@@ -31,6 +31,8 @@ OP_NCOMP = {OP_POISSON: 1, OP_MASS: 3, OP_CH: 2, OP_MOMENTUM: 3}
 KSP_CG, KSP_GMRES, KSP_FCG = 0, 1, 2
 APPLY_AUTO, APPLY_PATCH, APPLY_STREAM = 0, 1, 2
 PC_NONE, PC_JACOBI, PC_LEARNED, PC_CHEBYSHEV, PC_SCHUR, PC_MULTIGRID = 0, 1, 2, 3, 4, 5
+# chns_mg_operator
+MG_POISSON, MG_SHIFTED = 0, 1
 
 
 class ChnsError(RuntimeError):
@@ -144,8 +146,10 @@ _SIGS = {
     "chns_mg_destroy": ([_P], None),
     "chns_mg_levels": ([_P, C.POINTER(C.c_int32), _P, _P], C.c_int),
     "chns_mg_setup": ([_P, C.POINTER(chns_params), _P, C.c_int, _P], C.c_int),
-    "chns_mg_lambda": ([_P, C.c_int, _P], C.c_int),
-    "chns_mg_vcycle": ([_P, _P, _P, C.c_int, _P], C.c_int),
+    "chns_mg_setup_shifted": ([_P, C.POINTER(chns_params), C.c_double, C.c_double, C.c_int, _P],
+                              C.c_int),
+    "chns_mg_lambda": ([_P, C.c_int32, C.c_int, _P], C.c_int),
+    "chns_mg_vcycle": ([_P, C.c_int32, _P, _P, C.c_int, _P], C.c_int),
     "chns_mg_prolong": ([_P, C.c_int32, _P, _P, _P], C.c_int),
     "chns_mg_restrict": ([_P, C.c_int32, _P, _P, _P], C.c_int),
     "chns_mg_coefficient": ([_P, C.c_int32, _P, _P], C.c_int),
@@ -378,14 +382,19 @@ def chns_mg_setup(mg, prm, phi, prec=FP64, stream=None):
     _check(LIB.chns_mg_setup(mg, C.byref(prm), _ptr(phi), prec, _stream(stream)), "chns_mg_setup")
 
 
-def chns_mg_lambda(mg, n_levels, prec=FP64) -> np.ndarray:
+def chns_mg_setup_shifted(mg, prm, sa, sb, prec=FP64, stream=None):
+    _check(LIB.chns_mg_setup_shifted(mg, C.byref(prm), sa, sb, prec, _stream(stream)),
+           "chns_mg_setup_shifted")
+
+
+def chns_mg_lambda(mg, n_levels, prec=FP64, op=MG_POISSON) -> np.ndarray:
     out = np.zeros(n_levels, dtype=np.float64)
-    _check(LIB.chns_mg_lambda(mg, prec, _ptr(out)), "chns_mg_lambda")
+    _check(LIB.chns_mg_lambda(mg, op, prec, _ptr(out)), "chns_mg_lambda")
     return out
 
 
-def chns_mg_vcycle(mg, r, z, prec=FP64, stream=None):
-    _check(LIB.chns_mg_vcycle(mg, _ptr(r), _ptr(z), prec, _stream(stream)), "chns_mg_vcycle")
+def chns_mg_vcycle(mg, r, z, prec=FP64, stream=None, op=MG_POISSON):
+    _check(LIB.chns_mg_vcycle(mg, op, _ptr(r), _ptr(z), prec, _stream(stream)), "chns_mg_vcycle")
 
 
 def chns_mg_prolong(mg, level, xc, xf, stream=None):

@@ -857,9 +857,10 @@ struct SchurPC {
   T* dH = nullptr;
   T* t[8] = {};          // scratch N-vectors: CG r, z, p, q, p2; t, w, u
   int itH = 20, itM = 5;
+  chns_mg* mg = nullptr;  // when set, each H^-1 is one V-cycle of the shifted operator H
 
   // contexts and diagonals; vec: >= 10 scratch N-vectors
-  chns_status setup(const Ctx& c, T* const* vec, int inner_its) {
+  chns_status setup(const Ctx& c, T* const* vec, int inner_its, chns_mg* hier = nullptr) {
     const int64_t N = c.m->d.n_nodes;
     const double dt = c.prm->dt, Pe = c.prm->Pe, Cn = c.prm->Cn;
     const double kmu = 0.5 / (Pe * Cn), kphi = 0.5 * Cn * Cn;
@@ -881,6 +882,11 @@ struct SchurPC {
     for (int k = 0; k < 8; ++k) t[k] = vec[2 + k];
     const chns_precision pr = sizeof(T) == sizeof(double) ? CHNS_FP64 : CHNS_FP32;
     const void* phi = sizeof(T) == sizeof(double) ? c.coef64->phi_tilde : c.coefR.phi_tilde;
+    mg = hier;
+    if (mg) {  // H has constant coefficients: the hierarchy keeps its setup between solves
+      chns_status st = mg_setup_shifted(mg, c.prm, cH.sa, cH.sb, pr, c.s);
+      if (st != CHNS_OK) return st;
+    }
     chns_status st = diag_shift(c.m, c.prm, phi, cM.sa, cM.sb, dM, pr, c.s);
     if (st != CHNS_OK) return st;
     st = diag_shift(c.m, c.prm, phi, cH.sa, cH.sb, dH, pr, c.s);
@@ -910,11 +916,17 @@ struct SchurPC {
     if (st != CHNS_OK) return st;
     note_launch();
     k_axpby<T><<<vg, kVecThreads, 0, cM.s>>>(1.0, vphi, -1.0, tt, u, N);
-    st = cg_fixed<T>(cH, u, w, dH, itH, r, zz, p, q, p2);
+    if (mg)
+      st = mg_vcycle<T>(mg, kMgShifted, u, w, cM.s);
+    else
+      st = cg_fixed<T>(cH, u, w, dH, itH, r, zz, p, q, p2);
     if (st != CHNS_OK) return st;
     st = apply_T<T>(cM, w, tt);
     if (st != CHNS_OK) return st;
-    st = cg_fixed<T>(cH, tt, zphi, dH, itH, r, zz, p, q, p2);
+    if (mg)
+      st = mg_vcycle<T>(mg, kMgShifted, tt, zphi, cM.s);
+    else
+      st = cg_fixed<T>(cH, tt, zphi, dH, itH, r, zz, p, q, p2);
     if (st != CHNS_OK) return st;
     CHNS_CUDA(cudaGetLastError());
     return CHNS_OK;
@@ -947,7 +959,7 @@ chns_status fcg(const Ctx& c, const T* b, T* x, const T* dinv, chns_learned* L, 
       return CHNS_OK;
     }
     if (cheb) return cheb_apply<T>(c, s, *cheb, dinv, r, z, w, dcheb);
-    if (mg) return mg_vcycle<T>(mg, r, z, s);
+    if (mg) return mg_vcycle<T>(mg, kMgPoisson, r, z, s);
     note_launch();
     if (dinv) k_mul<T><<<vg, kVecThreads, 0, s>>>(dinv, r, z, n);
     else k_axpby<T><<<vg, kVecThreads, 0, s>>>(1.0, r, 0.0, r, z, n);
@@ -1191,6 +1203,8 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
                  (op == CHNS_OP_POISSON && sp->ksp != CHNS_KSP_GMRES && sp->mg &&
                   !sp->mg->lv.empty() && sp->mg->lv[0].mesh == m),
              CHNS_EINVAL, "multigrid: Poisson operator, CG or FCG, and a hierarchy of this mesh");
+  CHNS_CHECK(sp->pc != CHNS_PC_SCHUR || !sp->mg || (!sp->mg->lv.empty() && sp->mg->lv[0].mesh == m),
+             CHNS_EINVAL, "Schur preconditioner: the multigrid hierarchy is not of this mesh");
   // flexible GMRES keeps restart preconditioned vectors beside the restart + 1 basis vectors of
   // 2 n_nodes in the basis buffer of (CHNS_GMRES_MAX_RESTART + 1) x 3 n_nodes
   CHNS_CHECK(sp->pc != CHNS_PC_SCHUR ||
@@ -1288,7 +1302,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
       if (!spc64_ok) {
         double* vec[12];
         for (int k = 0; k < 12; ++k) vec[k] = ws.v64[3 + k / 3] + (k % 3) * Nn;
-        *err = spc64.setup(c, vec, sp->inner_its);
+        *err = spc64.setup(c, vec, sp->inner_its, sp->mg);
         if (*err != CHNS_OK) return nullptr;
         spc64_ok = true;
       }
@@ -1520,7 +1534,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
           if (schur && !spc32_ok) {
             float* vec[12];
             for (int k = 0; k < 12; ++k) vec[k] = ws.v32[3 + k / 3] + (k % 3) * Nn;
-            st = spc32.setup(c, vec, sp->inner_its);
+            st = spc32.setup(c, vec, sp->inner_its, sp->mg);
             if (st != CHNS_OK) return st;
             spc32_ok = true;
           }

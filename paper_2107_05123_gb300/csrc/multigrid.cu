@@ -149,9 +149,10 @@ __global__ void k_convert(const TI* __restrict__ a, TO* __restrict__ b, int64_t 
   MG_LOOP(i, n) b[i] = (TO)a[i];
 }
 
-// Dense matrix of the coarsest level's Poisson operator, A[i * n + j] += (P^T A_e P)_ij, one
-// thread per element: the element matrix column by column (the element operator applied to unit
-// vectors), distributed through the hanging constraints.
+// Dense matrix of the coarsest level's operator K (Poisson or shifted), A[i * n + j] +=
+// (P^T A_e P)_ij, one thread per element: the element matrix column by column (the element
+// operator applied to unit vectors), distributed through the hanging constraints.
+template <class K>
 __global__ void k_dense_assemble(MeshDev m, DevParams p, CoefArgs<double> cf,
                                  double* __restrict__ A, int n) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -159,7 +160,7 @@ __global__ void k_dense_assemble(MeshDev m, DevParams p, CoefArgs<double> cf,
   int idx[8];
   load_corners(m, e, idx);
   const Geo<double> g = geometry<double>(m, e);
-  PoissonK<double, double> k;
+  K k;
   k.load(m, p, cf, idx, g);
   // corner references: up to 4 (node, weight) pairs per corner
   int ref[8][4];
@@ -461,13 +462,17 @@ void mg_free(chns_mg* g) {
       dfree(L.v64[k]);
       dfree(L.v32[k]);
     }
-    dfree(L.phi64);
-    dfree(L.phi32);
-    dfree(L.dinv64);
-    dfree(L.dinv32);
+    for (int o = 0; o < kMgOps; ++o) {
+      dfree(L.op[o].phi64);
+      dfree(L.op[o].phi32);
+      dfree(L.op[o].dinv64);
+      dfree(L.op[o].dinv32);
+    }
   }
-  dfree(g->cinv64);
-  dfree(g->cinv32);
+  for (int o = 0; o < kMgOps; ++o) {
+    dfree(g->ops[o].cinv64);
+    dfree(g->ops[o].cinv32);
+  }
   dfree(g->cwork64);
   dfree(g->slots);
   if (g->h_slots) cudaFreeHost(g->h_slots);
@@ -508,6 +513,7 @@ chns_status mg_create(const chns_mesh* fine, const chns_mg_params* prm, cudaStre
   g->lv[0].n = fine->d.n_nodes;
   int maxl = fine->max_level;
   while (maxl > p.coarsest_level && st == CHNS_OK) {
+    CHNS_CHECK((int)g->lv.size() < kMgMaxLevels, CHNS_EINVAL, "chns_mg_create: too many levels");
     st = coarsen(a, l, ca, cl);
     if (st != CHNS_OK) break;
     chns_mesh* cm = new (std::nothrow) chns_mesh();
@@ -542,43 +548,41 @@ chns_status mg_create(const chns_mesh* fine, const chns_mg_params* prm, cudaStre
     l.swap(cl);
     maxl = cm->max_level;
   }
-  if (st == CHNS_OK) {
-    const int64_t nc = g->lv.back().n;
-    if (nc > kMgMaxCoarse) {
-      set_error("chns_mg_create: the coarsest level has more than 1024 nodes (lower coarsest_level)");
-      st = CHNS_EINVAL;
-    }
+  if (st == CHNS_OK && g->lv.back().n > kMgMaxCoarse) {
+    set_error("chns_mg_create: the coarsest level has more than 1024 nodes (lower coarsest_level)");
+    st = CHNS_EINVAL;
   }
   // vectors: level 0 needs the apply output and the Chebyshev direction; coarser levels also
-  // their right-hand side and correction
+  // their right-hand side and correction; per operator the inverse diagonal (and, Poisson, the
+  // injected coefficient on the coarser levels)
   auto alloc_level = [&](MgLevel& L, bool fine_level) -> chns_status {
     for (int k = fine_level ? 2 : 0; k < kMgVecs; ++k) {
       CHNS_CUDA(cudaMalloc(&L.v64[k], L.n * sizeof(double)));
       CHNS_CUDA(cudaMalloc(&L.v32[k], L.n * sizeof(float)));
     }
-    if (!fine_level) {
-      CHNS_CUDA(cudaMalloc(&L.phi64, L.n * sizeof(double)));
-      CHNS_CUDA(cudaMalloc(&L.phi32, L.n * sizeof(float)));
+    for (int o = 0; o < kMgOps; ++o) {
+      if (!fine_level && o == kMgPoisson) {
+        CHNS_CUDA(cudaMalloc(&L.op[o].phi64, L.n * sizeof(double)));
+        CHNS_CUDA(cudaMalloc(&L.op[o].phi32, L.n * sizeof(float)));
+      }
+      CHNS_CUDA(cudaMalloc(&L.op[o].dinv64, L.n * sizeof(double)));
+      CHNS_CUDA(cudaMalloc(&L.op[o].dinv32, L.n * sizeof(float)));
     }
-    CHNS_CUDA(cudaMalloc(&L.dinv64, L.n * sizeof(double)));
-    CHNS_CUDA(cudaMalloc(&L.dinv32, L.n * sizeof(float)));
     return CHNS_OK;
   };
   for (size_t k = 0; k < g->lv.size() && st == CHNS_OK; ++k) st = alloc_level(g->lv[k], k == 0);
   if (st == CHNS_OK) {
     const int64_t nc = g->lv.back().n;
-    if (cudaMalloc(&g->cinv64, nc * nc * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&g->cinv32, nc * nc * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&g->cwork64, nc * nc * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&g->slots, 2 * kMgMaxLevels * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&g->h_slots, 2 * kMgMaxLevels * sizeof(double)) != cudaSuccess) {
+    bool ok = cudaMalloc(&g->cwork64, nc * nc * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&g->slots, kMgMaxLevels * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost(&g->h_slots, kMgMaxLevels * sizeof(double)) == cudaSuccess;
+    for (int o = 0; o < kMgOps && ok; ++o)
+      ok = cudaMalloc(&g->ops[o].cinv64, nc * nc * sizeof(double)) == cudaSuccess &&
+           cudaMalloc(&g->ops[o].cinv32, nc * nc * sizeof(float)) == cudaSuccess;
+    if (!ok) {
       set_error("chns_mg_create: device allocation failed");
       st = CHNS_ENOMEM;
     }
-  }
-  if (st == CHNS_OK && (int)g->lv.size() > kMgMaxLevels) {
-    set_error("chns_mg_create: too many levels");
-    st = CHNS_EINVAL;
   }
   if (st != CHNS_OK) {
     mg_free(g);
@@ -590,76 +594,91 @@ chns_status mg_create(const chns_mesh* fine, const chns_mg_params* prm, cudaStre
 
 // ---------------------------------------------------------------- setup and cycle
 template <class T>
-static T* lv_phi(MgLevel& L);
-template <>
-double* lv_phi<double>(MgLevel& L) { return L.phi64; }
-template <>
-float* lv_phi<float>(MgLevel& L) { return L.phi32; }
-template <class T>
-static T* lv_dinv(MgLevel& L);
-template <>
-double* lv_dinv<double>(MgLevel& L) { return L.dinv64; }
-template <>
-float* lv_dinv<float>(MgLevel& L) { return L.dinv32; }
-template <class T>
-static T* lv_vec(MgLevel& L, int k);
-template <>
-double* lv_vec<double>(MgLevel& L, int k) { return L.v64[k]; }
-template <>
-float* lv_vec<float>(MgLevel& L, int k) { return L.v32[k]; }
-
+constexpr int pix() {
+  return sizeof(T) == sizeof(double) ? 0 : 1;
+}
 template <class T>
 constexpr chns_precision prec_of() {
   return sizeof(T) == sizeof(double) ? CHNS_FP64 : CHNS_FP32;
 }
+template <class T>
+static T* pick(double* a, float* b) {
+  if constexpr (sizeof(T) == sizeof(double))
+    return a;
+  else
+    return b;
+}
+template <class T>
+static T* lv_vec(MgLevel& L, int k) { return pick<T>(L.v64[k], L.v32[k]); }
+template <class T>
+static T* lv_dinv(MgLevel& L, int op) { return pick<T>(L.op[op].dinv64, L.op[op].dinv32); }
 
-// coefficient array of level l in precision T (level 0: the caller's)
+// Poisson coefficient array of level l in precision T (level 0: the caller's)
 template <class T>
 static const T* level_phi(chns_mg* g, int l) {
-  if (l == 0) return static_cast<const T*>(sizeof(T) == sizeof(double) ? g->phi0_64 : g->phi0_32);
-  return lv_phi<T>(g->lv[l]);
+  if (l == 0)
+    return static_cast<const T*>(sizeof(T) == sizeof(double) ? g->ops[kMgPoisson].phi0_64
+                                                             : g->ops[kMgPoisson].phi0_32);
+  return pick<T>(g->lv[l].op[kMgPoisson].phi64, g->lv[l].op[kMgPoisson].phi32);
 }
 
 template <class T>
-static chns_status level_apply(chns_mg* g, int l, const T* x, T* y, cudaStream_t s) {
+static chns_status level_apply(chns_mg* g, int op, int l, const T* x, T* y, cudaStream_t s) {
+  MgLevel& L = g->lv[l];
+  if (op == kMgShifted)  // the patch kernel gathers one coefficient field, unused here
+    return apply_shift(L.mesh, &g->phys, lv_dinv<T>(L, op), g->ops[op].sa, g->ops[op].sb, x, y,
+                       prec_of<T>(), s);
   chns_coef c{};
   c.phi_tilde = level_phi<T>(g, l);
-  return apply_op(g->lv[l].mesh, CHNS_OP_POISSON, &g->phys, &c, x, y, prec_of<T>(), s);
+  return apply_op(L.mesh, CHNS_OP_POISSON, &g->phys, &c, x, y, prec_of<T>(), s);
 }
 
 template <class T>
-chns_status mg_setup_T(chns_mg* g, const T* phi0, cudaStream_t s) {
-  const int NL = (int)g->lv.size();
-  g->ready[sizeof(T) == sizeof(double) ? 0 : 1] = false;
-  if (sizeof(T) == sizeof(double))
-    g->phi0_64 = phi0;
-  else
-    g->phi0_32 = phi0;
-  // injected coefficients
-  for (int l = 1; l < NL; ++l) {
-    note_launch();
-    k_inject<T><<<grid_for(g->lv[l].n), kMgThreads, 0, s>>>(
-        g->lv[l - 1].inj, level_phi<T>(g, l - 1), lv_phi<T>(g->lv[l]), g->lv[l].n);
-  }
-  // diagonals
-  for (int l = 0; l < NL; ++l) {
-    MgLevel& L = g->lv[l];
+static chns_status level_diag(chns_mg* g, int op, int l, cudaStream_t s) {
+  MgLevel& L = g->lv[l];
+  T* d = lv_dinv<T>(L, op);
+  if (op == kMgShifted) {
+    // diag_shift gathers (and ignores) a coefficient field: the apply-output vector serves
+    chns_status st = diag_shift(L.mesh, &g->phys, lv_vec<T>(L, 2), g->ops[op].sa, g->ops[op].sb,
+                                d, prec_of<T>(), s);
+    if (st != CHNS_OK) return st;
+  } else {
     chns_coef c{};
     c.phi_tilde = level_phi<T>(g, l);
-    chns_status st = diag_op(L.mesh, CHNS_OP_POISSON, &g->phys, &c, lv_dinv<T>(L), prec_of<T>(), s);
+    chns_status st = diag_op(L.mesh, CHNS_OP_POISSON, &g->phys, &c, d, prec_of<T>(), s);
     if (st != CHNS_OK) return st;
-    note_launch();
-    k_invert_diag<T, T><<<grid_for(L.n), kMgThreads, 0, s>>>(lv_dinv<T>(L), lv_dinv<T>(L), L.n);
+  }
+  note_launch();
+  k_invert_diag<T, T><<<grid_for(L.n), kMgThreads, 0, s>>>(d, d, L.n);
+  return CHNS_OK;
+}
+
+template <class T>
+chns_status mg_setup_T(chns_mg* g, int op, cudaStream_t s) {
+  const int NL = (int)g->lv.size();
+  MgOpState& O = g->ops[op];
+  O.ready[pix<T>()] = false;
+  // injected coefficients (Poisson)
+  if (op == kMgPoisson)
+    for (int l = 1; l < NL; ++l) {
+      note_launch();
+      k_inject<T><<<grid_for(g->lv[l].n), kMgThreads, 0, s>>>(
+          g->lv[l - 1].inj, level_phi<T>(g, l - 1),
+          pick<T>(g->lv[l].op[op].phi64, g->lv[l].op[op].phi32), g->lv[l].n);
+    }
+  for (int l = 0; l < NL; ++l) {
+    chns_status st = level_diag<T>(g, op, l, s);
+    if (st != CHNS_OK) return st;
   }
   // largest eigenvalue of D^-1 A per level (power iteration, normalised on the device)
   const int NS = NL - 1;  // the coarsest level is solved exactly
-  double* slot = g->slots + (sizeof(T) == sizeof(double) ? 0 : kMgMaxLevels);
+  double* slot = g->slots;
   if (NS > 0) {
     for (int l = 0; l < NS; ++l) {
       MgLevel& L = g->lv[l];
-      T* v = lv_vec<T>(L, 3);
       note_launch();
-      k_power_start<T><<<grid_for(L.n), kMgThreads, 0, s>>>(lv_dinv<T>(L), v, L.n);
+      k_power_start<T><<<grid_for(L.n), kMgThreads, 0, s>>>(lv_dinv<T>(L, op), lv_vec<T>(L, 3),
+                                                            L.n);
     }
     for (int it = 0; it <= g->prm.power_its; ++it) {
       CHNS_CUDA(cudaMemsetAsync(slot, 0, NS * sizeof(double), s));
@@ -668,10 +687,10 @@ chns_status mg_setup_T(chns_mg* g, const T* phi0, cudaStream_t s) {
         T* v = lv_vec<T>(L, 3);
         T* w = lv_vec<T>(L, 2);
         if (it > 0) {
-          chns_status st = level_apply<T>(g, l, v, w, s);
+          chns_status st = level_apply<T>(g, op, l, v, w, s);
           if (st != CHNS_OK) return st;
           note_launch();
-          k_mul<T><<<grid_for(L.n), kMgThreads, 0, s>>>(lv_dinv<T>(L), w, v, L.n);
+          k_mul<T><<<grid_for(L.n), kMgThreads, 0, s>>>(lv_dinv<T>(L, op), w, v, L.n);
         }
         note_launch();
         k_norm2<T><<<grid_for(L.n), kMgThreads, 0, s>>>(v, L.n, slot + l);
@@ -681,77 +700,83 @@ chns_status mg_setup_T(chns_mg* g, const T* phi0, cudaStream_t s) {
     }
     CHNS_CUDA(cudaMemcpyAsync(g->h_slots, slot, NS * sizeof(double), cudaMemcpyDeviceToHost, s));
   }
-  // coarsest: dense inverse of A + 1 1^T / n in FP64 (from the FP64 or FP32 coefficients)
+  // coarsest: dense inverse in FP64 (Poisson: of A + 1 1^T / n, the mean-zero solution)
   {
     MgLevel& C = g->lv.back();
     const int n = (int)C.n;
     // the FP32 setup works in its own FP64 matrix, so that the FP64 inverse stays valid
-    double* Aw = sizeof(T) == sizeof(double) ? g->cinv64 : g->cwork64;
+    double* Aw = sizeof(T) == sizeof(double) ? O.cinv64 : g->cwork64;
     CHNS_CUDA(cudaMemsetAsync(Aw, 0, (size_t)n * n * sizeof(double), s));
-    const double* phic = nullptr;
-    if (sizeof(T) == sizeof(double)) {
-      phic = reinterpret_cast<const double*>(level_phi<T>(g, NL - 1));
-    } else {
-      // FP64 copy of the FP32 coefficients in the coarsest level's FP64 scratch
-      double* tmp = NL == 1 ? C.v64[3] : C.v64[0];
-      note_launch();
-      k_convert<T, double><<<grid_for(n), kMgThreads, 0, s>>>(level_phi<T>(g, NL - 1), tmp, n);
-      phic = tmp;
-    }
+    DevParams p = make_dev_params(g->phys);
     CoefArgs<double> cf{};
-    cf.phi = phic;
     cf.phi_shift = 0.0f;
-    const DevParams p = make_dev_params(g->phys);
+    const unsigned nb = (unsigned)((C.mesh->d.n_elem + 127) / 128);
+    if (op == kMgPoisson) {
+      const double* phic = nullptr;
+      if (sizeof(T) == sizeof(double)) {
+        phic = reinterpret_cast<const double*>(level_phi<T>(g, NL - 1));
+      } else {
+        // FP64 copy of the FP32 coefficients in the coarsest level's FP64 apply-output vector
+        double* tmp = C.v64[2];
+        note_launch();
+        k_convert<T, double><<<grid_for(n), kMgThreads, 0, s>>>(level_phi<T>(g, NL - 1), tmp, n);
+        phic = tmp;
+      }
+      cf.phi = phic;
+      note_launch();
+      k_dense_assemble<PoissonK<double, double>><<<nb, 128, 0, s>>>(C.mesh->d, p, cf, Aw, n);
+    } else {
+      p.d.sa = O.sa;
+      p.d.sb = O.sb;
+      cf.phi = C.v64[2];  // gathered, unused
+      note_launch();
+      k_dense_assemble<ShiftK<double, double>><<<nb, 128, 0, s>>>(C.mesh->d, p, cf, Aw, n);
+    }
     note_launch();
-    k_dense_assemble<<<(unsigned)((C.mesh->d.n_elem + 127) / 128), 128, 0, s>>>(C.mesh->d, p, cf,
-                                                                               Aw, n);
-    note_launch();
-    k_gauss_jordan<<<1, 1024, 0, s>>>(Aw, n, 1.0 / n);
+    k_gauss_jordan<<<1, 1024, 0, s>>>(Aw, n, op == kMgPoisson ? 1.0 / n : 0.0);
     if (sizeof(T) == sizeof(float)) {
       note_launch();
       k_convert<double, float><<<grid_for((int64_t)n * n), kMgThreads, 0, s>>>(
-          Aw, g->cinv32, (int64_t)n * n);
+          Aw, O.cinv32, (int64_t)n * n);
     }
   }
   CHNS_CUDA(cudaGetLastError());
   CHNS_CUDA(cudaStreamSynchronize(s));
-  const int pi = sizeof(T) == sizeof(double) ? 0 : 1;
   for (int l = 0; l < NS; ++l) {
     const double lam = std::sqrt(g->h_slots[l]);
     CHNS_CHECK(std::isfinite(lam) && lam > 0.0, CHNS_EBREAKDOWN,
                "multigrid: power iteration failed");
-    MgLevel& L = g->lv[l];
-    L.lmax[pi] = g->prm.lmax_factor * lam;
-    L.lmin[pi] = L.lmax[pi] / g->prm.smooth_range;
+    MgOpLevel& Lo = g->lv[l].op[op];
+    Lo.lmax[pix<T>()] = g->prm.lmax_factor * lam;
+    Lo.lmin[pix<T>()] = Lo.lmax[pix<T>()] / g->prm.smooth_range;
   }
-  g->ready[pi] = true;
+  O.ready[pix<T>()] = true;
   return CHNS_OK;
 }
 
 // z = B r on level l (r and z of the level's size; level 0 uses the caller's vectors)
 template <class T>
-static chns_status vcycle(chns_mg* g, int l, const T* r, T* z, cudaStream_t s) {
+static chns_status vcycle(chns_mg* g, int op, int l, const T* r, T* z, cudaStream_t s) {
   const int NL = (int)g->lv.size();
   MgLevel& L = g->lv[l];
   const int64_t n = L.n;
   const unsigned vg = grid_for(n);
   if (l == NL - 1) {
-    const T* C = sizeof(T) == sizeof(double) ? reinterpret_cast<const T*>(g->cinv64)
-                                             : reinterpret_cast<const T*>(g->cinv32);
+    const T* C = pick<T>(g->ops[op].cinv64, g->ops[op].cinv32);
     note_launch();
     k_dense_mv<T><<<(unsigned)((n + 7) / 8), 256, 0, s>>>(C, r, z, (int)n);
     return CHNS_OK;
   }
-  const int pi = sizeof(T) == sizeof(double) ? 0 : 1;
-  const double lmax = L.lmax[pi], lmin = L.lmin[pi];
+  const MgOpLevel& Lo = L.op[op];
+  const double lmax = Lo.lmax[pix<T>()], lmin = Lo.lmin[pix<T>()];
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
-  const T* dinv = lv_dinv<T>(L);
+  const T* dinv = lv_dinv<T>(L, op);
   T* w = lv_vec<T>(L, 2);
   T* d = lv_vec<T>(L, 3);
   chns_status st;
   auto smooth = [&](bool guess) -> chns_status {
     if (guess) {
-      st = level_apply<T>(g, l, z, w, s);
+      st = level_apply<T>(g, op, l, z, w, s);
       if (st != CHNS_OK) return st;
       note_launch();
       k_cheb_first<T, true><<<vg, kMgThreads, 0, s>>>(dinv, r, w, z, d, (T)(1.0 / theta), n);
@@ -762,7 +787,7 @@ static chns_status vcycle(chns_mg* g, int l, const T* r, T* z, cudaStream_t s) {
     double rho_old = 1.0 / sigma;
     for (int i = 1; i < g->prm.degree; ++i) {
       const double rho = 1.0 / (2.0 * sigma - rho_old);
-      st = level_apply<T>(g, l, z, w, s);
+      st = level_apply<T>(g, op, l, z, w, s);
       if (st != CHNS_OK) return st;
       note_launch();
       k_cheb_next<T><<<vg, kMgThreads, 0, s>>>(dinv, r, w, z, d, (T)(rho * rho_old),
@@ -773,14 +798,14 @@ static chns_status vcycle(chns_mg* g, int l, const T* r, T* z, cudaStream_t s) {
   };
   if ((st = smooth(false)) != CHNS_OK) return st;
   // coarse correction: r_c = R (r - A z), z += P z_c
-  if ((st = level_apply<T>(g, l, z, w, s)) != CHNS_OK) return st;
+  if ((st = level_apply<T>(g, op, l, z, w, s)) != CHNS_OK) return st;
   MgLevel& Cl = g->lv[l + 1];
   T* rc = lv_vec<T>(Cl, 0);
   T* zc = lv_vec<T>(Cl, 1);
   note_launch();
   k_csr_gather<T, false, true><<<grid_for(Cl.n), kMgThreads, 0, s>>>(L.r_ptr, L.r_col, L.r_w, r, w,
                                                                       rc, Cl.n);
-  if ((st = vcycle<T>(g, l + 1, rc, zc, s)) != CHNS_OK) return st;
+  if ((st = vcycle<T>(g, op, l + 1, rc, zc, s)) != CHNS_OK) return st;
   note_launch();
   k_csr_gather<T, true, false><<<vg, kMgThreads, 0, s>>>(L.p_ptr, L.p_col, L.p_w, zc, nullptr, z,
                                                          n);
@@ -793,20 +818,43 @@ chns_status mg_setup(chns_mg* g, const chns_params* prm, const void* phi0, chns_
                      cudaStream_t s) {
   CHNS_CHECK(g && prm && phi0, CHNS_EINVAL, "multigrid setup: null argument");
   g->phys = *prm;
-  if (prec == CHNS_FP64) return mg_setup_T<double>(g, static_cast<const double*>(phi0), s);
-  if (prec == CHNS_FP32) return mg_setup_T<float>(g, static_cast<const float*>(phi0), s);
+  MgOpState& O = g->ops[kMgPoisson];
+  if (prec == CHNS_FP64) {
+    O.phi0_64 = phi0;
+    return mg_setup_T<double>(g, kMgPoisson, s);
+  }
+  if (prec == CHNS_FP32) {
+    O.phi0_32 = phi0;
+    return mg_setup_T<float>(g, kMgPoisson, s);
+  }
   set_error("multigrid setup: precision must be CHNS_FP64 or CHNS_FP32");
   return CHNS_EINVAL;
 }
 
-template <class T>
-chns_status mg_vcycle(chns_mg* g, const T* r, T* z, cudaStream_t s) {
-  const int pi = sizeof(T) == sizeof(double) ? 0 : 1;
-  CHNS_CHECK(g->ready[pi], CHNS_EINVAL, "multigrid: V-cycle before setup in this precision");
-  return vcycle<T>(g, 0, r, z, s);
+chns_status mg_setup_shifted(chns_mg* g, const chns_params* prm, double sa, double sb,
+                             chns_precision prec, cudaStream_t s) {
+  CHNS_CHECK(g && prm && sa > 0.0 && sb >= 0.0, CHNS_EINVAL,
+             "multigrid setup (shifted): null argument or sa <= 0 or sb < 0");
+  CHNS_CHECK(prec == CHNS_FP64 || prec == CHNS_FP32, CHNS_EINVAL,
+             "multigrid setup: precision must be CHNS_FP64 or CHNS_FP32");
+  MgOpState& O = g->ops[kMgShifted];
+  const int pi = prec == CHNS_FP64 ? 0 : 1;
+  if (O.ready[pi] && O.sa == sa && O.sb == sb) return CHNS_OK;  // constant coefficients
+  if (O.sa != sa || O.sb != sb) O.ready[0] = O.ready[1] = false;
+  O.sa = sa;
+  O.sb = sb;
+  g->phys = *prm;
+  return prec == CHNS_FP64 ? mg_setup_T<double>(g, kMgShifted, s) : mg_setup_T<float>(g, kMgShifted, s);
 }
-template chns_status mg_vcycle<double>(chns_mg*, const double*, double*, cudaStream_t);
-template chns_status mg_vcycle<float>(chns_mg*, const float*, float*, cudaStream_t);
+
+template <class T>
+chns_status mg_vcycle(chns_mg* g, int op, const T* r, T* z, cudaStream_t s) {
+  CHNS_CHECK(op >= 0 && op < kMgOps && g->ops[op].ready[pix<T>()], CHNS_EINVAL,
+             "multigrid: V-cycle before setup of this operator in this precision");
+  return vcycle<T>(g, op, 0, r, z, s);
+}
+template chns_status mg_vcycle<double>(chns_mg*, int, const double*, double*, cudaStream_t);
+template chns_status mg_vcycle<float>(chns_mg*, int, const float*, float*, cudaStream_t);
 
 }  // namespace chns
 
@@ -836,23 +884,29 @@ extern "C" chns_status chns_mg_setup(chns_mg* g, const chns_params* prm, const v
   return mg_setup(g, prm, phi_tilde, prec, as_stream(stream));
 }
 
-extern "C" chns_status chns_mg_lambda(const chns_mg* g, chns_precision prec, double* lmax) {
-  CHNS_CHECK(g && lmax && (prec == CHNS_FP64 || prec == CHNS_FP32), CHNS_EINVAL,
-             "chns_mg_lambda: bad argument");
+extern "C" chns_status chns_mg_setup_shifted(chns_mg* g, const chns_params* prm, double sa,
+                                             double sb, chns_precision prec, void* stream) {
+  return mg_setup_shifted(g, prm, sa, sb, prec, as_stream(stream));
+}
+
+extern "C" chns_status chns_mg_lambda(const chns_mg* g, int32_t op, chns_precision prec,
+                                      double* lmax) {
+  CHNS_CHECK(g && lmax && op >= 0 && op < kMgOps && (prec == CHNS_FP64 || prec == CHNS_FP32),
+             CHNS_EINVAL, "chns_mg_lambda: bad argument");
   const int pi = prec == CHNS_FP64 ? 0 : 1;
-  CHNS_CHECK(g->ready[pi], CHNS_EINVAL, "chns_mg_lambda: no setup in this precision");
-  for (size_t l = 0; l < g->lv.size(); ++l) lmax[l] = g->lv[l].lmax[pi];
+  CHNS_CHECK(g->ops[op].ready[pi], CHNS_EINVAL, "chns_mg_lambda: no setup in this precision");
+  for (size_t l = 0; l < g->lv.size(); ++l) lmax[l] = g->lv[l].op[op].lmax[pi];
   return CHNS_OK;
 }
 
-extern "C" chns_status chns_mg_vcycle(chns_mg* g, const void* r, void* z, chns_precision prec,
-                                      void* stream) {
+extern "C" chns_status chns_mg_vcycle(chns_mg* g, int32_t op, const void* r, void* z,
+                                      chns_precision prec, void* stream) {
   CHNS_CHECK(g && r && z && r != z, CHNS_EINVAL, "chns_mg_vcycle: bad argument");
   if (prec == CHNS_FP64)
-    return mg_vcycle<double>(g, static_cast<const double*>(r), static_cast<double*>(z),
+    return mg_vcycle<double>(g, op, static_cast<const double*>(r), static_cast<double*>(z),
                              as_stream(stream));
   if (prec == CHNS_FP32)
-    return mg_vcycle<float>(g, static_cast<const float*>(r), static_cast<float*>(z),
+    return mg_vcycle<float>(g, op, static_cast<const float*>(r), static_cast<float*>(z),
                             as_stream(stream));
   set_error("chns_mg_vcycle: precision must be CHNS_FP64 or CHNS_FP32");
   return CHNS_EINVAL;
@@ -885,9 +939,11 @@ extern "C" chns_status chns_mg_restrict(const chns_mg* g, int32_t level, const d
 
 extern "C" chns_status chns_mg_coefficient(const chns_mg* g, int32_t level, double* phi,
                                            void* stream) {
-  CHNS_CHECK(g && phi && level >= 0 && level < (int)g->lv.size() && g->ready[0], CHNS_EINVAL,
-             "chns_mg_coefficient: bad argument or no FP64 setup");
-  const double* src = level == 0 ? static_cast<const double*>(g->phi0_64) : g->lv[level].phi64;
+  CHNS_CHECK(g && phi && level >= 0 && level < (int)g->lv.size() &&
+                 g->ops[kMgPoisson].ready[0],
+             CHNS_EINVAL, "chns_mg_coefficient: bad argument or no FP64 Poisson setup");
+  const double* src = level == 0 ? static_cast<const double*>(g->ops[kMgPoisson].phi0_64)
+                                 : g->lv[level].op[kMgPoisson].phi64;
   CHNS_CUDA(cudaMemcpyAsync(phi, src, g->lv[level].n * sizeof(double), cudaMemcpyDeviceToDevice,
                             as_stream(stream)));
   return CHNS_OK;

@@ -9,6 +9,21 @@ namespace chns {
 
 constexpr int kMgVecs = 4;        // per level: right-hand side, correction, apply output, direction
 constexpr int kMgMaxLevels = 32;
+// level operators a hierarchy can be set up for (each keeps its own diagonals, intervals and
+// coarsest inverse, so that both can be live at once)
+constexpr int kMgPoisson = 0;     // (grad q, (1/rho(phi~*)) grad p), pure Neumann
+constexpr int kMgShifted = 1;     // sa (q, p) + sb (grad q, grad p), constant sa > 0, sb >= 0
+constexpr int kMgOps = 2;
+
+// per level and operator: coefficients (Poisson), inverse diagonal and Chebyshev interval, per
+// precision (index 0 FP64, 1 FP32)
+struct MgOpLevel {
+  double* phi64 = nullptr;
+  float* phi32 = nullptr;
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+  double lmax[2] = {0.0, 0.0}, lmin[2] = {0.0, 0.0};
+};
 
 struct MgLevel {
   chns_mesh* mesh = nullptr;  // level 0: the caller's mesh (not owned)
@@ -24,14 +39,20 @@ struct MgLevel {
   float* r_w = nullptr;
   int32_t* inj = nullptr;
   int64_t p_nnz = 0;
-  // vectors [kMgVecs] and coefficients per precision (level 0 holds only vectors 2 and 3)
+  // work vectors [kMgVecs] per precision (level 0 holds only vectors 2 and 3)
   double* v64[kMgVecs] = {};
   float* v32[kMgVecs] = {};
-  double* phi64 = nullptr;
-  float* phi32 = nullptr;
-  double* dinv64 = nullptr;
-  float* dinv32 = nullptr;
-  double lmax[2] = {0.0, 0.0}, lmin[2] = {0.0, 0.0};  // Chebyshev interval [FP64, FP32]
+  MgOpLevel op[kMgOps];
+};
+
+// state of one level operator over the hierarchy
+struct MgOpState {
+  const void* phi0_64 = nullptr;  // Poisson: fine-level coefficients of the last setup
+  const void* phi0_32 = nullptr;
+  double sa = 0.0, sb = 0.0;      // shifted operator
+  double* cinv64 = nullptr;       // dense inverse of the coarsest operator
+  float* cinv32 = nullptr;
+  bool ready[2] = {false, false};  // set up in FP64 / FP32
 };
 
 }  // namespace chns
@@ -40,14 +61,10 @@ struct chns_mg {
   std::vector<chns::MgLevel> lv;
   chns_mg_params prm;
   chns_params phys{};
-  const void* phi0_64 = nullptr;  // fine-level coefficients of the last setup (caller's arrays)
-  const void* phi0_32 = nullptr;
-  double* cinv64 = nullptr;   // dense inverse of the coarsest operator (+ 1 1^T / n)
-  float* cinv32 = nullptr;
-  double* cwork64 = nullptr;  // FP64 work matrix of the FP32 setup
-  double* slots = nullptr;    // power-iteration norms [2][kMgMaxLevels]
+  chns::MgOpState ops[chns::kMgOps];
+  double* cwork64 = nullptr;  // FP64 work matrix of the FP32 setups
+  double* slots = nullptr;    // power-iteration norms [kMgMaxLevels]
   double* h_slots = nullptr;  // pinned host copy
-  bool ready[2] = {false, false};  // set up in FP64 / FP32
 };
 
 namespace chns {
@@ -60,8 +77,12 @@ void mg_free(chns_mg* g);
 // intervals, coarsest inverse. Synchronises the stream once.
 chns_status mg_setup(chns_mg* g, const chns_params* prm, const void* phi0, chns_precision prec,
                      cudaStream_t s);
-// z = B r, one V-cycle (kernels only: no allocation, no host synchronisation)
+// Level operators sa M + sb K (constant coefficients, sa > 0); a repeated setup with the same
+// sa, sb and precision returns at once.
+chns_status mg_setup_shifted(chns_mg* g, const chns_params* prm, double sa, double sb,
+                             chns_precision prec, cudaStream_t s);
+// z = B r, one V-cycle of operator op (kernels only: no allocation, no host synchronisation)
 template <class T>
-chns_status mg_vcycle(chns_mg* g, const T* r, T* z, cudaStream_t s);
+chns_status mg_vcycle(chns_mg* g, int op, const T* r, T* z, cudaStream_t s);
 
 }  // namespace chns

@@ -149,3 +149,64 @@ def test_multigrid_in_time_step_matches_jacobi():
         assert max(ib) * 4 < min(ia)
     finally:
         capi.chns_mg_destroy(mg)
+
+
+def _h_shift(prm):
+    k = 0.5 / (prm["Pe"] * prm["Cn"])
+    return 1.0 / np.sqrt(prm["dt"]), prm["Cn"] * np.sqrt(k)
+
+
+def test_shifted_vcycle_matches_oracle_beside_the_poisson_setup(pair):
+    """The hierarchy keeps the Poisson and the shifted (sa M + sb K) setups side by side: after
+    both setups each V-cycle matches its oracle cycle."""
+    sa, sb = _h_shift(PRM)
+    prm = capi.make_params(PRM)
+    phi_d = dev(pair.phi)
+    capi.chns_mg_setup(pair.mg, prm, phi_d, capi.FP64)
+    capi.chns_mg_setup_shifted(pair.mg, prm, sa, sb, capi.FP64)
+    Bp = omg.VCycle(pair.oms, PRM, pair.phi, degree=pair.degree)
+    Bs = omg.VCycle(pair.oms, PRM, shift=(sa, sb), degree=pair.degree)
+    lam = capi.chns_mg_lambda(pair.mg, len(pair.oms), capi.FP64, op=capi.MG_SHIFTED)
+    for l in range(len(pair.oms) - 1):
+        assert abs(lam[l] - Bs.lmax[l]) <= 1e-10 * Bs.lmax[l]
+    rng = np.random.default_rng(12)
+    r = rng.standard_normal(pair.om.n_nodes)
+    z = torch.zeros_like(dev(r))
+    capi.chns_mg_vcycle(pair.mg, dev(r), z, capi.FP64, op=capi.MG_SHIFTED)
+    assert relerr(z.cpu().numpy(), Bs(r)) < 1e-10
+    r -= r.mean()
+    capi.chns_mg_vcycle(pair.mg, dev(r), z, capi.FP64, op=capi.MG_POISSON)
+    assert relerr(z.cpu().numpy(), Bp(r)) < 1e-10
+
+
+@pytest.mark.parametrize("inner", [capi.FP64, capi.FP32])
+def test_schur_with_multigrid_inner_solves(inner):
+    """The CH Newton system with the Schur-complement preconditioner whose H^-1 is one V-cycle:
+    the solution agrees with the oracle's direct solve (FP64) or reaches the FP64 residual
+    (mixed precision), in no more GMRES iterations than with 20 inner CG iterations."""
+    from gpu_common import fields, oracle_operator
+    stiff = dict(PRM, Cn=0.02, Pe=1.0 / (3 * 0.02 ** 2), dt=2e-2)
+    om, gm = meshes("drop_l3_5")
+    f = fields(om.n_nodes, 93)
+    f["phi"] = np.tanh(f["phi"])
+    A = oracle_operator(om, capi.OP_CH, stiff, f["phi"], f["u"], f["mu"])
+    b = f["x"][:2].ravel().copy()
+    coef = capi.make_coef(dev(f["phi"]), [dev(f["u"][i]) for i in range(3)], dev(f["mu"]))
+    mg = capi.chns_mg_create(gm.handle)
+    try:
+        rtol = 1e-12 if inner == capi.FP64 else 1e-10
+        its = {}
+        for name, hier in (("cg", None), ("mg", mg)):
+            x = torch.zeros(2 * gm.n_nodes, dtype=torch.float64, device="cuda")
+            s = capi.make_solver(capi.KSP_GMRES, capi.PC_SCHUR, rtol, 2000, 30, inner, 1e-3, 40,
+                                 mg=hier)
+            st = capi.chns_krylov_solve(gm.handle, capi.OP_CH, capi.make_params(stiff), coef,
+                                        dev(b), x, s)
+            its[name] = st.iterations
+            xh = x.cpu().numpy()
+            assert np.linalg.norm(b - A @ xh) <= 1.05 * rtol * np.linalg.norm(b)
+            if inner == capi.FP64:
+                assert relerr(xh, solvers.direct(A, b)) < 1e-8
+        assert its["mg"] <= its["cg"], its
+    finally:
+        capi.chns_mg_destroy(mg)

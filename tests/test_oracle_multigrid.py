@@ -238,3 +238,32 @@ def test_fcg_with_vcycle_solves_and_beats_jacobi():
     assert rel <= 1e-10
     assert np.linalg.norm(x - xj) <= 1e-7 * np.linalg.norm(xj)
     assert it * 4 < itj
+
+
+def test_shifted_vcycle_preconditions_h_of_the_schur_preconditioner():
+    """For H = M/sqrt(dt) + Cn sqrt(k) K (the inner operator of solvers.ch_schur_precond) the
+    cycle is symmetric and CG with it converges in a few iterations, far fewer than Jacobi."""
+    from oracle import solvers
+    a, l = TREES["drop"]
+    ms = mg.hierarchy(a, l, (1.0, 1.0, 1.0), coarsest_level=2)
+    Cn, dt = 0.02, 1e-3
+    Pe = 1.0 / (3 * Cn ** 2)
+    k = 0.5 / (Pe * Cn)
+    sa, sb = 1.0 / np.sqrt(dt), Cn * np.sqrt(k)
+    B = mg.VCycle(ms, PRM, shift=(sa, sb))
+    m = ms[0]
+    el = fem.Elem(m)
+    ones = np.ones((m.n_elem, 8))
+    H = (fem.mass(el, ones) / np.sqrt(dt) + Cn * np.sqrt(k) * fem.stiffness(el, ones)).tocsr()
+    assert abs(B.A[0] - H).max() < 1e-14 * abs(H).max()
+    rng = np.random.default_rng(3)
+    r1, r2 = rng.standard_normal(m.n_nodes), rng.standard_normal(m.n_nodes)
+    assert abs(r1 @ B(r2) - r2 @ B(r1)) < 1e-10 * abs(r1 @ B(r2))
+    # exact on the coarsest level (no null space: no 1 1^T term)
+    Bc = mg.VCycle(ms[-1:], PRM, shift=(sa, sb))
+    rc = rng.standard_normal(ms[-1].n_nodes)
+    assert np.linalg.norm(Bc.A[0] @ Bc(rc) - rc) < 1e-10 * np.linalg.norm(rc)
+    b = rng.standard_normal(m.n_nodes)
+    x, it, rel = mg.fcg_mg(H, b - b.mean(), B, rtol=1e-10)
+    _, itj, _ = solvers.pcg(H, b - b.mean(), rtol=1e-10)
+    assert rel <= 1e-10 and it * 3 < itj
