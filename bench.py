@@ -855,6 +855,32 @@ def run_pp_only(args):
     print(json.dumps({"mode": "pp", "n_nodes": N, "solves": res}))
 
 
+def run_step_only(args):
+    """Profiling aid: the headline path on the headline mesh, `--warmup` untimed steps, then one
+    step inside an NVTX range "timed_step" (for an ncu launch list restricted to that range)."""
+    torch, capi, w, mesh, f0, prm = _rt_setup()
+    from paper_2107_05123_gb300.session import DeviceState, default_step_params
+    mg_pp = capi.chns_mg_create(mesh.handle, degree=2)
+    mg_ch = capi.chns_mg_create(mesh.handle, degree=2)
+    sp = rt_step_params(capi, default_step_params, capi.FP32, mg_pp, mg_ch)
+    ds = DeviceState(dict(phi=f0["phi"], mu=f0["mu"], u=f0["u"], p=f0["p"]))
+    for _ in range(args.warmup):
+        capi.chns_step(mesh.handle, ds.c, prm, sp)
+    torch.cuda.synchronize()
+    l0 = capi.chns_kernel_launches()
+    torch.cuda.nvtx.range_push("timed_step")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st = capi.chns_step(mesh.handle, ds.c, prm, sp)
+    e1.record()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"mode": "step", "ms": e0.elapsed_time(e1), "phases_ms": _phases(st),
+                      "launches": capi.chns_kernel_launches() - l0}))
+    capi.chns_mg_destroy(mg_pp)
+    capi.chns_mg_destroy(mg_ch)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -880,7 +906,7 @@ def main():
     ap.add_argument("--learned-grid", type=int, default=64, help="grid size D of the network")
     ap.add_argument("--apply-op", choices=["poisson", "mass", "ch", "momentum"], default="poisson")
     ap.add_argument("--apply-prec", choices=["fp32", "fp64"], default="fp32")
-    ap.add_argument("--mode", choices=["bench", "apply", "pp", "learned"], default="bench",
+    ap.add_argument("--mode", choices=["bench", "apply", "pp", "step", "learned"], default="bench",
                     help="apply / pp: time only one apply / the pressure solve (profiling); "
                          "learned: only the learned-preconditioner part")
     args = ap.parse_args()
@@ -888,6 +914,8 @@ def main():
         run_apply_only(args)
     elif args.mode == "pp":
         run_pp_only(args)
+    elif args.mode == "step":
+        run_step_only(args)
     elif args.mode == "learned":
         print(json.dumps(run_learned(args)))
     elif args.impl == "reference":
