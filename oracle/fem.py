@@ -17,7 +17,7 @@ Operators (readings of ambiguous passages are listed by number in the design not
 * velocity update (Def. weak_VMS_disc_vel_update): (w, rho~ u)
 * velocity prediction (Def. weak_VMS_disc): the linear operator in v^{c,k+1} with the RBVMS
   closure rho~ v^f = -tau_m R_m, tau_m with C_I = 6 and G = diag(4/h^2) [readings R1, R3, R4, R5, R8]
-  (R4: the mixed term u.G.J/(rho Pe) of the printed tau_m is bounded below by -u.G.u)
+  (R4: the printed radicand of tau_m is floored at 4/dt^2, i.e. tau_m <= dt/2)
 * Cahn-Hilliard (Def. weak_VMS_disc_CH): residual and Newton Jacobian in (phi^{k+1}, mu^{k+1})
   [reading R2: the diffusion term enters with a plus sign, as in the strong form]
 
@@ -113,6 +113,13 @@ class Elem:
         return np.einsum("kqaij,ka->kqij", self.H, self.mesh.element_values(nodal))
 
 
+def qp_coords(el: Elem) -> np.ndarray:
+    """Physical coordinates of the Gauss points (E, q, 3): element anchor + h (1 + xi) / 2."""
+    m = el.mesh
+    x0 = m.anchors.astype(np.float64) / float(1 << 20) * m.extent[None, :]
+    return x0[:, None, :] + m.h[:, None, :] * 0.5 * (1.0 + QP[None, :, :])
+
+
 # ============================================================================ scalar operators
 def stiffness(el: Elem, cq: np.ndarray) -> sp.csr_matrix:
     """(grad q, c grad p) with c given at the qps (E, q)."""
@@ -142,9 +149,14 @@ def phi_mass(el: Elem, phi: np.ndarray) -> float:
 
 
 # ============================================================================ Cahn-Hilliard
-def ch_residual(el: Elem, co: Coeffs, phi, mu, phi_k, mu_k, u_t):
+def ch_residual(el: Elem, co: Coeffs, phi, mu, phi_k, mu_k, u_t, f_phi=None, f_mu=None):
     """Residual of the discrete CH equations (Def. weak_VMS_disc_CH) at (phi, mu) = new-time
-    unknowns; u_t (3, N) is the advecting velocity u~. Returns (F_phi, F_mu)."""
+    unknowns; u_t (3, N) is the advecting velocity u~. Returns (F_phi, F_mu).
+
+    f_phi, f_mu (E, q): optional body forces at the Gauss points, used only by the
+    manufactured-solution tests (Sec. 6.1 puts the residual of a chosen solution on the right-hand
+    sides): -(q, f_phi) is added to F_phi and +(q, f_mu) to F_mu, the weak forms of
+    dphi/dt + div(u phi) - lap(mu)/(Pe Cn) = f_phi and -mu + psi'(phi) - Cn^2 lap(phi) + f_mu = 0."""
     pt = 0.5 * (phi + phi_k)
     mt = 0.5 * (mu + mu_k)
     pq, gpt = el.val(pt), el.grad(pt)
@@ -158,6 +170,10 @@ def ch_residual(el: Elem, co: Coeffs, phi, mu, phi_k, mu_k, u_t):
             + (1.0 / (co.Pe * co.Cn)) * np.einsum("e,eqad,eqd->ea", el.detJ, el.G, gmt))
     fmu = (np.einsum("e,qa,eq->ea", el.detJ, N_Q, -mtq + (pq ** 3 - pq))
            + co.Cn ** 2 * np.einsum("e,eqad,eqd->ea", el.detJ, el.G, gpt))
+    if f_phi is not None:
+        fphi = fphi - np.einsum("e,qa,eq->ea", el.detJ, N_Q, f_phi)
+    if f_mu is not None:
+        fmu = fmu + np.einsum("e,qa,eq->ea", el.detJ, N_Q, f_mu)
     return el.mesh.assemble_vector(fphi), el.mesh.assemble_vector(fmu)
 
 
@@ -182,8 +198,11 @@ class VMSState:
     """Quadrature-point coefficients of the RBVMS momentum operator for one block:
     rho~, eta~, grad eta~, u_hat, J_hat, tau_m (Def. weak_VMS_disc, tau_m definition)."""
 
-    def __init__(self, el: Elem, co: Coeffs, phi_t, u_hat, mu_t):
+    def __init__(self, el: Elem, co: Coeffs, phi_t, u_hat, mu_t, f_v=None):
+        """f_v (E, q, 3): optional body force of the manufactured-solution tests, part of the
+        strong residual R_m (R_m - f_v) and of the right-hand side (w, f_v)."""
         self.el, self.co = el, co
+        self.f_v = f_v
         pq = el.val(phi_t)
         self.rho = co.rho(pq)
         self.eta = co.eta(pq)
@@ -192,14 +211,14 @@ class VMSState:
         self.uh = np.stack([el.val(u_hat[i]) for i in range(3)], axis=-1)
         self.J = -(co.alpha / co.Cn) * el.grad(mu_t)                   # [R5]
         G = el.gGd[:, None, :]                                          # (E, 1, 3)
-        # printed tau_m; its mixed term u.G.J/(rho Pe) is bounded below by -u.G.u so that the
-        # radicand stays >= 4/dt^2 + C_I (eta/(rho Re))^2 G:G [reading R4: unbounded, the printed
-        # radicand goes negative where J/(rho Pe) >> u]
+        # printed tau_m, with its radicand floored at 4/dt^2 (tau_m <= dt/2) [reading R4: the
+        # mixed term u.G.J/(rho Pe) can take the printed radicand below 4/dt^2 and negative where
+        # J/(rho Pe) >> u; elsewhere the printed value is used as it stands]
         ugu = np.sum(self.uh * G * self.uh, axis=-1)
         ugj = (1.0 / (self.rho * co.Pe)) * np.sum(self.uh * G * self.J, axis=-1)
-        t = (4.0 / co.dt ** 2 + ugu + np.maximum(ugj, -ugu)
+        t = (4.0 / co.dt ** 2 + ugu + ugj
              + co.C_I * (self.eta / (self.rho * co.Re)) ** 2 * np.sum(G ** 2, axis=-1))
-        self.tau = t ** -0.5
+        self.tau = np.maximum(t, 4.0 / co.dt ** 2) ** -0.5
         # forcing d_j(d_i phi d_j phi) from the element Hessian (reading R8)
         gp = el.grad(phi_t)
         Hp = el.hess(phi_t)
@@ -238,6 +257,8 @@ class VMSState:
                            + gp[..., i]
                            - (1.0 / co.Re) * np.sum(self.geta * gvt, axis=-1)
                            - self.rho * GHAT[i] / co.Fr)
+            if self.f_v is not None:
+                out[..., i] -= self.f_v[..., i]
         return out
 
 
@@ -269,6 +290,9 @@ def vp_rhs(vs: VMSState, u_k, p_k):
         f_n = (vs.rho * uq / co.dt - 0.5 * vs.rho * np.sum(vs.uh * gu, -1)
                - (0.5 / co.Pe) * np.sum(vs.J * gu, -1) - gp[..., i]
                + vs.rho * GHAT[i] / co.Fr)                               # times N_a
+        if vs.f_v is not None:
+            r0 = r0 - vs.f_v[..., i]
+            f_n = f_n + vs.f_v[..., i]
         f_g = (-(0.5 / co.Re) * vs.eta[..., None] * gu
                + (co.Cn / co.We) * vs.gphi[..., i:i + 1] * vs.gphi)        # dotted with grad N_a
         be = (np.einsum("e,qa,eq->ea", el.detJ, N_Q, f_n)

@@ -41,7 +41,14 @@ def _lin(A, b, kind, x0=None, rtol=1e-12):
 
 
 def chns_step(mesh: Mesh, prm: dict, st: State, lin="direct", newton_rtol=1e-10,
-              pp_rtol=1e-12, blocks=2, log=None):
+              pp_rtol=1e-12, blocks=2, log=None, forcing=None, t=0.0, velocity_bc=None):
+    """One step from the state at time t. Two optional arguments serve the
+    manufactured-solution tests only:
+    forcing: a callable (x_qp (E, q, 3), time) -> dict(f_v (E, q, 3), f_phi (E, q), f_mu (E, q))
+      of body forces, evaluated at the midpoint t + dt/2 where the scheme's time averages are
+      centred;
+    velocity_bc: a callable (x_nodes (N, 3), time) -> (3, N) velocity values whose boundary
+      entries at t + dt are imposed on v^{k+1} and u^{k+1} (Dirichlet data instead of no-slip)."""
     el = fem.Elem(mesh)
     co = fem.Coeffs(prm)
     N = mesh.n_nodes
@@ -50,11 +57,14 @@ def chns_step(mesh: Mesh, prm: dict, st: State, lin="direct", newton_rtol=1e-10,
     phi, mu = st.phi.copy(), st.mu.copy()
     u_blk = st.u.copy()
     p_new = st.p.copy()
+    fq = forcing(fem.qp_coords(el), t + 0.5 * co.dt) if forcing is not None else {}
+    g = velocity_bc(mesh.node_xyz, t + co.dt) if velocity_bc is not None else np.zeros((3, N))
     for l in range(blocks):
         u_t = 0.5 * (st.u + u_blk)
 
         def F(x):
-            a, b = fem.ch_residual(el, co, x[:N], x[N:], st.phi, st.mu, u_t)
+            a, b = fem.ch_residual(el, co, x[:N], x[N:], st.phi, st.mu, u_t,
+                                   fq.get("f_phi"), fq.get("f_mu"))
             return np.concatenate([a, b])
 
         def J(x):
@@ -64,12 +74,12 @@ def chns_step(mesh: Mesh, prm: dict, st: State, lin="direct", newton_rtol=1e-10,
                                     linsolve=lambda A, b: _lin(A, b, lin))
         phi, mu = x[:N], x[N:]
         phi_t, mu_t = 0.5 * (phi + st.phi), 0.5 * (mu + st.mu)
-        vs = fem.VMSState(el, co, phi_t, u_hat, mu_t)
+        vs = fem.VMSState(el, co, phi_t, u_hat, mu_t, fq.get("f_v"))
         Am = fem.momentum(vs)
         bv = fem.vp_rhs(vs, st.u, st.p)
         v = np.zeros((3, N))
         for i in range(3):
-            A2, b2 = solvers.dirichlet(Am, bv[i], bnd)
+            A2, b2 = solvers.dirichlet(Am, bv[i], bnd, g[i])
             v[i] = _lin(A2, b2, lin)
         Ap = fem.poisson(el, co, phi_t)
         bp = fem.pp_rhs(vs, v, st.u, st.p)
@@ -78,7 +88,7 @@ def chns_step(mesh: Mesh, prm: dict, st: State, lin="direct", newton_rtol=1e-10,
         bu = fem.vu_rhs(vs, v, st.u, st.p, p_new)
         u_new = np.zeros((3, N))
         for i in range(3):
-            A2, b2 = solvers.dirichlet(Mr, bu[i], bnd)
+            A2, b2 = solvers.dirichlet(Mr, bu[i], bnd, g[i])
             u_new[i] = _lin(A2, b2, lin)
         u_blk = u_new
         if log is not None:

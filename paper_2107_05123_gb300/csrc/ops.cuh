@@ -300,7 +300,10 @@ __device__ __forceinline__ VmsQ<T> vms_at(const T pe[8], const T ue[3][8], const
   }
   const T er = o.eta * ir * k.inv_re;
   ugj *= jpe;
-  o.tau = rsqrt(k.four_idt2 + ugu + (ugj > -ugu ? ugj : -ugu) + k.C_I * er * er * gg);
+  // the printed radicand, floored at 4/dt^2 (tau_m <= dt/2) where its mixed term u.G.J/(rho Pe)
+  // would take it lower or negative
+  const T rad = k.four_idt2 + ugu + ugj + k.C_I * er * er * gg;
+  o.tau = rsqrt(rad > k.four_idt2 ? rad : k.four_idt2);
   o.a0 = o.rho * k.idt;
   o.e = o.eta * k.h2re;
   const T h2pe = k.h2pe, h2re = k.h2re;
