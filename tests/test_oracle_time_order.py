@@ -175,3 +175,23 @@ def test_newton_converges_in_one_iteration_at_the_paper_tolerance():
             st = ostep.chns_step(m, w.params.as_dict(), st, newton_rtol=tol, log=log)
             its += [b["newton_its"] for b in log]
         assert its[0] <= bound_first and max(its[1:]) <= bound_rest, (tol, its)
+
+
+def test_planted_missing_advection_in_the_closure_residual_is_caught(monkeypatch):
+    """R_m enters the velocity prediction, the pressure Poisson and the velocity update right-hand
+    sides through the RBVMS closure; without its advection term it no longer vanishes at the
+    exact solution and the velocity loses its second order."""
+    orig = fem.VMSState.residual_m
+
+    def no_advection(self, v, u_k, p_k):
+        out = orig(self, v, u_k, p_k)
+        vt = 0.5 * (v + u_k)
+        for i in range(3):
+            out[..., i] -= self.rho * np.sum(self.uh * self.el.grad(vt[i]), axis=-1)
+        return out
+
+    monkeypatch.setattr(fem.VMSState, "residual_m", no_advection)
+    e = _errors()
+    ru = [np.log2(e[i]["u"] / e[i + 1]["u"]) for i in range(2)]
+    assert max(ru) < 1.2, ru
+    assert e[-1]["p"] > 0.5
