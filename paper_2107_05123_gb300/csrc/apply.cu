@@ -904,9 +904,14 @@ chns_status apply_shift(const chns_mesh* m, const chns_params* prm, const void* 
         nullptr, s);
   } else if (prec == CHNS_FP32) {
     CHNS_CUDA(cudaMemsetAsync(y, 0, N * sizeof(float), s));
-    launch_patch<ShiftK<float, float>, float, float, float, false>(
-        m, p, coef_args<float>(&c), static_cast<const float*>(x), static_cast<float*>(y), nullptr,
-        s);
+    if (use_stream<ShiftK<float, float>, float, float, float>(m))
+      launch_stream<ShiftK<float, float>, float, false, false>(
+          m, p, coef_args<float>(&c), static_cast<const float*>(x), static_cast<float*>(y),
+          nullptr, s);
+    else
+      launch_patch<ShiftK<float, float>, float, float, float, false>(
+          m, p, coef_args<float>(&c), static_cast<const float*>(x), static_cast<float*>(y),
+          nullptr, s);
   } else {
     set_error("shifted apply: bad precision");
     return CHNS_EINVAL;

@@ -271,6 +271,32 @@ __device__ __forceinline__ void grad_compact_T(const T sx[4], const T sy[4], con
   }
 }
 
+// Physical gradient components at Gauss point Q from the compact data of grad_compact:
+// d/dx at (qy, qz) = gx[Q >> 1] / h_x, d/dy at (qx, qz) = gy[(Q & 1) + 2 (Q >> 2)] / h_y,
+// d/dz at (qx, qy) = gz[Q & 3] / h_z.
+__device__ __forceinline__ constexpr int gxi(int Q) { return Q >> 1; }
+__device__ __forceinline__ constexpr int gyi(int Q) { return (Q & 1) + 2 * (Q >> 2); }
+__device__ __forceinline__ constexpr int gzi(int Q) { return Q & 3; }
+
+// r_a += sum_q grad N_a(q) . V_q for per-point vectors V[d][q] (physical units, quadrature
+// weights and coefficients included): the x component of grad N_a does not depend on qx, so V_x
+// is first summed over qx (likewise y, z), then the compact transpose applies.
+template <class T>
+__device__ __forceinline__ void grad_T(const T V[3][8], const Geo<T>& g, T r[8]) {
+  T sx[4], sy[4], sz[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    sx[j] = V[0][2 * j] + V[0][2 * j + 1];
+    sz[j] = V[2][j] + V[2][j + 4];
+  }
+#pragma unroll
+  for (int z = 0; z < 2; ++z)
+#pragma unroll
+    for (int x = 0; x < 2; ++x) sy[x + 2 * z] = V[1][x + 4 * z] + V[1][x + 2 + 4 * z];
+  const T sc[3] = {g.ih[0], g.ih[1], g.ih[2]};
+  grad_compact_T(sx, sy, sz, sc, r);
+}
+
 // ---- per-quadrature-point evaluation (direct; used by the multi-field operators)
 __device__ __forceinline__ constexpr double b1(int a, int q) { return a == q ? kW0 : kW1; }
 __device__ __forceinline__ constexpr double sg(int a) { return a ? 1.0 : -1.0; }

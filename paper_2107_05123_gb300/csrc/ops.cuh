@@ -165,7 +165,7 @@ template <class T, class C>
 struct ShiftK {
   static constexpr bool QDATA = false;
   static constexpr int MIN_CTAS = sizeof(T) == 4 ? 6 : 3;
-  static constexpr int STREAM_CTAS = 0;
+  static constexpr int STREAM_CTAS = sizeof(T) == 4 ? 5 : 0;  // persistent apply (FP32)
   static constexpr int NC = 1;
   static constexpr bool DIR = false;
   static constexpr bool DIAG_PER_COMP = false;
@@ -182,16 +182,25 @@ struct ShiftK {
     const T f[NF][8] = {};
     setup(f, g, p);
   }
+  // sa = 0 or sb = 0 (the stiffness K and the mass M of the Schur preconditioner) skip the other
+  // part: the branch is uniform over the whole launch
   __device__ __forceinline__ void apply(const Geo<T>& g, const DevParams&, const T x[NC][8],
                                         T r[NC][8]) const {
-    stiff_local(ck, g, x[0], r[0]);
-    T v[8], t[8];
-    interp3(x[0], v);
+    if (ck[0] != T(0)) {
+      stiff_local(ck, g, x[0], r[0]);
+    } else {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] *= cm;
-    interp3(v, t);
+      for (int a = 0; a < 8; ++a) r[0][a] = T(0);
+    }
+    if (cm != T(0)) {
+      T v[8], t[8];
+      interp3(x[0], v);
 #pragma unroll
-    for (int a = 0; a < 8; ++a) r[0][a] += t[a];
+      for (int q = 0; q < 8; ++q) v[q] *= cm;
+      interp3(v, t);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) r[0][a] += t[a];
+    }
   }
 };
 
@@ -226,30 +235,54 @@ struct ChK {
 #pragma unroll
     for (int d = 0; d < 3; ++d) gather<T, false>(m, idx, cf.u[d], ue[d]);
   }
+  // Sum-factorised: values at the Gauss points by interp3, gradients by grad_compact, and the
+  // transposes (interp3 is its own transpose, grad_T) on the per-point terms.
   __device__ __forceinline__ void apply(const Geo<T>& g, const DevParams& p, const T x[NC][8],
                                         T r[NC][8]) const {
-#pragma unroll
-    for (int a = 0; a < 8; ++a) r[0][a] = r[1][a] = T(0);
     const PrmT<T>& pk = p.get<T>();
-    const T idt = pk.idt, kmu = pk.kmu, kphi = pk.kphi;
     const T J = g.detJ;
-    for_qp([&](auto QC) {
-      constexpr int Q = decltype(QC)::value;
-      T pq = val_at<Q>(pe);
-      T psi2 = T(3) * pq * pq - T(1);
-      T uq[3] = {val_at<Q>(ue[0]), val_at<Q>(ue[1]), val_at<Q>(ue[2])};
-      T fv, fg[3], mv, mg[3];
-      vg_at<Q>(x[0], g, fv, fg);
-      vg_at<Q>(x[1], g, mv, mg);
-      T V0[3], V1[3];
+    T pq[8], fv[8], mv[8];
+    interp3(pe, pq);
+    interp3(x[0], fv);
+    interp3(x[1], mv);
+    T s[8], V[3][8];
+    // row mu: -1/2 (q, dmu) + 1/2 (q, psi''(phi~) dphi) + Cn^2/2 (grad q, grad dphi)
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      s[q] = J * T(0.5) * ((T(3) * pq[q] * pq[q] - T(1)) * fv[q] - mv[q]);
+    interp3(s, r[1]);
+    {
+      T gx[4], gy[4], gz[4];
+      grad_compact(x[0], gx, gy, gz);
+      const T c = J * pk.kphi;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        V[0][q] = c * gx[gxi(q)] * g.ih[0];
+        V[1][q] = c * gy[gyi(q)] * g.ih[1];
+        V[2][q] = c * gz[gzi(q)] * g.ih[2];
+      }
+      grad_T(V, g, r[1]);
+    }
+    // row phi: (q, dphi)/dt - 1/2 (grad q, u~ dphi) + 1/(2 Pe Cn) (grad q, grad dmu)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s[q] = J * pk.idt * fv[q];
+    interp3(s, r[0]);
+    {
+      T gx[4], gy[4], gz[4];
+      grad_compact(x[1], gx, gy, gz);
+      const T c = J * pk.kmu;
+      T uq[8];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        V0[d] = J * (T(-0.5) * uq[d] * fv + kmu * mg[d]);
-        V1[d] = J * kphi * fg[d];
+        interp3(ue[d], uq);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const T gm = d == 0 ? gx[gxi(q)] : d == 1 ? gy[gyi(q)] : gz[gzi(q)];
+          V[d][q] = c * gm * g.ih[d] - J * T(0.5) * uq[q] * fv[q];
+        }
       }
-      add_test<Q>(r[0], J * fv * idt, V0, g);
-      add_test<Q>(r[1], J * (T(-0.5) * mv + T(0.5) * psi2 * fv), V1, g);
-    });
+      grad_T(V, g, r[0]);
+    }
   }
 };
 

@@ -41,23 +41,45 @@ k_residual_ch(MeshDev m, DevParams p, const double* __restrict__ phi, const doub
   for (int i = 0; i < 8; ++i) mt[i] = 0.5 * (a[i] + b[i]);
 #pragma unroll
   for (int d = 0; d < 3; ++d) gather<double, false>(m, idx, u.c[d], ue[d]);
-  double r0[8] = {0}, r1[8] = {0};
+  // sum-factorised: values at the Gauss points by interp3, gradients by grad_compact, and the
+  // transposes interp3 / grad_T on the per-point terms
+  double r0[8], r1[8];
   const double J = g.detJ, kmu = p.d.inv_pecn, c2 = p.d.cn2;
-  for_qp([&](auto QC) {
-    constexpr int Q = decltype(QC)::value;
-    double pv, pg[3], mv, mg[3];
-    vg_at<Q>(pt, g, pv, pg);
-    vg_at<Q>(mt, g, mv, mg);
-    double dv = val_at<Q>(dp);
-    double V0[3], V1[3];
+  double pv[8], mv[8], s[8], V[3][8];
+  interp3(pt, pv);
+  interp3(mt, mv);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s[q] = J * (pv[q] * pv[q] * pv[q] - pv[q] - mv[q]);
+  interp3(s, r1);
+  {
+    double gx[4], gy[4], gz[4];
+    grad_compact(pt, gx, gy, gz);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      V[0][q] = J * c2 * gx[gxi(q)] * g.ih[0];
+      V[1][q] = J * c2 * gy[gyi(q)] * g.ih[1];
+      V[2][q] = J * c2 * gz[gzi(q)] * g.ih[2];
+    }
+    grad_T(V, g, r1);
+  }
+  interp3(dp, s);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s[q] *= J;
+  interp3(s, r0);
+  {
+    double gx[4], gy[4], gz[4], uq[8];
+    grad_compact(mt, gx, gy, gz);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      V0[d] = J * (-val_at<Q>(ue[d]) * pv + kmu * mg[d]);
-      V1[d] = J * c2 * pg[d];
+      interp3(ue[d], uq);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const double gm = d == 0 ? gx[gxi(q)] : d == 1 ? gy[gyi(q)] : gz[gzi(q)];
+        V[d][q] = J * (kmu * gm * g.ih[d] - uq[q] * pv[q]);
+      }
     }
-    add_test<Q>(r0, J * dv, V0, g);
-    add_test<Q>(r1, J * (-mv + pv * pv * pv - pv), V1, g);
-  });
+    grad_T(V, g, r0);
+  }
   scatter<double, false>(m, idx, r0, f);
   scatter<double, false>(m, idx, r1, f + m.n_nodes);
 }

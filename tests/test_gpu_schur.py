@@ -34,6 +34,21 @@ def _solve(gm, prm, coef, b, pc, inner=capi.FP64, rtol=1e-12, max_it=20000, inne
     return x.cpu().numpy(), st
 
 
+@pytest.mark.parametrize("kernel", [capi.APPLY_PATCH, capi.APPLY_STREAM])
+def test_schur_mixed_precision_through_either_apply_kernel(kernel):
+    """The FP32 shifted operator of the preconditioner runs through the per-patch or the
+    persistent pipelined kernel (the automatic choice on large meshes); both reach the FP64
+    residual the oracle's matrix confirms."""
+    om, gm, A, b, coef = _system(PRM, 94)
+    capi.chns_mesh_set_apply_config(gm.handle, kernel, 0)
+    try:
+        x, st = _solve(gm, PRM, coef, b, capi.PC_SCHUR, inner=capi.FP32, rtol=1e-10)
+    finally:
+        capi.chns_mesh_set_apply_config(gm.handle, capi.APPLY_AUTO, 0)
+    assert st.status == capi.OK
+    assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1.05e-10
+
+
 @pytest.mark.parametrize("inner_its", [0, 6])
 def test_schur_solve_fp64_matches_oracle(inner_its):
     om, gm, A, b, coef = _system(PRM, 91)
