@@ -456,8 +456,45 @@ struct MomQK {
     ne = n_elem;
     e = elem;
   }
-  __device__ __forceinline__ void apply(const Geo<T>& g, const DevParams&, const T x[NC][8],
+  __device__ __forceinline__ void apply(const Geo<T>& g, const DevParams& p, const T x[NC][8],
                                         T r[NC][8]) const {
+    if constexpr (sizeof(T) == sizeof(double))
+      apply_sf(g, x, r);
+    else
+      apply_direct(g, p, x, r);
+  }
+  // Sum-factorised, one component at a time (values by interp3, gradients from the compact
+  // per-axis data, transposes interp3 / grad_T); the quadrature data is read per component (the
+  // FP64 arithmetic, not the reads, bounds this form).
+  __device__ __forceinline__ void apply_sf(const Geo<T>& g, const T x[NC][8], T r[NC][8]) const {
+    const T J = g.detJ;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      T v[8], gx[4], gy[4], gz[4], s[8], V[3][8];
+      interp3(x[k], v);
+      grad_compact(x[k], gx, gy, gz);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const T* qq = qd + (int64_t)q * kMomQ * ne + e;
+        const T vg[3] = {gx[gxi(q)] * g.ih[0], gy[gyi(q)] * g.ih[1], gz[gzi(q)] * g.ih[2]};
+        const T a0 = __ldg(qq);
+        T sb = a0 * v[q], R = a0 * v[q];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          sb += __ldg(qq + (1 + d) * ne) * vg[d];
+          R += __ldg(qq + (4 + d) * ne) * vg[d];
+        }
+        const T ce = __ldg(qq + 7 * ne);
+        s[q] = J * sb;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) V[d][q] = J * (ce * vg[d] + R * __ldg(qq + (8 + d) * ne));
+      }
+      interp3(s, r[k]);
+      grad_T(V, g, r[k]);
+    }
+  }
+  __device__ __forceinline__ void apply_direct(const Geo<T>& g, const DevParams&,
+                                               const T x[NC][8], T r[NC][8]) const {
 #pragma unroll
     for (int k = 0; k < NC; ++k)
 #pragma unroll
