@@ -54,9 +54,7 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
   T* ys = xs + NC * kPatchSlots;                // [NC][kPatchSlots]
   T* fs = ys + NC * kPatchSlots;                // [NF][kPatchSlots]
   const int pidx = blockIdx.x;
-  const int pn = m.patch_nreg[pidx];
-  const int s0 = m.patch_slot[pidx], ns = m.patch_slot[pidx + 1] - s0, nreg = pn & kNregMask;
-  const int ncol = pn >> kNcolShift;
+  const int s0 = m.patch_slot[pidx], ns = m.patch_slot[pidx + 1] - s0, nreg = m.patch_nreg[pidx];
   const int64_t N = m.n_nodes;
   const C* fptr[5] = {cf.phi, cf.u[0], cf.u[1], cf.u[2], cf.mu};
   // CG direction update fused into the gather (CGP): p_new = z + beta p_old with
@@ -137,19 +135,11 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
   __syncthreads();
   // 3. elements
   typename Acc<T>::type en[1] = {Acc<T>::zero()};
-  T r[NC][8];
-  int sl[8];
-  const int col = has_elem ? (int)((lp.x >> kElocColourShift) & kElocColourMask) : -1;
   if (has_elem) {
     const int lev = (int)(lp.x >> kElocLevelShift) & kElocLevelMask;
-    sl[0] = (int)(lp.x & kElocSlotMask);
-    sl[1] = (int)((lp.x >> 16) & kElocSlotMask);
-    sl[2] = (int)(lp.y & 0xffff);
-    sl[3] = (int)(lp.y >> 16);
-    sl[4] = (int)(lp.z & 0xffff);
-    sl[5] = (int)(lp.z >> 16);
-    sl[6] = (int)(lp.w & 0xffff);
-    sl[7] = (int)(lp.w >> 16);
+    const int sl[8] = {(int)(lp.x & kElocSlotMask), (int)(lp.x >> 16), (int)(lp.y & 0xffff),
+                       (int)(lp.y >> 16),    (int)(lp.z & 0xffff), (int)(lp.z >> 16),
+                       (int)(lp.w & 0xffff), (int)(lp.w >> 16)};
     const Geo<T> g = level_geometry<T>(m, lev);
     T fe[NF][8];
 #pragma unroll
@@ -164,25 +154,19 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
     for (int c = 0; c < NC; ++c)
 #pragma unroll
       for (int a = 0; a < 8; ++a) xin[c][a] = xs[c * kPatchSlots + sl[a]];
+    T r[NC][8];
     constexpr bool EF = PQ && HasEnergy<K>::value;
     if constexpr (EF)
       Acc<T>::add(en[0], k.apply_energy(g, p, xin, r));
     else
       k.apply(g, p, xin, r);
-    if (PQ && !EF)
 #pragma unroll
-      for (int c = 0; c < NC; ++c)
+    for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int a = 0; a < 8; ++a) Acc<T>::fma(en[0], xin[c][a], r[c][a]);
-  }
-  // accumulate colour by colour (no two elements of a colour share a slot)
-  for (int cc = 0; cc < ncol; ++cc) {
-    if (col == cc)
-#pragma unroll
-      for (int c = 0; c < NC; ++c)
-#pragma unroll
-        for (int a = 0; a < 8; ++a) ys[c * kPatchSlots + sl[a]] += r[c][a];
-    __syncthreads();
+      for (int a = 0; a < 8; ++a) {
+        if (PQ && !EF) Acc<T>::fma(en[0], xin[c][a], r[c][a]);
+        atomicAdd(ys + c * kPatchSlots + sl[a], r[c][a]);
+      }
   }
   // p.Ap
   if (PQ) {
@@ -339,7 +323,7 @@ k_apply_stream(MeshDev m, DevParams p, CoefArgs<T> cf, const T* __restrict__ x, 
   };
   // slot table of patch q (ring entry r landed) into index buffer bi
   auto issue_idx = [&](int r, int bi) {
-    const int s0 = mt[8 * r], nr = mt[8 * r + 2] & kNregMask;
+    const int s0 = mt[8 * r], nr = mt[8 * r + 2];
     int32_t* dst = ib + bi * kPatchSlots;
     for (int i = tid; i < nr; i += kPatchElems) cp_async_b<4>(dst + i, m.slot_node + s0 + i);
   };
@@ -347,7 +331,7 @@ k_apply_stream(MeshDev m, DevParams p, CoefArgs<T> cf, const T* __restrict__ x, 
   // (from index buffer bi: each thread reads only entries its own copies wrote), element slot
   // tables, parents of the first kPqStage hanging slots
   auto issue_stage = [&](int r, int st, int bi) {
-    const int s0 = mt[8 * r], s1 = mt[8 * r + 1], nr = mt[8 * r + 2] & kNregMask;
+    const int s0 = mt[8 * r], s1 = mt[8 * r + 1], nr = mt[8 * r + 2];
     const int e0 = mt[8 * r + 3], e1 = mt[8 * r + 4];
     const int32_t* src = ib + bi * kPatchSlots;
     T* dst = vb + st * NA * kPatchSlots;
@@ -383,8 +367,7 @@ k_apply_stream(MeshDev m, DevParams p, CoefArgs<T> cf, const T* __restrict__ x, 
     if (pid + 2 * G < np) issue_idx((k + 2) & 3, (k + 2) % 3);
     if (pid + 3 * G < np) issue_meta(pid + 3 * G, (k + 3) & 3);
     cp_async_commit();
-    const int s0 = mt[8 * rc], ns = mt[8 * rc + 1] - s0, nreg = mt[8 * rc + 2] & kNregMask;
-    const int ncol = mt[8 * rc + 2] >> kNcolShift;
+    const int s0 = mt[8 * rc], ns = mt[8 * rc + 1] - s0, nreg = mt[8 * rc + 2];
     const int e0 = mt[8 * rc + 3], ne = mt[8 * rc + 4] - e0;
     T* xs = vb + st * NA * kPatchSlots;
     const T* zs = xs + NC * kPatchSlots;
@@ -431,21 +414,12 @@ k_apply_stream(MeshDev m, DevParams p, CoefArgs<T> cf, const T* __restrict__ x, 
     }
     __syncthreads();
     // 3. elements
-    T r[NC][8];
-    int sl[8];
-    int col = -1;
     if (tid < ne) {
       const uint4 lp = elb[st * kPatchElems + tid];
       const int lev = (int)(lp.x >> kElocLevelShift) & kElocLevelMask;
-      col = (int)((lp.x >> kElocColourShift) & kElocColourMask);
-      sl[0] = (int)(lp.x & kElocSlotMask);
-      sl[1] = (int)((lp.x >> 16) & kElocSlotMask);
-      sl[2] = (int)(lp.y & 0xffff);
-      sl[3] = (int)(lp.y >> 16);
-      sl[4] = (int)(lp.z & 0xffff);
-      sl[5] = (int)(lp.z >> 16);
-      sl[6] = (int)(lp.w & 0xffff);
-      sl[7] = (int)(lp.w >> 16);
+      const int sl[8] = {(int)(lp.x & kElocSlotMask), (int)(lp.x >> 16), (int)(lp.y & 0xffff),
+                         (int)(lp.y >> 16),    (int)(lp.z & 0xffff), (int)(lp.z >> 16),
+                         (int)(lp.w & 0xffff), (int)(lp.w >> 16)};
       const Geo<T> g = level_geometry<T>(m, lev);
       T fe[NF][8];
 #pragma unroll
@@ -459,27 +433,21 @@ k_apply_stream(MeshDev m, DevParams p, CoefArgs<T> cf, const T* __restrict__ x, 
       for (int c = 0; c < NC; ++c)
 #pragma unroll
         for (int a = 0; a < 8; ++a) xin[c][a] = xs[c * kPatchSlots + sl[a]];
+      T r[NC][8];
       constexpr bool EF = PQ && HasEnergy<K>::value;
       if constexpr (EF)
         Acc<T>::add(en[0], kk.apply_energy(g, p, xin, r));
       else
         kk.apply(g, p, xin, r);
-      if (PQ && !EF)
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
+      for (int c = 0; c < NC; ++c)
 #pragma unroll
-          for (int a = 0; a < 8; ++a) Acc<T>::fma(en[0], xin[c][a], r[c][a]);
+        for (int a = 0; a < 8; ++a) {
+          if (PQ && !EF) Acc<T>::fma(en[0], xin[c][a], r[c][a]);
+          atomicAdd(ys + c * kPatchSlots + sl[a], r[c][a]);
+        }
     }
-    // accumulate colour by colour (no two elements of a colour share a slot); the last barrier
-    // also orders the accumulators before the hanging pass
-    for (int cc = 0; cc < ncol; ++cc) {
-      if (col == cc)
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-#pragma unroll
-          for (int a = 0; a < 8; ++a) ys[c * kPatchSlots + sl[a]] += r[c][a];
-      __syncthreads();
-    }
+    __syncthreads();
     // 4. hanging slots -> parents
     for (int i = nreg + tid; i < ns; i += kPatchElems) {
       const ushort4 q = parents(i);

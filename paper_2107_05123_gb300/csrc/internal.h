@@ -23,19 +23,10 @@ constexpr int32_t kNodeMask = kOwnBit - 1;
 constexpr int kPatchElems = 256;
 constexpr int kPatchSlots = 1024;
 // Per element of a patch, eloc holds its 8 corner slots as uint16; slots are < kPatchSlots, so the
-// first entry also carries the element's level in bits 10-14 and the second its colour in bits
-// 10-13. Elements of one colour share no slot of their patch, so the element results are added
-// into the patch's shared accumulators colour by colour with plain read-modify-write (shared-memory
-// float atomics compile to compare-and-swap loops). A patch has at most kMaxColours colours; the
-// count sits in bits 16-20 of its patch_nreg entry (the regular-slot count in bits 0-15).
+// first entry also carries the element's level in bits 10-14.
 constexpr uint32_t kElocSlotMask = 0x3ff;
 constexpr int kElocLevelShift = 10;
 constexpr uint32_t kElocLevelMask = 0x1f;
-constexpr int kElocColourShift = 26;  // in the first 32-bit word (second uint16, bits 10-13)
-constexpr uint32_t kElocColourMask = 0xf;
-constexpr int kMaxColours = 16;
-constexpr uint32_t kNregMask = 0xffff;
-constexpr int kNcolShift = 16;
 // The persistent, pipelined apply is chosen automatically once the mesh has at least this many
 // patches per SM.
 constexpr int kStreamMinPatchesPerSm = 16;

@@ -165,10 +165,6 @@ static void build_patches(int64_t n, int64_t N, const std::vector<int32_t>& enod
   std::vector<int32_t> count(N, 0);
   std::vector<int32_t> reg, hg;                    // current patch: node ids, hanging ids
   std::vector<std::array<int32_t, 8>> ecorner;     // provisional: >= 0 regular slot, < 0 ~hslot
-  std::vector<uint8_t> ecol;                       // colour of each element of the patch
-  // colours used by the elements touching each slot of the current patch (regular, hanging)
-  std::vector<uint16_t> mask_n(kPatchSlots, 0), mask_h(kPatchSlots, 0);
-  int ncol = 0;
   int32_t pid = 0;
   int64_t e0 = 0;
   P.eloc.resize(n);
@@ -176,7 +172,7 @@ static void build_patches(int64_t n, int64_t N, const std::vector<int32_t>& enod
     const int32_t nr = (int32_t)reg.size();
     P.elem.push_back((int32_t)e0);
     P.slot.push_back((int32_t)P.node.size());
-    P.nreg.push_back(nr | (ncol << kNcolShift));
+    P.nreg.push_back(nr);
     for (int32_t id : reg) {
       P.node.push_back(id);
       P.par.push_back(make_ushort4(0xffff, 0xffff, 0xffff, 0xffff));
@@ -198,17 +194,12 @@ static void build_patches(int64_t n, int64_t N, const std::vector<int32_t>& enod
         l[c] = (unsigned short)(v >= 0 ? v : nr + ~v);
       }
       l[0] = (unsigned short)(l[0] | ((uint32_t)levels[e] << kElocLevelShift));
-      l[1] = (unsigned short)(l[1] | ((uint32_t)ecol[e - e0] << (kElocColourShift - 16)));
       P.eloc[e] = make_uint4(l[0] | (l[1] << 16), l[2] | (l[3] << 16), l[4] | (l[5] << 16),
                              l[6] | (l[7] << 16));
     }
-    for (size_t k = 0; k < reg.size(); ++k) mask_n[k] = 0;
-    for (size_t k = 0; k < hg.size(); ++k) mask_h[k] = 0;
-    ncol = 0;
     reg.clear();
     hg.clear();
     ecorner.clear();
-    ecol.clear();
     ++pid;
     e0 = e_end;
   };
@@ -243,19 +234,7 @@ static void build_patches(int64_t n, int64_t N, const std::vector<int32_t>& enod
       }
     }
     const int64_t slots = (int64_t)reg.size() + hg.size() + nn + nh;
-    // colour: the lowest one not used by an element that shares a slot already in the patch
-    uint32_t forbidden = 0;
-    for (int c = 0; c < 8; ++c) {
-      const int32_t j = enode[8 * e + c] & kIdxMask;
-      if (j < N) {
-        if (stamp_n[j] == pid) forbidden |= mask_n[slot_n[j]];
-      } else if (stamp_h[j - (int32_t)N] == pid) {
-        forbidden |= mask_h[slot_h[j - (int32_t)N]];
-      }
-    }
-    int colour = 0;
-    while (colour < kMaxColours && (forbidden >> colour) & 1u) ++colour;
-    if (e > e0 && (e - e0 >= kPatchElems || slots > kPatchSlots || colour >= kMaxColours)) {
+    if (e > e0 && (e - e0 >= kPatchElems || slots > kPatchSlots)) {
       close(e);
       --e;  // re-examine this element in the new patch
       continue;
@@ -275,14 +254,8 @@ static void build_patches(int64_t n, int64_t N, const std::vector<int32_t>& enod
     for (int c = 0; c < 8; ++c) {
       const int32_t j = enode[8 * e + c] & kIdxMask;
       ec[c] = j < N ? slot_n[j] : ~slot_h[j - (int32_t)N];
-      if (j < N)
-        mask_n[slot_n[j]] |= (uint16_t)(1u << colour);
-      else
-        mask_h[slot_h[j - (int32_t)N]] |= (uint16_t)(1u << colour);
     }
     ecorner.push_back(ec);
-    ecol.push_back((uint8_t)colour);
-    ncol = std::max(ncol, colour + 1);
   }
   close(n);
   P.elem.push_back((int32_t)n);

@@ -212,7 +212,7 @@ struct ShiftK {
 template <class T, class C>
 struct ChK {
   static constexpr bool QDATA = false;
-  static constexpr int MIN_CTAS = sizeof(T) == 4 ? 3 : 1;
+  static constexpr int MIN_CTAS = sizeof(T) == 4 ? 4 : 1;
   static constexpr int STREAM_CTAS = 0;  // persistent apply (0: not used)
   static constexpr int NC = 2;
   static constexpr bool DIR = false;
