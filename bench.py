@@ -881,6 +881,77 @@ def run_step_only(args):
     capi.chns_mg_destroy(mg_ch)
 
 
+def run_breakup(args):
+    """The many-drop breakup workload (64 seeded drops of radius 0.02-0.08, the shear
+    u = (2y - 1, 0, 0) imposed on every wall, density ratio 100, viscosity ratio 50, Re 2000,
+    We 50, Cn 0.002, dt 1e-4) on the levels --breakup-levels: time per step of the
+    mixed-precision path with the multigrid preconditioners (the headline settings) beside one
+    step of the all-FP64 Jacobi path from the same state, and each FP32 apply's HBM fraction on
+    this mesh."""
+    import torch
+
+    from chns_workloads import configs
+    from paper_2107_05123_gb300 import capi
+    from paper_2107_05123_gb300.session import DeviceState, Mesh, VelocityBC, default_step_params
+
+    lmin, lmax = (int(v) for v in args.breakup_levels.split(","))
+    t0 = time.perf_counter()
+    w = configs.breakup(lmin, lmax)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mesh = Mesh(w.anchors, w.levels, w.extent)
+    t_mesh = time.perf_counter() - t0
+    N = mesh.n_nodes
+    f0 = w.init(mesh.node_xyz)
+    bc = VelocityBC(w.info["velocity_bc"](mesh.node_xyz, 0.0))
+    prm = capi.make_params(w.params.as_dict())
+    t0 = time.perf_counter()
+    mg_pp = capi.chns_mg_create(mesh.handle, degree=2)
+    mg_ch = capi.chns_mg_create(mesh.handle, degree=2)
+    t_mg = time.perf_counter() - t0
+    _say(f"[breakup] {mesh.n_elem} leaves, {N} nodes (octree {t_gen:.1f} s, mesh {t_mesh:.1f} s, "
+         f"multigrid {t_mg:.1f} s)")
+    flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    flush = lambda: flush_buf.fill_(1.0)
+    sync = torch.cuda.synchronize
+    sp = bc.attach(rt_step_params(capi, default_step_params, capi.FP32, mg_pp, mg_ch))
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        head = run_steps(capi, DeviceState, mesh, prm, f0, sp, args.warmup, args.steps, sync)
+    ms = statistics.mean(head["step_ms"])
+    _say(f"[breakup] mixed precision + multigrid {ms:.1f} ms/step")
+    last = head["last"]
+    out = {"mode": "breakup", "workload": f"breakup64_levels{lmin}-{lmax}",
+           "n_elem": int(mesh.n_elem), "n_nodes": int(N), "n_hanging": int(mesh.n_hanging),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
+           "first_step_ms": round(head["first_ms"], 1), "phases_ms": _phases(last),
+           "newton_its": list(last.newton_its),
+           "ch_gmres_its": [last.ch[l].iterations for l in range(2)],
+           "vp_gmres_its": [last.vp[l].iterations for l in range(2)],
+           "pp_fcg_its": [last.pp[l].iterations for l in range(2)],
+           "pp_dofs_per_s": N * head["pp_n"] / (head["pp_ms"] * 1e-3),
+           "mass_drift": abs(last.phi_mass_after - last.phi_mass_before),
+           "gpu_launches": head["launches"], "clocks": clk.summary(),
+           "setup_s": {"octree": round(t_gen, 1), "mesh": round(t_mesh, 1),
+                       "multigrid": round(t_mg, 1)}}
+    if not args.no_plain:
+        sp64 = bc.attach(rt_step_params(capi, default_step_params, capi.FP64))
+        plain = run_steps(capi, DeviceState, mesh, prm, f0, sp64, 0, 1, sync)
+        out["plain_fp64"] = {"ms_per_step": round(plain["step_ms"][0], 1),
+                             "phases_ms": _phases(plain["last"]),
+                             "pp_its": [plain["last"].pp[l].iterations for l in range(2)]}
+        out["speedup_first_step_vs_plain_fp64"] = round(plain["step_ms"][0] / head["first_ms"], 2)
+        out["field_error_vs_plain_fp64_after_1_step"] = field_errors(head["first"], plain["first"])
+    ap = time_applies(capi, mesh, prm, f0, flush)
+    out["applies_hbm_frac_fp32"] = {k: ap["fp32"][k]["frac"] for k in ("poisson", "mass", "ch",
+                                                                         "momentum")}
+    out["applies_ms"] = {p: {k: ap[p][k]["ms"] for k in ("poisson", "mass", "ch", "momentum")}
+                         for p in ("fp32", "fp64")}
+    out["peak_gbs"], out["peak_kind"] = ap["peak_gbs"], ap["peak_kind"]
+    capi.chns_mg_destroy(mg_pp)
+    capi.chns_mg_destroy(mg_ch)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -906,9 +977,13 @@ def main():
     ap.add_argument("--learned-grid", type=int, default=64, help="grid size D of the network")
     ap.add_argument("--apply-op", choices=["poisson", "mass", "ch", "momentum"], default="poisson")
     ap.add_argument("--apply-prec", choices=["fp32", "fp64"], default="fp32")
-    ap.add_argument("--mode", choices=["bench", "apply", "pp", "step", "learned"], default="bench",
+    ap.add_argument("--breakup-levels", default="6,9",
+                    help="octree levels lmin,lmax of the many-drop breakup workload")
+    ap.add_argument("--mode", choices=["bench", "apply", "pp", "step", "learned", "breakup"],
+                    default="bench",
                     help="apply / pp: time only one apply / the pressure solve (profiling); "
-                         "learned: only the learned-preconditioner part")
+                         "learned: only the learned-preconditioner part; breakup: the many-drop "
+                         "breakup workload under shear")
     args = ap.parse_args()
     if args.mode == "apply":
         run_apply_only(args)
@@ -918,6 +993,8 @@ def main():
         run_step_only(args)
     elif args.mode == "learned":
         print(json.dumps(run_learned(args)))
+    elif args.mode == "breakup":
+        print(json.dumps(run_breakup(args)))
     elif args.impl == "reference":
         run_reference(args)
     else:

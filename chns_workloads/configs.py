@@ -123,6 +123,36 @@ def many_drops(seed: int = 0, n: int = 8, rmin: float = 0.05, rmax: float = 0.12
                     _drops_init(c, r, Cn), steps=1, info=dict(centres=c, radii=r))
 
 
+def shear_velocity(x, U=1.0):
+    """The linear shear u = U (2y - 1, 0, 0) of the unit cube: the walls y = 0 and y = 1 move
+    with -U and +U, the faces x = 0 and x = 1 see the profile flow in and out (zero net flux)."""
+    u = np.zeros((3, len(x)))
+    u[0] = U * (2.0 * x[:, 1] - 1.0)
+    return u
+
+
+def breakup(lmin: int = 6, lmax: int = 11, Cn: float = 0.002, n: int = 64, seed: int = 0,
+            U: float = 1.0) -> Workload:
+    """Many-drop breakup: n seeded non-overlapping drops of radius 0.02-0.08 (phi = -1 inside) in
+    the unit cube under the shear u = U (2y - 1, 0, 0), imposed as velocity Dirichlet data on
+    every face and taken as the initial velocity; density ratio 100, viscosity ratio 50,
+    Re 2000, We 50, Fr 1, dt 1e-4; levels lmin..lmax refined where |phi| < 0.9."""
+    c, r = fields.sample_drops(seed, n, 0.02, 0.08)
+    phi_fn = lambda x: np.tanh(fields.nearest_drop(x, c, r)[1] / (np.sqrt(2.0) * Cn))
+    a, l = octree.build_octree(octree.refine_band(phi_fn, (1, 1, 1), 0.9), lmin, lmax)
+    a, l = octree.balance21(a, l)
+    p = Params(Re=2000.0, We=50.0, Cn=Cn, Pe=1.0 / (3 * Cn * Cn), Fr=1.0, rho_ratio=100.0,
+               eta_ratio=50.0, dt=1e-4)
+
+    def init(x):
+        phi, lap = fields.drops_phi_nearest(x, c, r, Cn)
+        return dict(phi=phi, mu=fields.chem_potential(phi, lap, Cn), u=shear_velocity(x, U),
+                    p=np.zeros(len(x)))
+    return Workload(f"breakup{n}_s{seed}_l{lmin}-{lmax}", a, l, (1.0, 1.0, 1.0), p, init,
+                    steps=50, info=dict(centres=c, radii=r,
+                                        velocity_bc=lambda x, t: shear_velocity(x, U)))
+
+
 def random_balanced(seed: int, lmin: int = 1, lmax: int = 4, frac: float = 0.3):
     """A small random 2:1-balanced octree (for hanging-node tests): refine a random fraction
     of octants at each level, then balance."""

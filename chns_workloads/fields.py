@@ -92,6 +92,36 @@ def rt_phi(x, Cn, y0=2.0, amp=0.05):
     return _tanh_profile(d, g2, lapd, Cn)
 
 
+def nearest_drop(x, centres, radii, chunk: int = 1 << 20):
+    """Index of the drop with the smallest signed distance |x - c_i| - R_i at each point and that
+    distance, for many points and drops (squared distances through one matrix product per chunk
+    of points)."""
+    c = np.atleast_2d(np.asarray(centres, dtype=np.float64))
+    R = np.atleast_1d(np.asarray(radii, dtype=np.float64))
+    cc = np.sum(c * c, axis=1)
+    idx = np.empty(len(x), dtype=np.int64)
+    dmin = np.empty(len(x))
+    for s in range(0, len(x), chunk):
+        xs = np.asarray(x[s:s + chunk], dtype=np.float64)
+        d2 = np.sum(xs * xs, axis=1)[:, None] - 2.0 * (xs @ c.T) + cc[None, :]
+        d = np.sqrt(np.maximum(d2, 0.0)) - R[None, :]
+        i = np.argmin(d, axis=1)
+        idx[s:s + chunk] = i
+        dmin[s:s + chunk] = d[np.arange(len(xs)), i]
+    return idx, dmin
+
+
+def drops_phi_nearest(x, centres, radii, Cn):
+    """The phase of many drops, phi = tanh(d / (sqrt(2) Cn)) with d the smallest signed distance
+    to a drop (tanh is increasing, so this is the minimum over drops of each drop's profile), and
+    its Laplacian from that nearest drop, with r evaluated exactly for it."""
+    c = np.atleast_2d(np.asarray(centres, dtype=np.float64))
+    R = np.atleast_1d(np.asarray(radii, dtype=np.float64))
+    i, _ = nearest_drop(x, c, R)
+    r = np.linalg.norm(x - c[i], axis=1)
+    return _tanh_profile(r - R[i], 1.0, 2.0 / np.maximum(r, 1e-300), Cn)
+
+
 def sample_drops(seed: int, n: int, rmin: float, rmax: float, margin: float = 0.02,
                  max_tries: int = 100000):
     """Non-overlapping drops in the unit cube by rejection sampling (seeded)."""

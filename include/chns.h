@@ -302,6 +302,13 @@ typedef struct {
   int32_t collect_every;
   int32_t collect_max;
   int32_t collect_with_net;  /* iterates of FCG with the network instead of Jacobi-PCG */
+  /* Velocity Dirichlet data: three FP64 device arrays of n_nodes (only the entries of boundary
+   * nodes are read) imposed on v^{k+1} and u^{k+1} in place of no-slip; NULL (all three) is
+   * no-slip. The data is lifted into the right-hand sides of the velocity prediction and update
+   * (b - A g on the other rows, g on the boundary rows), which keeps the solved systems those of
+   * zero data. The paper's weak forms assume u.n = 0 on the walls (Sec. 4): data with a normal
+   * component leaves the Cahn-Hilliard boundary flux out, as the paper's forms do. */
+  const double* u_bc[3];
 } chns_step_params;
 
 typedef struct {

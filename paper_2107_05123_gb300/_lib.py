@@ -87,7 +87,8 @@ class chns_step_params(C.Structure):
                 ("newton_rtol", C.c_double), ("newton_atol", C.c_double),
                 ("newton_max_it", C.c_int32), ("blocks", C.c_int32),
                 ("collect", C.c_void_p), ("collect_every", C.c_int32),
-                ("collect_max", C.c_int32), ("collect_with_net", C.c_int32)]
+                ("collect_max", C.c_int32), ("collect_with_net", C.c_int32),
+                ("u_bc", C.c_void_p * 3)]
 
 
 class chns_step_stats(C.Structure):

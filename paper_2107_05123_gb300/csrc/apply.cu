@@ -805,6 +805,37 @@ chns_status apply_op(const chns_mesh* m, chns_operator op, const chns_params* pr
   return CHNS_OK;
 }
 
+// The operator K with its Dirichlet rows and columns kept (the lifting of Dirichlet data).
+template <class K>
+struct NoDirK : K {
+  static constexpr bool DIR = false;
+};
+
+chns_status apply_op_full(const chns_mesh* m, chns_operator op, const chns_params* prm,
+                          const chns_coef* coef, const double* x, double* y, cudaStream_t s) {
+  CHNS_CHECK(m && prm && x && y && x != y && (op == CHNS_OP_MASS || op == CHNS_OP_MOMENTUM),
+             CHNS_EINVAL, "apply without Dirichlet rows: bad argument");
+  chns_status st = check_coef(op, coef);
+  if (st != CHNS_OK) return st;
+  const DevParams p = make_dev_params(*prm);
+  CHNS_CUDA(cudaMemsetAsync(y, 0, 3 * m->d.n_nodes * sizeof(double), s));
+  if (op == CHNS_OP_MASS)
+    launch_patch<NoDirK<MassK<double, double>>, double, double, double, false>(
+        m, p, coef_args<double>(coef), x, y, nullptr, s);
+  else
+    launch_patch<NoDirK<MomK<double, double>>, double, double, double, false>(
+        m, p, coef_args<double>(coef), x, y, nullptr, s);
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
+chns_status dirichlet_set(const chns_mesh* m, int nc, const double* x, double* y, cudaStream_t s) {
+  CHNS_CHECK(m && x && y, CHNS_EINVAL, "dirichlet_set: null argument");
+  dirichlet_rows<double>(m, nc, x, y, s);
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
 chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm,
                     const chns_coef* coef, void* d, chns_precision prec, cudaStream_t s) {
   CHNS_CHECK(m && prm && d, CHNS_EINVAL, "diagonal: null argument");

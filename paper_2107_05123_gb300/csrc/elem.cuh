@@ -194,10 +194,13 @@ __device__ __forceinline__ void scatter(const MeshDev& m, const int idx[8], cons
 }
 
 // ---- sum-factorised Q1 kernels
+// o0 = W0 a + W1 b and o1 = W1 a + W0 b, written with W0 = 1 - W1 as a + W1 (b - a) and
+// b - W1 (b - a): one subtraction and two fused multiply-adds.
 template <class T>
 __device__ __forceinline__ void interp1(T a, T b, T& o0, T& o1) {
-  o0 = T(kW0) * a + T(kW1) * b;
-  o1 = T(kW1) * a + T(kW0) * b;
+  const T d = b - a;
+  o0 = a + T(kW1) * d;
+  o1 = b - T(kW1) * d;
 }
 
 // 2D interpolation of 4 values (i0 + 2 i1) to the 4 Gauss points; B symmetric => self-transpose.

@@ -199,6 +199,12 @@ chns_status diag_op(const chns_mesh* m, chns_operator op, const chns_params* prm
 // 2x2 nodal blocks of the CH Jacobian, d4 = [d_pp, d_pm, d_mp, d_mm] x n_nodes (FP64 or FP32)
 chns_status block_diag_ch(const chns_mesh* m, const chns_params* prm, const chns_coef* coef,
                           void* d4, chns_precision prec, cudaStream_t s);
+// y = A x for MASS or MOMENTUM in FP64 without the Dirichlet treatment (boundary rows and columns
+// kept), for lifting Dirichlet data into right-hand sides; y is overwritten.
+chns_status apply_op_full(const chns_mesh* m, chns_operator op, const chns_params* prm,
+                          const chns_coef* coef, const double* x, double* y, cudaStream_t s);
+// y[c N + j] = x[c N + j] for every boundary node j and component c < nc (FP64)
+chns_status dirichlet_set(const chns_mesh* m, int nc, const double* x, double* y, cudaStream_t s);
 int op_ncomp(chns_operator op);
 bool op_dirichlet(chns_operator op);
 // internal operator code of the Krylov context: y = sa M x + sb K x (apply_shift)

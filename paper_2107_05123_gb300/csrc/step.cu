@@ -70,6 +70,29 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
   double* v = ws.v64[11];
   double* bv = ws.v64[12];
   double* un = ws.v64[13];
+  // velocity Dirichlet data (lifted into the velocity right-hand sides): the data, the data on
+  // the boundary rows only, and A applied to that (free between the Newton solves)
+  const bool has_bc = sp->u_bc[0] && sp->u_bc[1] && sp->u_bc[2];
+  CHNS_CHECK(has_bc || (!sp->u_bc[0] && !sp->u_bc[1] && !sp->u_bc[2]), CHNS_EINVAL,
+             "chns_step: give all three velocity Dirichlet arrays or none");
+  double* gfull = ws.v64[9];
+  double* gb = ws.v64[10];
+  double* lw = ws.v64[14];
+  // b <- b - A g_b on the other rows and g on the boundary rows; x0 takes g on the boundary
+  auto lift = [&](chns_operator op, const chns_coef* cf, double* b, double* x0) -> chns_status {
+    for (int d = 0; d < 3; ++d)
+      CHNS_CUDA(cudaMemcpyAsync(gfull + d * N, sp->u_bc[d], N * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+    CHNS_CUDA(cudaMemsetAsync(gb, 0, 3 * N * sizeof(double), s));
+    chns_status r = dirichlet_set(m, 3, gfull, gb, s);
+    if (r != CHNS_OK) return r;
+    r = apply_op_full(m, op, prm, cf, gb, lw, s);
+    if (r != CHNS_OK) return r;
+    lin(1.0, b, -1.0, lw, b, 3 * N, s);
+    r = dirichlet_set(m, 3, gfull, b, s);
+    if (r != CHNS_OK) return r;
+    return dirichlet_set(m, 3, gfull, x0, s);
+  };
   chns_step_stats S{};
   Timer total(s);
   chns_status rc;
@@ -150,6 +173,10 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
       if (rc != CHNS_OK) return rc;
       for (int d = 0; d < 3; ++d)
         CHNS_CUDA(cudaMemcpyAsync(v + d * N, uk[d], N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      if (has_bc) {
+        rc = lift(CHNS_OP_MOMENTUM, &cv, bv, v);
+        if (rc != CHNS_OK) return rc;
+      }
       rc = krylov_solve(m, CHNS_OP_MOMENTUM, prm, &cv, bv, v, &sp->vp, &S.vp[l], s);
       if (rc != CHNS_OK) STEP_FAIL("velocity prediction", rc);
       S.ms_vp += t.stop();
@@ -177,6 +204,10 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
       rc = rhs_vu(m, prm, &cv, vv, uk, st->p, pnew, bv, s);
       if (rc != CHNS_OK) return rc;
       CHNS_CUDA(cudaMemcpyAsync(un, v, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      if (has_bc) {
+        rc = lift(CHNS_OP_MASS, &cv, bv, un);
+        if (rc != CHNS_OK) return rc;
+      }
       rc = krylov_solve(m, CHNS_OP_MASS, prm, &cv, bv, un, &sp->vu, &S.vu[l], s);
       if (rc != CHNS_OK) STEP_FAIL("velocity update", rc);
       S.ms_vu += t.stop();

@@ -71,3 +71,18 @@ class DeviceState:
                     u=np.stack([x.cpu().numpy() for x in self.u]),
                     u_old=np.stack([x.cpu().numpy() for x in self.u_old]),
                     p=self.p.cpu().numpy())
+
+
+class VelocityBC:
+    """Velocity Dirichlet data on the device: three FP64 arrays of n_nodes (only the entries of
+    boundary nodes are read), imposed by chns_step in place of no-slip once attached to the step
+    parameters. The arrays must outlive every step that uses them."""
+
+    def __init__(self, g, device="cuda"):
+        import torch
+        self.g = [torch.as_tensor(np.ascontiguousarray(g[i], dtype=np.float64), device=device)
+                  for i in range(3)]
+
+    def attach(self, sp):
+        sp.u_bc = (capi.C.c_void_p * 3)(*[x.data_ptr() for x in self.g])
+        return sp
