@@ -906,7 +906,9 @@ def run_breakup(args):
     bc = VelocityBC(w.info["velocity_bc"](mesh.node_xyz, 0.0))
     prm = capi.make_params(w.params.as_dict())
     t0 = time.perf_counter()
-    mg_pp = capi.chns_mg_create(mesh.handle, degree=2)
+    # degree-2 smoothing with a 12-step power estimate left the pressure FCG stagnating near
+    # 4e-4 on levels 6-10; degree 3 with a 40-step estimate converges in about 12 iterations
+    mg_pp = capi.chns_mg_create(mesh.handle, degree=3, power_its=40)
     mg_ch = capi.chns_mg_create(mesh.handle, degree=2)
     t_mg = time.perf_counter() - t0
     _say(f"[breakup] {mesh.n_elem} leaves, {N} nodes (octree {t_gen:.1f} s, mesh {t_mesh:.1f} s, "
@@ -952,6 +954,56 @@ def run_breakup(args):
     return out
 
 
+def run_amr(args):
+    """The rising drop (levels 5-8) stepped --steps times in mixed precision with a remesh
+    after every --amr-every steps (band |phi| <= 0.95 on levels 5-8): time per step and per
+    remesh (band flags, new leaves, mesh tables, transfer of the five fields), leaf counts, and
+    the phi mass change of each remesh (the transfer is not mass conserving, Sec. 6.2) beside the
+    steps' own drift."""
+    import torch
+
+    from chns_workloads import configs
+    from paper_2107_05123_gb300 import capi
+    from paper_2107_05123_gb300.session import DeviceState, Mesh, default_step_params, remesh
+
+    w = configs.rising_drop(5, 8)
+    mesh = Mesh(w.anchors, w.levels, w.extent)
+    f0 = w.init(mesh.node_xyz)
+    ds = DeviceState(dict(phi=f0["phi"], mu=f0["mu"], u=f0["u"], p=f0["p"]))
+    prm = capi.make_params(w.params.as_dict())
+    sp = default_step_params(rtol=1e-8, inner=capi.FP32, pp_check_every=8)
+    step_ms, remesh_ms, leaves, remesh_dmass, step_dmass = [], [], [int(mesh.n_elem)], [], []
+    for k in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = capi.chns_step(mesh.handle, ds.c, prm, sp)
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            step_ms.append(e0.elapsed_time(e1))
+            step_dmass.append(st.phi_mass_after - st.phi_mass_before)
+        if (k + 1) % args.amr_every == 0:
+            m0 = capi.chns_phi_mass(mesh.handle, ds.phi)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            new_mesh, new_ds = remesh(mesh, ds, 0.95, 5, 8)
+            torch.cuda.synchronize()
+            dt_ms = (time.perf_counter() - t0) * 1e3
+            m1 = capi.chns_phi_mass(new_mesh.handle, new_ds.phi)
+            mesh.close()
+            mesh, ds = new_mesh, new_ds
+            if k >= args.warmup:
+                remesh_ms.append(dt_ms)
+                remesh_dmass.append(m1 - m0)
+                leaves.append(int(mesh.n_elem))
+    return {"mode": "amr", "workload": "rising_drop_levels5-8", "steps": args.steps,
+            "warmup": args.warmup, "remesh_every": args.amr_every,
+            "ms_per_step": round(statistics.mean(step_ms), 2),
+            "ms_per_remesh": round(statistics.mean(remesh_ms), 1) if remesh_ms else None,
+            "leaves": leaves, "phi_mass_change_per_remesh": remesh_dmass,
+            "phi_mass_change_per_step_max": max(abs(x) for x in step_dmass)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -979,11 +1031,13 @@ def main():
     ap.add_argument("--apply-prec", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--breakup-levels", default="6,9",
                     help="octree levels lmin,lmax of the many-drop breakup workload")
-    ap.add_argument("--mode", choices=["bench", "apply", "pp", "step", "learned", "breakup"],
+    ap.add_argument("--amr-every", type=int, default=2, help="steps between remeshes (amr mode)")
+    ap.add_argument("--mode", choices=["bench", "apply", "pp", "step", "learned", "breakup",
+                                       "amr"],
                     default="bench",
                     help="apply / pp: time only one apply / the pressure solve (profiling); "
                          "learned: only the learned-preconditioner part; breakup: the many-drop "
-                         "breakup workload under shear")
+                         "breakup workload under shear; amr: rising drop with remeshing")
     args = ap.parse_args()
     if args.mode == "apply":
         run_apply_only(args)
@@ -995,6 +1049,8 @@ def main():
         print(json.dumps(run_learned(args)))
     elif args.mode == "breakup":
         print(json.dumps(run_breakup(args)))
+    elif args.mode == "amr":
+        print(json.dumps(run_amr(args)))
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -463,6 +463,39 @@ chns_status chns_learned_train(chns_learned* net, const chns_mesh* mesh, const c
                                int32_t iterations, double lr, uint64_t seed, float* loss_host,
                                void* stream);
 
+/* ------------------------------------------------------------------ adaptive remeshing
+ * One remesh changes every leaf by one level at most and moves the fields from the current mesh
+ * to the new one (Sec. 5.4, "Traversal-based Intergrid Transfers"); the interface band is
+ * |phi| <= threshold (0.95 in the scaling runs, Sec. 7). */
+
+/* Band flags of the leaves (int8, device, n_elem, Morton order): the smallest |phi_h| over the
+ * leaf's 8 corners (hanging corners interpolated) and its centre (the mean of the corners) is
+ * <= threshold: +1 (refine) if the leaf's level is below lmax, else 0; otherwise -1 (coarsening
+ * candidate) if the level is above lmin, else 0. phi: FP64 device, n_nodes.
+ * CHNS_EINVAL for null pointers, 0 <= lmin <= lmax < CHNS_MAXD violated or a non-finite
+ * threshold. */
+chns_status chns_remesh_flags(const chns_mesh* mesh, const double* phi, double threshold,
+                              int32_t lmin, int32_t lmax, int8_t* flags, void* stream);
+/* The leaves of a mesh (host buffers of 3 n_elem anchors and n_elem levels, Morton order). */
+chns_status chns_mesh_leaves(const chns_mesh* mesh, uint32_t* anchors, uint8_t* levels);
+/* A new mesh from the band flags of phi (chns_remesh_flags): +1 leaves are split into their 8
+ * children, the 8 children of one parent that are all leaves and all -1 are merged into it, and
+ * the list is completed to the coarsest 2:1-balanced octree that refines it (balancing only
+ * splits). *out is a new mesh on the same device and extent, owned by the caller
+ * (chns_mesh_destroy); the source mesh is unchanged. Errors as chns_remesh_flags and
+ * chns_mesh_create. */
+chns_status chns_mesh_remesh(const chns_mesh* mesh, const double* phi, double threshold,
+                             int32_t lmin, int32_t lmax, void* stream, chns_mesh** out);
+/* Intergrid transfer: dst[f][j] = the finite-element function src[f] of `from` (hanging
+ * corners through their constraints) evaluated at node j of `to`, for f < n_fields (1..16).
+ * src[f]: FP64 device, from's n_nodes; dst[f]: FP64 device, to's n_nodes, written. On leaves
+ * both meshes share this copies the values, on leaves refined in `to` it interpolates the
+ * parent's shape functions at the child nodes, on leaves coarsened in `to` it injects the
+ * values at the parent's corners. The meshes must cover the same cube on the same device.
+ * A temporary of 8 bytes per leaf of `from` is allocated and freed on the stream. */
+chns_status chns_transfer(const chns_mesh* from, const chns_mesh* to, int32_t n_fields,
+                          const double* const* src, double* const* dst, void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* chns_last_error(void);
 /* Library version string. */

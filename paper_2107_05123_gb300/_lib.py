@@ -154,6 +154,10 @@ _SIGS = {
     "chns_mg_prolong": ([_P, C.c_int32, _P, _P, _P], C.c_int),
     "chns_mg_restrict": ([_P, C.c_int32, _P, _P, _P], C.c_int),
     "chns_mg_coefficient": ([_P, C.c_int32, _P, _P], C.c_int),
+    "chns_remesh_flags": ([_P, _P, C.c_double, C.c_int32, C.c_int32, _P, _P], C.c_int),
+    "chns_mesh_leaves": ([_P, _P, _P], C.c_int),
+    "chns_mesh_remesh": ([_P, _P, C.c_double, C.c_int32, C.c_int32, _P, C.POINTER(_P)], C.c_int),
+    "chns_transfer": ([_P, _P, C.c_int32, _P, _P, _P], C.c_int),
     "chns_last_error": ([], C.c_char_p),
     "chns_version": ([], C.c_char_p),
     "chns_kernel_launches": ([], C.c_uint64),
@@ -239,6 +243,37 @@ def chns_mesh_create(anchors, levels, extent=(1.0, 1.0, 1.0), stream=None):
     _check(LIB.chns_mesh_create(a.ctypes.data, lv.ctypes.data, len(lv), ext, _stream(stream),
                                 C.byref(out)), "chns_mesh_create")
     return out.value
+
+
+def chns_remesh_flags(mesh, phi, threshold, lmin, lmax, flags, stream=None):
+    """flags: int8 device buffer of n_elem."""
+    _check(LIB.chns_remesh_flags(mesh, _ptr(phi), float(threshold), int(lmin), int(lmax),
+                                 _ptr(flags), _stream(stream)), "chns_remesh_flags")
+
+
+def chns_mesh_leaves(mesh, n_elem):
+    """(anchors (n_elem, 3) uint32, levels (n_elem,) uint8) of a mesh, Morton order."""
+    a = np.zeros((n_elem, 3), dtype=np.uint32)
+    lv = np.zeros(n_elem, dtype=np.uint8)
+    _check(LIB.chns_mesh_leaves(mesh, a.ctypes.data, lv.ctypes.data), "chns_mesh_leaves")
+    return a, lv
+
+
+def chns_mesh_remesh(mesh, phi, threshold, lmin, lmax, stream=None):
+    out = C.c_void_p()
+    _check(LIB.chns_mesh_remesh(mesh, _ptr(phi), float(threshold), int(lmin), int(lmax),
+                                _stream(stream), C.byref(out)), "chns_mesh_remesh")
+    return out.value
+
+
+def chns_transfer(src_mesh, dst_mesh, src, dst, stream=None):
+    """src, dst: equal-length lists of FP64 device buffers (src_mesh / dst_mesh n_nodes)."""
+    n = len(src)
+    if n != len(dst):
+        raise ValueError("chns_transfer: src and dst differ in length")
+    sp = (C.c_void_p * n)(*[_ptr(x) for x in src])
+    dp = (C.c_void_p * n)(*[_ptr(x) for x in dst])
+    _check(LIB.chns_transfer(src_mesh, dst_mesh, n, sp, dp, _stream(stream)), "chns_transfer")
 
 
 def chns_mesh_get_info(mesh) -> chns_mesh_info:

@@ -10,8 +10,12 @@ from . import _lib as capi
 class Mesh:
     """Owns a chns_mesh built from a Morton-ordered, 2:1-balanced leaf list."""
 
-    def __init__(self, anchors, levels, extent=(1.0, 1.0, 1.0), stream=None):
-        self.handle = capi.chns_mesh_create(anchors, levels, extent, stream)
+    def __init__(self, anchors=None, levels=None, extent=(1.0, 1.0, 1.0), stream=None,
+                 handle=None):
+        """From a leaf list, or (handle=) taking ownership of a mesh the library created."""
+        if handle is None:
+            handle = capi.chns_mesh_create(anchors, levels, extent, stream)
+        self.handle = handle
         info = capi.chns_mesh_get_info(self.handle)
         self.n_elem = info.n_elem
         self.n_nodes = info.n_nodes
@@ -22,6 +26,10 @@ class Mesh:
         self.node_int = capi.chns_mesh_node_coords(self.handle, self.n_nodes)
         self.boundary = capi.chns_mesh_boundary(self.handle, self.n_nodes).astype(bool)
         self.node_xyz = self.node_int.astype(np.float64) / float(1 << capi.MAXD) * self.extent
+
+    def leaves(self):
+        """(anchors, levels) of the mesh in Morton order."""
+        return capi.chns_mesh_leaves(self.handle, self.n_elem)
 
     def close(self):
         if self.handle:
@@ -61,6 +69,9 @@ class DeviceState:
         uo = fields.get("u_old", fields["u"])
         self.u_old = [t(uo[i]) for i in range(3)]
         self.p = t(fields["p"])
+        self._bind()
+
+    def _bind(self):
         self.c = capi.chns_state(self.phi.data_ptr(), self.mu.data_ptr(),
                                  (capi.C.c_void_p * 3)(*[x.data_ptr() for x in self.u]),
                                  (capi.C.c_void_p * 3)(*[x.data_ptr() for x in self.u_old]),
@@ -86,3 +97,25 @@ class VelocityBC:
     def attach(self, sp):
         sp.u_bc = (capi.C.c_void_p * 3)(*[x.data_ptr() for x in self.g])
         return sp
+
+
+def remesh(mesh: Mesh, ds: "DeviceState", threshold=0.95, lmin=None, lmax=None, stream=None):
+    """One adaptive remesh (Sec. 5.4): the new mesh from the interface band of ds.phi and every
+    field of ds (phi, mu, u, u_old, p) transferred to it. Returns (new Mesh, new DeviceState);
+    the old ones are left unchanged."""
+    import torch
+    lmin = mesh.min_level if lmin is None else lmin
+    lmax = mesh.max_level if lmax is None else lmax
+    new_mesh = Mesh(handle=capi.chns_mesh_remesh(mesh.handle, ds.phi, threshold, lmin, lmax,
+                                                 stream))
+    n = new_mesh.n_nodes
+    z = lambda: torch.empty(n, dtype=torch.float64, device=ds.phi.device)
+    new = DeviceState.__new__(DeviceState)
+    new.phi, new.mu, new.p = z(), z(), z()
+    new.u = [z() for _ in range(3)]
+    new.u_old = [z() for _ in range(3)]
+    capi.chns_transfer(mesh.handle, new_mesh.handle,
+                       [ds.phi, ds.mu, *ds.u, *ds.u_old, ds.p],
+                       [new.phi, new.mu, *new.u, *new.u_old, new.p], stream)
+    new._bind()
+    return new_mesh, new
