@@ -739,6 +739,8 @@ def cpu_baseline(budget_s=60.0):
             timings["smooth_uniform_level4"] = {"n_nodes": int(osm.n_nodes),
                                                 "full_step_s": round(time.perf_counter() - ta, 2)}
         timings[WORKLOAD] = "skipped: memory (assembled matrices of 6.9e6 elements, ~10 GB)"
+        timings["breakup64_levels6-10"] = ("skipped: memory (2.8e7 elements: ~40 GB of assembled "
+                                           "matrices per scalar operator)")
     except Exception as e:  # the baseline value above stands
         timings["error"] = f"{type(e).__name__}: {e}"
     out["oracle_timings"] = timings

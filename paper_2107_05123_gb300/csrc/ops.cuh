@@ -302,17 +302,17 @@ struct VmsQ {
   T rho, eta, a0, b[3], bp[3], e, t[3], tau, uq[3], J[3], ge[3], gphi[3];
 };
 
-template <int Q, class T>
-__device__ __forceinline__ VmsQ<T> vms_at(const T pe[8], const T ue[3][8], const T me[8],
-                                          const Geo<T>& g, const DevParams& p) {
+// The coefficients at one point from the point values of phi~ (pv, grad gp), grad mu~ (mg) and
+// u_hat (uq).
+template <class T>
+__device__ __forceinline__ VmsQ<T> vms_point(T pv, const T gp[3], const T mg[3], const T uq[3],
+                                             const Geo<T>& g, const DevParams& p) {
   VmsQ<T> o;
-  T pv, mv;
-  vg_at<Q>(pe, g, pv, o.gphi);
-  T mg[3];
-  vg_at<Q>(me, g, mv, mg);
-  (void)mv;
 #pragma unroll
-  for (int d = 0; d < 3; ++d) o.uq[d] = val_at<Q>(ue[d]);
+  for (int d = 0; d < 3; ++d) {
+    o.gphi[d] = gp[d];
+    o.uq[d] = uq[d];
+  }
   const PrmT<T>& k = p.get<T>();
   T pc = clamp1(pv);
   o.rho = k.alpha * pc + k.beta;
@@ -348,6 +348,33 @@ __device__ __forceinline__ VmsQ<T> vms_at(const T pe[8], const T ue[3][8], const
   }
   return o;
 }
+
+template <int Q, class T>
+__device__ __forceinline__ VmsQ<T> vms_at(const T pe[8], const T ue[3][8], const T me[8],
+                                          const Geo<T>& g, const DevParams& p) {
+  T pv, mv, gp[3], mg[3], uq[3];
+  vg_at<Q>(pe, g, pv, gp);
+  vg_at<Q>(me, g, mv, mg);
+  (void)mv;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) uq[d] = val_at<Q>(ue[d]);
+  return vms_point(pv, gp, mg, uq, g, p);
+}
+
+// A field at the 8 Gauss points by sum factorisation: values (interp3) and the compact
+// per-axis gradient data (grad_compact); grad(q, d) is the physical derivative d/dx_d at q.
+template <class T>
+struct QpField {
+  T v[8], gx[4], gy[4], gz[4];
+  __device__ __forceinline__ void eval(const T u[8]) {
+    interp3(u, v);
+    grad_compact(u, gx, gy, gz);
+  }
+  __device__ __forceinline__ void eval_grad(const T u[8]) { grad_compact(u, gx, gy, gz); }
+  __device__ __forceinline__ T grad(int q, int d, const Geo<T>& g) const {
+    return d == 0 ? gx[gxi(q)] * g.ih[0] : d == 1 ? gy[gyi(q)] * g.ih[1] : gz[gzi(q)] * g.ih[2];
+  }
+};
 
 template <class T, class C>
 struct MomK {
@@ -423,9 +450,23 @@ k_mom_qdata(MeshDev m, DevParams p, CoefArgs<C> cf, T* __restrict__ qd) {
   MomK<T, C> k;
   k.load(m, p, cf, idx, g);
   const int64_t E = m.n_elem;
+  // the fields at the Gauss points by sum factorisation
+  QpField<T> fp, fm;
+  fp.eval(k.pe);
+  fm.eval_grad(k.me);
+  T uq[3][8];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) interp3(k.ue[d], uq[d]);
   for_qp([&](auto QC) {
     constexpr int Q = decltype(QC)::value;
-    const VmsQ<T> c = vms_at<Q>(k.pe, k.ue, k.me, g, p);
+    T gp[3], mg[3], uv[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      gp[d] = fp.grad(Q, d, g);
+      mg[d] = fm.grad(Q, d, g);
+      uv[d] = uq[d][Q];
+    }
+    const VmsQ<T> c = vms_point(fp.v[Q], gp, mg, uv, g, p);
     T* q = qd + (int64_t)Q * kMomQ * E + e;
     q[0] = c.a0;
 #pragma unroll

@@ -100,6 +100,14 @@ __device__ __forceinline__ void forcing_at(const double pe[8], const Geo<double>
 //   (w, rho u_i/dt) - 1/2 (w, rho u.grad u_i) - 1/(2Pe) (w, J.grad u_i) - 1/(2Re) (grad w, eta grad u_i)
 //   + Cn/We (d_j w, d_i phi d_j phi) - (w, d_i p) + (w, rho g_i/Fr) - (grad w . t, R0_i)
 // with R0_i the part of R_m that does not depend on v^{k+1}.
+// Sum-factorised: every field's values and gradients at the 8 Gauss points come from interp3 /
+// grad_compact, the per-point coefficients (tau_m and the advection and stabilisation vectors)
+// are formed once per point, and each component's test-function sums are the transposes interp3
+// and grad_T of its per-point terms.
+struct MomPt {  // per-point data shared by the three components
+  double a0, b[3], bp[3], e, t[3], rho, gphi[3], F[3], pg[3];
+};
+
 __global__ void __launch_bounds__(kRhsThreads)
 k_rhs_momentum(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 uk,
                const double* __restrict__ pk, double* __restrict__ b) {
@@ -108,67 +116,148 @@ k_rhs_momentum(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 uk,
   int idx[8];
   load_corners(m, e, idx);
   const Geo<double> g = geometry<double>(m, e);
-  double pe[8], ue[3][8], me[8], pp[8];
-  gather<double, false>(m, idx, cf.phi, pe);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) gather<double, false>(m, idx, cf.u[d], ue[d]);
-  gather<double, false>(m, idx, cf.mu, me);
-  gather<double, false>(m, idx, pk, pp);
   const double J = g.detJ, cw = p.d.cw;
-  // the quadrature-point coefficients (tau_m, the advection and stabilisation vectors, the
-  // forcing) are the same for the three components: computed once per point
-  double ui[3][8], r[3][8] = {{0}};
+  MomPt c[8];
+  {
+    double pe[8], ue[3][8], me[8], pp[8];
+    gather<double, false>(m, idx, cf.phi, pe);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) gather<double, false>(m, idx, uk.c[i], ui[i]);
-  for_qp([&](auto QC) {
-    constexpr int Q = decltype(QC)::value;
-    VmsQ<double> c = vms_at<Q>(pe, ue, me, g, p);
-    double F[3];
-    forcing_at<Q>(pe, g, c.gphi, F);
-    double pv, pg[3];
-    vg_at<Q>(pp, g, pv, pg);
+    for (int d = 0; d < 3; ++d) gather<double, false>(m, idx, cf.u[d], ue[d]);
+    gather<double, false>(m, idx, cf.mu, me);
+    gather<double, false>(m, idx, pk, pp);
+    QpField<double> fp, fm, fr;
+    fp.eval(pe);
+    fm.eval_grad(me);
+    fr.eval_grad(pp);
+    double uq[3][8];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) interp3(ue[d], uq[d]);
+    for_qp([&](auto QC) {
+      constexpr int Q = decltype(QC)::value;
+      double gp[3], mg[3], uv[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        gp[d] = fp.grad(Q, d, g);
+        mg[d] = fm.grad(Q, d, g);
+        uv[d] = uq[d][Q];
+      }
+      const VmsQ<double> v = vms_point(fp.v[Q], gp, mg, uv, g, p);
+      MomPt& o = c[Q];
+      o.a0 = v.a0;
+      o.e = v.e;
+      o.rho = v.rho;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        o.b[d] = v.b[d];
+        o.bp[d] = v.bp[d];
+        o.t[d] = v.t[d];
+        o.gphi[d] = v.gphi[d];
+        o.pg[d] = fr.grad(Q, d, g);
+      }
+      forcing_at<Q>(pe, g, v.gphi, o.F);
+    });
+  }
 #pragma unroll 1
-    for (int i = 0; i < 3; ++i) {
-      double v, vg[3];
-      vg_at<Q>(ui[i], g, v, vg);
-      const double grav = c.rho * ghat(i) * p.d.inv_fr;
-      double bdot = c.b[0] * vg[0] + c.b[1] * vg[1] + c.b[2] * vg[2];
-      double bpdot = c.bp[0] * vg[0] + c.bp[1] * vg[1] + c.bp[2] * vg[2];
-      double r0 = -c.a0 * v + bpdot + cw * F[i] + pg[i] - grav;
-      double fn = c.a0 * v - bdot - pg[i] + grav;
-      double V[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) V[d] = J * (-c.e * vg[d] + cw * c.gphi[i] * c.gphi[d] - c.t[d] * r0);
-      add_test<Q>(r[i], J * fn, V, g);
-    }
-  });
-#pragma unroll
-  for (int i = 0; i < 3; ++i) scatter<double, true>(m, idx, r[i], b + i * m.n_nodes);
-}
-
-// Full R_m,i(v) at Q (Def. of R_m) with v~ = (v + u_k)/2.
-template <int Q>
-__device__ __forceinline__ void rm_at(const VmsQ<double>& c, const DevParams& p, const double F[3],
-                                      const double pg[3], const double ve[3][8],
-                                      const double ue[3][8], const Geo<double>& g, double R[3],
-                                      double vq[3], double& div) {
-  div = 0.0;
   for (int i = 0; i < 3; ++i) {
-    double vv, vgr[3], uv, ug[3];
-    vg_at<Q>(ve[i], g, vv, vgr);
-    vg_at<Q>(ue[i], g, uv, ug);
-    div += vgr[i];
-    vq[i] = vv;
-    double tg[3];
+    double ui[8];
+    gather<double, false>(m, idx, uk.c[i], ui);
+    QpField<double> fu;
+    fu.eval(ui);
+    double s[8], V[3][8];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) tg[d] = 0.5 * (vgr[d] + ug[d]);
-    double adv = c.uq[0] * tg[0] + c.uq[1] * tg[1] + c.uq[2] * tg[2];
-    double jdv = c.J[0] * tg[0] + c.J[1] * tg[1] + c.J[2] * tg[2];
-    double edv = c.ge[0] * tg[0] + c.ge[1] * tg[1] + c.ge[2] * tg[2];
-    R[i] = c.rho * (vv - uv) * p.d.idt + c.rho * adv + jdv * p.d.inv_pe + p.d.cw * F[i] + pg[i] -
-           edv * p.d.inv_re - c.rho * ghat(i) * p.d.inv_fr;
+    for (int q = 0; q < 8; ++q) {
+      const MomPt& o = c[q];
+      const double v = fu.v[q];
+      const double vg[3] = {fu.grad(q, 0, g), fu.grad(q, 1, g), fu.grad(q, 2, g)};
+      const double grav = o.rho * ghat(i) * p.d.inv_fr;
+      const double bdot = o.b[0] * vg[0] + o.b[1] * vg[1] + o.b[2] * vg[2];
+      const double bpdot = o.bp[0] * vg[0] + o.bp[1] * vg[1] + o.bp[2] * vg[2];
+      const double r0 = -o.a0 * v + bpdot + cw * o.F[i] + o.pg[i] - grav;
+      const double fn = o.a0 * v - bdot - o.pg[i] + grav;
+      s[q] = J * fn;
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        V[d][q] = J * (-o.e * vg[d] + cw * o.gphi[i] * o.gphi[d] - o.t[d] * r0);
+    }
+    double r[8];
+    interp3(s, r);
+    grad_T(V, g, r);
+    scatter<double, true>(m, idx, r, b + i * m.n_nodes);
   }
 }
+
+// Full R_m,i(v) at a point (Def. of R_m) with v~ = (v + u_k)/2, from the point values vv and
+// gradients vgr of v and ug of u_k (uv: u_k's values).
+__device__ __forceinline__ void rm_point(const VmsQ<double>& c, const DevParams& p,
+                                         const double F[3], const double pg[3],
+                                         const double vv[3], const double vgr[3][3],
+                                         const double uv[3], const double ug[3][3], double R[3],
+                                         double& div) {
+  div = vgr[0][0] + vgr[1][1] + vgr[2][2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double tg[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) tg[d] = 0.5 * (vgr[i][d] + ug[i][d]);
+    const double adv = c.uq[0] * tg[0] + c.uq[1] * tg[1] + c.uq[2] * tg[2];
+    const double jdv = c.J[0] * tg[0] + c.J[1] * tg[1] + c.J[2] * tg[2];
+    const double edv = c.ge[0] * tg[0] + c.ge[1] * tg[1] + c.ge[2] * tg[2];
+    R[i] = c.rho * (vv[i] - uv[i]) * p.d.idt + c.rho * adv + jdv * p.d.inv_pe + p.d.cw * F[i] +
+           pg[i] - edv * p.d.inv_re - c.rho * ghat(i) * p.d.inv_fr;
+  }
+}
+
+// The fields of the pressure-Poisson and velocity-update right-hand sides at the 8 Gauss points.
+struct ProjFields {
+  QpField<double> fp, fm, fr, fv[3], fu[3];
+  double uq[3][8];
+  __device__ __forceinline__ void load(const MeshDev& m, const int idx[8],
+                                       const CoefArgs<double>& cf, const Ptr3& v, const Ptr3& uk,
+                                       const double* pk, double pe[8]) {
+    double t[8];
+    gather<double, false>(m, idx, cf.phi, pe);
+    fp.eval(pe);
+    gather<double, false>(m, idx, cf.mu, t);
+    fm.eval_grad(t);
+    gather<double, false>(m, idx, pk, t);
+    fr.eval_grad(t);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      gather<double, false>(m, idx, cf.u[d], t);
+      interp3(t, uq[d]);
+      gather<double, false>(m, idx, v.c[d], t);
+      fv[d].eval(t);
+      gather<double, false>(m, idx, uk.c[d], t);
+      fu[d].eval(t);
+    }
+  }
+  // the coefficients, forcing, grad p_k and R_m at point Q
+  template <int Q>
+  __device__ __forceinline__ VmsQ<double> at(const double pe[8], const Geo<double>& g,
+                                             const DevParams& p, double pg[3], double R[3],
+                                             double vv[3], double& div) const {
+    double gp[3], mg[3], uv0[3], vgr[3][3], ug[3][3], uv[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      gp[d] = fp.grad(Q, d, g);
+      mg[d] = fm.grad(Q, d, g);
+      uv0[d] = uq[d][Q];
+      pg[d] = fr.grad(Q, d, g);
+      vv[d] = fv[d].v[Q];
+      uv[d] = fu[d].v[Q];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        vgr[d][k] = fv[d].grad(Q, k, g);
+        ug[d][k] = fu[d].grad(Q, k, g);
+      }
+    }
+    const VmsQ<double> c = vms_point(fp.v[Q], gp, mg, uv0, g, p);
+    double F[3];
+    forcing_at<Q>(pe, g, c.gphi, F);
+    rm_point(c, p, F, pg, vv, vgr, uv, ug, R, div);
+    return c;
+  }
+};
 
 // ---- pressure-Poisson right-hand side (Def. weak_VMS_disc_pp_vel, scalar test q):
 //   -(2/dt)(q, div v) - (2/dt)(grad q, tau R_m / rho~) + (grad q, grad p_k / rho~)
@@ -180,30 +269,23 @@ k_rhs_poisson(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 v, Ptr3 uk,
   int idx[8];
   load_corners(m, e, idx);
   const Geo<double> g = geometry<double>(m, e);
-  double pe[8], ue[3][8], me[8], pp[8], ve[3][8], uke[3][8];
-  gather<double, false>(m, idx, cf.phi, pe);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    gather<double, false>(m, idx, cf.u[d], ue[d]);
-    gather<double, false>(m, idx, v.c[d], ve[d]);
-    gather<double, false>(m, idx, uk.c[d], uke[d]);
-  }
-  gather<double, false>(m, idx, cf.mu, me);
-  gather<double, false>(m, idx, pk, pp);
-  double r[8] = {0};
+  double pe[8];
+  ProjFields f;
+  f.load(m, idx, cf, v, uk, pk, pe);
   const double J = g.detJ, k2 = p.d.k2dt;
+  double s[8], V[3][8];
   for_qp([&](auto QC) {
     constexpr int Q = decltype(QC)::value;
-    VmsQ<double> c = vms_at<Q>(pe, ue, me, g, p);
-    double F[3], pv, pg[3], R[3], vq[3], div;
-    forcing_at<Q>(pe, g, c.gphi, F);
-    vg_at<Q>(pp, g, pv, pg);
-    rm_at<Q>(c, p, F, pg, ve, uke, g, R, vq, div);
-    double V[3];
+    double pg[3], R[3], vv[3], div;
+    const VmsQ<double> c = f.at<Q>(pe, g, p, pg, R, vv, div);
+    const double ir = 1.0 / c.rho;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) V[d] = J * (-k2 * c.tau * R[d] + pg[d]) / c.rho;
-    add_test<Q>(r, J * (-k2 * div), V, g);
+    for (int d = 0; d < 3; ++d) V[d][Q] = J * (-k2 * c.tau * R[d] + pg[d]) * ir;
+    s[Q] = J * (-k2 * div);
   });
+  double r[8];
+  interp3(s, r);
+  grad_T(V, g, r);
   scatter<double, false>(m, idx, r, b);
 }
 
@@ -217,34 +299,34 @@ k_rhs_vu(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 v, Ptr3 uk,
   int idx[8];
   load_corners(m, e, idx);
   const Geo<double> g = geometry<double>(m, e);
-  double pe[8], ue[3][8], me[8], pp[8], dpe[8], ve[3][8], uke[3][8];
-  gather<double, false>(m, idx, cf.phi, pe);
+  double pe[8];
+  ProjFields f;
+  f.load(m, idx, cf, v, uk, pk, pe);
+  QpField<double> fd;  // p_new - p_k
+  {
+    double a[8], c0[8];
+    gather<double, false>(m, idx, pn, a);
+    gather<double, false>(m, idx, pk, c0);
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    gather<double, false>(m, idx, cf.u[d], ue[d]);
-    gather<double, false>(m, idx, v.c[d], ve[d]);
-    gather<double, false>(m, idx, uk.c[d], uke[d]);
+    for (int k = 0; k < 8; ++k) a[k] -= c0[k];
+    fd.eval_grad(a);
   }
-  gather<double, false>(m, idx, cf.mu, me);
-  gather<double, false>(m, idx, pk, pp);
-  gather<double, false>(m, idx, pn, dpe);
-#pragma unroll
-  for (int a = 0; a < 8; ++a) dpe[a] -= pp[a];
-  double r[3][8] = {{0}};
   const double J = g.detJ;
+  double s[3][8];
   for_qp([&](auto QC) {
     constexpr int Q = decltype(QC)::value;
-    VmsQ<double> c = vms_at<Q>(pe, ue, me, g, p);
-    double F[3], pv, pg[3], R[3], vq[3], div, dv, dg[3];
-    forcing_at<Q>(pe, g, c.gphi, F);
-    vg_at<Q>(pp, g, pv, pg);
-    rm_at<Q>(c, p, F, pg, ve, uke, g, R, vq, div);
-    vg_at<Q>(dpe, g, dv, dg);
-    const double V0[3] = {0.0, 0.0, 0.0};
+    double pg[3], R[3], vv[3], div;
+    const VmsQ<double> c = f.at<Q>(pe, g, p, pg, R, vv, div);
+#pragma unroll
     for (int i = 0; i < 3; ++i)
-      add_test<Q>(r[i], J * (c.rho * vq[i] - c.tau * R[i] - p.d.half_dt * dg[i]), V0, g);
+      s[i][Q] = J * (c.rho * vv[i] - c.tau * R[i] - p.d.half_dt * fd.grad(Q, i, g));
   });
-  for (int i = 0; i < 3; ++i) scatter<double, true>(m, idx, r[i], b + i * m.n_nodes);
+#pragma unroll 1
+  for (int i = 0; i < 3; ++i) {
+    double r[8];
+    interp3(s[i], r);
+    scatter<double, true>(m, idx, r, b + i * m.n_nodes);
+  }
 }
 
 // ---- phi mass: sum_e detJ sum_q phi(q) = sum_e detJ sum_a phi_a (2-point Gauss weights sum to 1
