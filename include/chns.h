@@ -254,6 +254,8 @@ typedef struct {
   chns_learned* learned;    /* CHNS_PC_LEARNED: the network (not owned); else ignored */
   int32_t inner_its;        /* CHNS_PC_SCHUR: CG iterations of each inner solve with H (0: 20) */
   chns_mg* mg;              /* CHNS_PC_MULTIGRID: the hierarchy of this mesh (not owned) */
+  int32_t mass_its;         /* CHNS_PC_SCHUR: Jacobi-CG iterations of each M^-1 (0: the larger of
+                             * 4 and inner_its / 4) */
 } chns_solver_params;
 
 typedef struct {

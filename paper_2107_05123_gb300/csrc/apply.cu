@@ -358,6 +358,12 @@ k_apply_stream(MeshDev m, DevParams p, CoefArgs<T> cf, const T* __restrict__ x, 
   __syncthreads();
   if (pid < np) issue_stage(0, 0, 0);
   cp_async_commit();
+  // Without Dirichlet rows or the fused CG update the regular slots need no pass of their own:
+  // the accumulators are cleared once here and then by the passes that read them (4 and 5), so
+  // that every slot is zero again when the next patch starts.
+  constexpr bool ZERO_IN_PLACE = !K::DIR && !CGP;
+  if constexpr (ZERO_IN_PLACE)
+    for (int i = tid; i < NC * kPatchSlots; i += kPatchElems) ys[i] = T(0);
   typename Acc<T>::type en[1] = {Acc<T>::zero()};
   for (int k = 0; pid < np; pid += G, ++k) {
     const int st = k & 1, bc = k % 3, rc = k & 3;
@@ -376,21 +382,23 @@ k_apply_stream(MeshDev m, DevParams p, CoefArgs<T> cf, const T* __restrict__ x, 
     const ushort4* pq = pqb + st * kPqStage;
     auto parents = [&](int i) { return i - nreg < kPqStage ? pq[i - nreg] : m.slot_par[s0 + i]; };
     // 1. regular slots: CG direction update, Dirichlet zeros, accumulators cleared
-    for (int i = tid; i < nreg; i += kPatchElems) {
-      const int32_t v = ic[i];
-      const bool dir = K::DIR && (v & kDirBit);
+    if constexpr (!ZERO_IN_PLACE) {
+      for (int i = tid; i < nreg; i += kPatchElems) {
+        const int32_t v = ic[i];
+        const bool dir = K::DIR && (v & kDirBit);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        T xv = xs[c * kPatchSlots + i];
-        if (CGP) {
-          xv = zs[c * kPatchSlots + i] + s_beta * xv;
-          (pout + c * N)[v & kNodeMask] = xv;  // patches sharing the node store the same value
+        for (int c = 0; c < NC; ++c) {
+          T xv = xs[c * kPatchSlots + i];
+          if (CGP) {
+            xv = zs[c * kPatchSlots + i] + s_beta * xv;
+            (pout + c * N)[v & kNodeMask] = xv;  // patches sharing the node store the same value
+          }
+          xs[c * kPatchSlots + i] = dir ? T(0) : xv;
+          ys[c * kPatchSlots + i] = T(0);
         }
-        xs[c * kPatchSlots + i] = dir ? T(0) : xv;
-        ys[c * kPatchSlots + i] = T(0);
       }
+      __syncthreads();
     }
-    __syncthreads();
     // 2. hanging slots
     for (int i = nreg + tid; i < ns; i += kPatchElems) {
       const ushort4 q = parents(i);
@@ -402,7 +410,7 @@ k_apply_stream(MeshDev m, DevParams p, CoefArgs<T> cf, const T* __restrict__ x, 
         T v = a[q.x] + a[q.y];
         if (four) v += a[q.z] + a[q.w];
         xs[c * kPatchSlots + i] = w * v;
-        ys[c * kPatchSlots + i] = T(0);
+        if (!ZERO_IN_PLACE) ys[c * kPatchSlots + i] = T(0);
       }
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
@@ -457,6 +465,7 @@ k_apply_stream(MeshDev m, DevParams p, CoefArgs<T> cf, const T* __restrict__ x, 
       for (int c = 0; c < NC; ++c) {
         T* a = ys + c * kPatchSlots;
         const T v = w * a[i];
+        if (ZERO_IN_PLACE) a[i] = T(0);
         atomicAdd(a + q.x, v);
         atomicAdd(a + q.y, v);
         if (four) {
@@ -474,6 +483,7 @@ k_apply_stream(MeshDev m, DevParams p, CoefArgs<T> cf, const T* __restrict__ x, 
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const T val = ys[c * kPatchSlots + i];
+        if (ZERO_IN_PLACE) ys[c * kPatchSlots + i] = T(0);
         T* yc = y + c * N;
         if (v & kOwnBit)
           yc[g] = val;

@@ -21,7 +21,7 @@ constexpr int32_t kNodeMask = kOwnBit - 1;
 // A patch is a run of Morton-consecutive elements processed by one CTA (one thread per element)
 // whose distinct nodes (regular nodes and hanging corners) fit in kPatchSlots shared slots.
 constexpr int kPatchElems = 256;
-constexpr int kPatchSlots = 1024;
+constexpr int kPatchSlots = 640;
 // Per element of a patch, eloc holds its 8 corner slots as uint16; slots are < kPatchSlots, so the
 // first entry also carries the element's level in bits 10-14.
 constexpr uint32_t kElocSlotMask = 0x3ff;

@@ -860,12 +860,13 @@ struct SchurPC {
   chns_mg* mg = nullptr;  // when set, each H^-1 is one V-cycle of the shifted operator H
 
   // contexts and diagonals; vec: >= 10 scratch N-vectors
-  chns_status setup(const Ctx& c, T* const* vec, int inner_its, chns_mg* hier = nullptr) {
+  chns_status setup(const Ctx& c, T* const* vec, int inner_its, chns_mg* hier = nullptr,
+                    int mass_its = 0) {
     const int64_t N = c.m->d.n_nodes;
     const double dt = c.prm->dt, Pe = c.prm->Pe, Cn = c.prm->Cn;
     const double kmu = 0.5 / (Pe * Cn), kphi = 0.5 * Cn * Cn;
     itH = inner_its > 0 ? inner_its : 20;
-    itM = std::max(4, itH / 4);
+    itM = mass_its > 0 ? mass_its : std::max(4, itH / 4);
     cM = c;
     cM.op = kOpShift;
     cM.n = N;
@@ -1209,8 +1210,10 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
   // 2 n_nodes in the basis buffer of (CHNS_GMRES_MAX_RESTART + 1) x 3 n_nodes
   CHNS_CHECK(sp->pc != CHNS_PC_SCHUR ||
                  (op == CHNS_OP_CH && sp->ksp == CHNS_KSP_GMRES && sp->inner_its >= 0 &&
+                  sp->mass_its >= 0 &&
                   2 * (2 * sp->restart + 1) <= 3 * (CHNS_GMRES_MAX_RESTART + 1)),
-             CHNS_EINVAL, "Schur preconditioner: CH operator, GMRES, restart <= 30, inner_its >= 0");
+             CHNS_EINVAL,
+             "Schur preconditioner: CH operator, GMRES, restart <= 30, inner_its and mass_its >= 0");
   CHNS_CHECK(sp->pc != CHNS_PC_CHEBYSHEV ||
                  (op == CHNS_OP_POISSON && sp->ksp != CHNS_KSP_GMRES && sp->restart >= 1 &&
                   sp->restart <= 16),
@@ -1302,7 +1305,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
       if (!spc64_ok) {
         double* vec[12];
         for (int k = 0; k < 12; ++k) vec[k] = ws.v64[3 + k / 3] + (k % 3) * Nn;
-        *err = spc64.setup(c, vec, sp->inner_its, sp->mg);
+        *err = spc64.setup(c, vec, sp->inner_its, sp->mg, sp->mass_its);
         if (*err != CHNS_OK) return nullptr;
         spc64_ok = true;
       }
@@ -1534,7 +1537,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
           if (schur && !spc32_ok) {
             float* vec[12];
             for (int k = 0; k < 12; ++k) vec[k] = ws.v32[3 + k / 3] + (k % 3) * Nn;
-            st = spc32.setup(c, vec, sp->inner_its, sp->mg);
+            st = spc32.setup(c, vec, sp->inner_its, sp->mg, sp->mass_its);
             if (st != CHNS_OK) return st;
             spc32_ok = true;
           }

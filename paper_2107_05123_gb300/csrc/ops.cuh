@@ -89,7 +89,7 @@ struct PoissonK {
   // CTAs of the patch apply resident per SM that the register allocation must allow (FP32: 6,
   // i.e. at most 42 registers; FP64: 3)
   static constexpr int MIN_CTAS = sizeof(T) == 4 ? 6 : 3;
-  static constexpr int STREAM_CTAS = sizeof(T) == 4 ? 5 : 0;  // persistent apply (0: not used)
+  static constexpr int STREAM_CTAS = sizeof(T) == 4 ? 6 : 0;  // persistent apply (0: not used)
   static constexpr int NC = 1;
   static constexpr bool DIR = false;
   static constexpr bool DIAG_PER_COMP = false;
@@ -165,41 +165,81 @@ template <class T, class C>
 struct ShiftK {
   static constexpr bool QDATA = false;
   static constexpr int MIN_CTAS = sizeof(T) == 4 ? 6 : 3;
-  static constexpr int STREAM_CTAS = sizeof(T) == 4 ? 5 : 0;  // persistent apply (FP32)
+  static constexpr int STREAM_CTAS = sizeof(T) == 4 ? 6 : 0;  // persistent apply (FP32)
   static constexpr int NC = 1;
   static constexpr bool DIR = false;
   static constexpr bool DIAG_PER_COMP = false;
   static constexpr int NF = 1;  // (phi~ gathered but unused: the patch kernel's layout)
-  T cm, ck[8];
+  // Constant coefficients on a box: the 2x2x2 Gauss rule is exact, and the element matrices are
+  // Kronecker products of the 1D Q1 matrices m = h/6 [[2, 1], [1, 2]] and k = 1/h [[1, -1],
+  // [-1, 1]]: M_e = m x m x m, K_e = k x m x m + m x k x m + m x m x k. With P(a, b) = (2a + b,
+  // a + 2b) and D(a, b) = (a - b, b - a) along one axis and V = h_x h_y h_z,
+  //   y = sa M_e x + sb K_e x = Px (cm B + cy C + cz E) + cx Dx B,
+  //   B = Py Pz x, C = Dy Pz x, E = Py Dz x, cm = sa V / 216, c_d = sb V / (36 h_d^2).
+  T cm, cx, cy, cz;
   __device__ __forceinline__ void setup(const T[NF][8], const Geo<T>& g, const DevParams& p) {
     const PrmT<T>& k = p.get<T>();
-    cm = k.sa * g.detJ;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) ck[q] = k.sb * g.detJ;
+    const T V = T(8) * g.detJ;
+    cm = k.sa * V * T(1.0 / 216.0);
+    const T ks = k.sb * V * T(1.0 / 36.0);
+    cx = ks * g.ih[0] * g.ih[0];
+    cy = ks * g.ih[1] * g.ih[1];
+    cz = ks * g.ih[2] * g.ih[2];
   }
   __device__ __forceinline__ void load(const MeshDev&, const DevParams& p, const CoefArgs<C>&,
                                        const int[8], const Geo<T>& g) {
     const T f[NF][8] = {};
     setup(f, g, p);
   }
-  // sa = 0 or sb = 0 (the stiffness K and the mass M of the Schur preconditioner) skip the other
-  // part: the branch is uniform over the whole launch
-  __device__ __forceinline__ void apply(const Geo<T>& g, const DevParams&, const T x[NC][8],
+  // sb = 0 (the mass M of the Schur preconditioner) skips the stiffness part: the branch is
+  // uniform over the whole launch
+  __device__ __forceinline__ void apply(const Geo<T>&, const DevParams&, const T x[NC][8],
                                         T r[NC][8]) const {
-    if (ck[0] != T(0)) {
-      stiff_local(ck, g, x[0], r[0]);
-    } else {
+    const T* X = x[0];
+    T u[8], B[8], S[8];
 #pragma unroll
-      for (int a = 0; a < 8; ++a) r[0][a] = T(0);
+    for (int j = 0; j < 4; ++j) {  // P along z: pairs (j, j + 4)
+      u[j] = T(2) * X[j] + X[j + 4];
+      u[j + 4] = X[j] + T(2) * X[j + 4];
     }
-    if (cm != T(0)) {
-      T v[8], t[8];
-      interp3(x[0], v);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] *= cm;
-      interp3(v, t);
+    for (int z = 0; z < 2; ++z)
 #pragma unroll
-      for (int a = 0; a < 8; ++a) r[0][a] += t[a];
+      for (int i = 0; i < 2; ++i) {  // P along y: pairs (i + 4z, i + 2 + 4z)
+        const int a = i + 4 * z, b = a + 2;
+        B[a] = T(2) * u[a] + u[b];
+        B[b] = u[a] + T(2) * u[b];
+      }
+    if (cx == T(0) && cy == T(0) && cz == T(0)) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a) S[a] = cm * B[a];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {  // P along x: pairs (2j, 2j + 1)
+        r[0][2 * j] = T(2) * S[2 * j] + S[2 * j + 1];
+        r[0][2 * j + 1] = S[2 * j] + T(2) * S[2 * j + 1];
+      }
+      return;
+    }
+    T w[4];  // Dz x on the z = 0 layer (the z = 1 layer is its negative)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = X[j] - X[j + 4];
+#pragma unroll
+    for (int z = 0; z < 2; ++z)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int a = i + 4 * z, b = a + 2;
+        const T c = u[a] - u[b];                      // Dy Pz x
+        const T e0 = T(2) * w[i] + w[i + 2];           // Py Dz x at (i, 0)
+        const T e1 = w[i] + T(2) * w[i + 2];           // ... at (i, 1)
+        const T sgn = z ? T(-1) : T(1);
+        S[a] = cm * B[a] + cy * c + cz * (sgn * e0);
+        S[b] = cm * B[b] - cy * c + cz * (sgn * e1);
+      }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const T dx = cx * (B[2 * j] - B[2 * j + 1]);
+      r[0][2 * j] = T(2) * S[2 * j] + S[2 * j + 1] + dx;
+      r[0][2 * j + 1] = S[2 * j] + T(2) * S[2 * j + 1] - dx;
     }
   }
 };
