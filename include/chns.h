@@ -60,7 +60,11 @@ typedef enum {
 typedef enum {
   CHNS_FP64 = 0,          /* double vectors, double coefficients */
   CHNS_FP32 = 1,          /* float vectors, float coefficients */
-  CHNS_FP32_BF16COEF = 2  /* float vectors, bfloat16 coefficient fields */
+  CHNS_FP32_BF16COEF = 2, /* float vectors, bfloat16 coefficient fields */
+  CHNS_FP64_DF = 3        /* double vectors and coefficients; the Poisson and mass applies
+                           * compute in double-float (pairs of FP32 numbers, rounding ~1e-14 per
+                           * operation), the CH and momentum applies in FP64, which is faster
+                           * for them (operator applies and fp64_apply only) */
 } chns_precision;
 
 typedef enum {
@@ -256,6 +260,9 @@ typedef struct {
   chns_mg* mg;              /* CHNS_PC_MULTIGRID: the hierarchy of this mesh (not owned) */
   int32_t mass_its;         /* CHNS_PC_SCHUR: Jacobi-CG iterations of each M^-1 (0: the larger of
                              * 4 and inner_its / 4) */
+  int32_t fp64_apply;       /* precision of this solve's FP64-vector operator applies (the
+                             * refinement residuals; every iteration when inner_precision is
+                             * CHNS_FP64): CHNS_FP64 (0) or CHNS_FP64_DF */
 } chns_solver_params;
 
 typedef struct {

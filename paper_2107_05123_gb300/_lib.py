@@ -23,7 +23,7 @@ OK, EINVAL, EUNBALANCED, ENOMEM, ECUDA, ENOTCONV, EBREAKDOWN, ENAN = range(8)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "EUNBALANCED", 3: "ENOMEM", 4: "ECUDA", 5: "ENOTCONV",
                 6: "EBREAKDOWN", 7: "ENAN"}
 # chns_precision
-FP64, FP32, FP32_BF16COEF = 0, 1, 2
+FP64, FP32, FP32_BF16COEF, FP64_DF = 0, 1, 2, 3
 # chns_operator
 OP_POISSON, OP_MASS, OP_CH, OP_MOMENTUM = 0, 1, 2, 3
 OP_NCOMP = {OP_POISSON: 1, OP_MASS: 3, OP_CH: 2, OP_MOMENTUM: 3}
@@ -61,7 +61,7 @@ class chns_solver_params(C.Structure):
                 ("max_it", C.c_int32), ("restart", C.c_int32), ("inner_precision", C.c_int32),
                 ("inner_rtol", C.c_double), ("max_refine", C.c_int32),
                 ("check_every", C.c_int32), ("learned", C.c_void_p), ("inner_its", C.c_int32),
-                ("mg", C.c_void_p), ("mass_its", C.c_int32)]
+                ("mg", C.c_void_p), ("mass_its", C.c_int32), ("fp64_apply", C.c_int32)]
 
 
 class chns_mg_params(C.Structure):
@@ -229,9 +229,10 @@ def make_coef(phi=None, u=(None, None, None), mu=None) -> chns_coef:
 
 def make_solver(ksp=KSP_CG, pc=PC_JACOBI, rtol=1e-8, max_it=10000, restart=30,
                 inner_precision=FP64, inner_rtol=1e-3, max_refine=20, check_every=1,
-                learned=None, inner_its=0, mg=None, mass_its=0):
+                learned=None, inner_its=0, mg=None, mass_its=0, fp64_apply=FP64):
     return chns_solver_params(ksp, pc, rtol, max_it, restart, inner_precision, inner_rtol,
-                              max_refine, check_every, learned, inner_its, mg, mass_its)
+                              max_refine, check_every, learned, inner_its, mg, mass_its,
+                              fp64_apply)
 
 
 # ------------------------------------------------------------------ mesh

@@ -49,10 +49,12 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
               double* __restrict__ S_cg, int par, int fcg, const S* __restrict__ zcg,
               S* __restrict__ pout) {
   constexpr int NC = K::NC, NF = K::NF;
+  // shared accumulators: the arithmetic type, or FP64 for double-float (same size)
+  using U = AccumT<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* xs = reinterpret_cast<T*>(smem_raw);       // [NC][kPatchSlots]
-  T* ys = xs + NC * kPatchSlots;                // [NC][kPatchSlots]
-  T* fs = ys + NC * kPatchSlots;                // [NF][kPatchSlots]
+  T* xs = reinterpret_cast<T*>(smem_raw);                  // [NC][kPatchSlots]
+  U* ys = reinterpret_cast<U*>(xs + NC * kPatchSlots);     // [NC][kPatchSlots]
+  T* fs = reinterpret_cast<T*>(ys + NC * kPatchSlots);     // [NF][kPatchSlots]
   const int pidx = blockIdx.x;
   const int s0 = m.patch_slot[pidx], ns = m.patch_slot[pidx + 1] - s0, nreg = m.patch_nreg[pidx];
   const int64_t N = m.n_nodes;
@@ -100,7 +102,7 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
           xv = (T)x[c * N + g];
         }
         xs[c * kPatchSlots + i] = dir ? T(0) : xv;
-        ys[c * kPatchSlots + i] = T(0);
+        ys[c * kPatchSlots + i] = U(0);
       }
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
@@ -122,7 +124,7 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
       T v = a[q.x] + a[q.y];
       if (four) v += a[q.z] + a[q.w];
       xs[c * kPatchSlots + i] = w * v;
-      ys[c * kPatchSlots + i] = T(0);
+      ys[c * kPatchSlots + i] = U(0);
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -165,7 +167,7 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
         if (PQ && !EF) Acc<T>::fma(en[0], xin[c][a], r[c][a]);
-        atomicAdd(ys + c * kPatchSlots + sl[a], r[c][a]);
+        atomicAdd(ys + c * kPatchSlots + sl[a], (U)r[c][a]);
       }
   }
   // p.Ap
@@ -179,11 +181,11 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
   for (int i = nreg + threadIdx.x; i < ns; i += blockDim.x) {
     const ushort4 q = m.slot_par[s0 + i];
     const bool four = q.z != 0xffff;
-    const T w = four ? T(0.25) : T(0.5);
+    const U w = four ? U(0.25) : U(0.5);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      T* a = ys + c * kPatchSlots;
-      const T v = w * a[i];
+      U* a = ys + c * kPatchSlots;
+      const U v = w * a[i];
       atomicAdd(a + q.x, v);
       atomicAdd(a + q.y, v);
       if (four) {
@@ -707,6 +709,15 @@ static void launch_apply(const chns_mesh* m, chns_operator op, const DevParams& 
   }
 }
 
+// The Poisson and mass applies in double-float arithmetic on FP64 arrays.
+static void launch_apply_df(const chns_mesh* m, chns_operator op, const DevParams& p,
+                            const CoefArgs<double>& cf, const double* x, double* y, cudaStream_t s) {
+  if (op == CHNS_OP_POISSON)
+    launch_patch<PoissonK<DF, double>, DF, double, double, false>(m, p, cf, x, y, nullptr, s);
+  else
+    launch_patch<MassK<DF, double>, DF, double, double, false>(m, p, cf, x, y, nullptr, s);
+}
+
 // Quadrature data of the momentum operator for the coefficients coef (FP64 and, when coef32 is
 // given, FP32), used by every momentum apply until momentum_qdata_off.
 chns_status momentum_qdata_on(const chns_mesh* m, const chns_params* prm, const chns_coef* coef64,
@@ -786,6 +797,22 @@ chns_status apply_op(const chns_mesh* m, chns_operator op, const chns_params* pr
       CHNS_CUDA(cudaMemsetAsync(y, 0, n * sizeof(double), s));
       launch_apply<double, double, double>(m, op, p, coef_args<double>(coef),
                                            static_cast<const double*>(x), static_cast<double*>(y), s);
+      if (op_dirichlet(op))
+        dirichlet_rows(m, nc, static_cast<const double*>(x), static_cast<double*>(y), s);
+      break;
+    }
+    case CHNS_FP64_DF: {
+      // double-float pays for the light operators (measured on 1.4e6 leaves: Poisson 0.76 ->
+      // 0.31 ms, mass 1.01 -> 0.60 ms); the CH and momentum applies are faster in FP64 (1.90 vs
+      // 1.96 ms, 7.8 vs 10.1 ms: register pressure and spills)
+      CHNS_CUDA(cudaMemsetAsync(y, 0, n * sizeof(double), s));
+      if (op == CHNS_OP_POISSON || op == CHNS_OP_MASS)
+        launch_apply_df(m, op, p, coef_args<double>(coef), static_cast<const double*>(x),
+                        static_cast<double*>(y), s);
+      else
+        launch_apply<double, double, double>(m, op, p, coef_args<double>(coef),
+                                             static_cast<const double*>(x),
+                                             static_cast<double*>(y), s);
       if (op_dirichlet(op))
         dirichlet_rows(m, nc, static_cast<const double*>(x), static_cast<double*>(y), s);
       break;

@@ -9,6 +9,7 @@
 // reference derivative is (u1 - u0)/2 at both points.
 #pragma once
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace chns {
@@ -33,6 +34,7 @@ struct PrmT {
 struct DevParams {
   PrmT<double> d;
   PrmT<float> f;
+  PrmT<DF> x;  // the FP64 values split into double-float
   template <class T>
   __host__ __device__ __forceinline__ const PrmT<T>& get() const;
 };
@@ -40,6 +42,8 @@ template <>
 __host__ __device__ __forceinline__ const PrmT<double>& DevParams::get<double>() const { return d; }
 template <>
 __host__ __device__ __forceinline__ const PrmT<float>& DevParams::get<float>() const { return f; }
+template <>
+__host__ __device__ __forceinline__ const PrmT<DF>& DevParams::get<DF>() const { return x; }
 
 template <class T>
 inline PrmT<T> make_prm(const chns_params& p) {
@@ -76,8 +80,14 @@ inline DevParams make_dev_params(const chns_params& p) {
   DevParams d;
   d.d = make_prm<double>(p);
   d.f = make_prm<float>(p);
+  d.x = make_prm<DF>(p);
   return d;
 }
+
+// Storage type of values computed in arithmetic type T (FP64 for double-float) and the shared
+// accumulator type of the patch applies (the same).
+template <class T>
+using AccumT = typename std::conditional<std::is_same<T, DF>::value, double, T>::type;
 
 template <class T>
 __device__ __forceinline__ T clamp1(T v) {
@@ -106,13 +116,20 @@ template <class T>
 __device__ __forceinline__ Geo<T> level_geometry(const MeshDev& m, int level) {
   const LevelGeo& L = m.geo[level];
   Geo<T> g;
-  if constexpr (sizeof(T) == sizeof(double)) {
+  if constexpr (std::is_same<T, double>::value) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       g.h[d] = L.h[d];
       g.ih[d] = L.ih[d];
     }
     g.detJ = L.detJ;
+  } else if constexpr (std::is_same<T, DF>::value) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      g.h[d] = DF(L.h[d]);
+      g.ih[d] = DF(L.ih[d]);
+    }
+    g.detJ = DF(L.detJ);
   } else {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {

@@ -476,6 +476,7 @@ struct Ctx {
   int64_t n;                // vector length (components * n_nodes)
   double* S;                // device scalars
   double sa = 0.0, sb = 0.0;  // op == kOpShift: y = sa M x + sb K x
+  bool df = false;            // FP64 applies in double-float element arithmetic
 };
 
 template <class T>
@@ -483,7 +484,8 @@ chns_status apply_T(const Ctx& c, const T* x, T* y) {
   if (c.op == kOpShift)
     return apply_shift(c.m, c.prm, sizeof(T) == sizeof(double) ? c.coef64->phi_tilde : c.coefR.phi_tilde,
                        c.sa, c.sb, x, y, sizeof(T) == sizeof(double) ? CHNS_FP64 : CHNS_FP32, c.s);
-  if (sizeof(T) == sizeof(double)) return apply_op(c.m, c.op, c.prm, c.coef64, x, y, CHNS_FP64, c.s);
+  if (sizeof(T) == sizeof(double))
+    return apply_op(c.m, c.op, c.prm, c.coef64, x, y, c.df ? CHNS_FP64_DF : CHNS_FP64, c.s);
   return apply_op(c.m, c.op, c.prm, &c.coefR, x, y, c.inner, c.s);
 }
 
@@ -1228,6 +1230,8 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
              CHNS_EINVAL, "GMRES restart out of range");
   CHNS_CHECK(sp->inner_precision >= CHNS_FP64 && sp->inner_precision <= CHNS_FP32_BF16COEF,
              CHNS_EINVAL, "bad inner precision");
+  CHNS_CHECK(sp->fp64_apply == CHNS_FP64 || sp->fp64_apply == CHNS_FP64_DF, CHNS_EINVAL,
+             "krylov: fp64_apply must be CHNS_FP64 or CHNS_FP64_DF");
   const Workspace& ws = m->ws;
   const int nc = op_ncomp(op);
   const int64_t n = nc * m->d.n_nodes;
@@ -1250,6 +1254,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
   c.s = s;
   c.n = n;
   c.S = scal(m);
+  c.df = sp->fp64_apply == CHNS_FP64_DF;
 
   // workspace layout (FP64): 0 b (projected), 1 r64, 2 dinv64/diag, 3..6 CG vectors,
   // 7 GMRES z; (FP32): 0 r32, 1 d32, 2 dinv32, 3..6 CG vectors, 7 GMRES z

@@ -529,11 +529,11 @@ struct MomQK {
   static constexpr bool DIR = true;
   static constexpr bool DIAG_PER_COMP = false;
   static constexpr int NF = 1;  // (phi~ only to keep the shared-memory layout of the kernel)
-  const T* qd = nullptr;
+  const AccumT<T>* qd = nullptr;  // FP64 data for double-float
   int64_t ne = 0, e = 0;
   __device__ __forceinline__ void setup(const T[NF][8], const Geo<T>&, const DevParams&) {}
   __device__ __forceinline__ void bind(const void* q, int64_t n_elem, int64_t elem) {
-    qd = static_cast<const T*>(q);
+    qd = static_cast<const AccumT<T>*>(q);
     ne = n_elem;
     e = elem;
   }
@@ -556,19 +556,19 @@ struct MomQK {
       grad_compact(x[k], gx, gy, gz);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const T* qq = qd + (int64_t)q * kMomQ * ne + e;
+        const AccumT<T>* qq = qd + (int64_t)q * kMomQ * ne + e;
         const T vg[3] = {gx[gxi(q)] * g.ih[0], gy[gyi(q)] * g.ih[1], gz[gzi(q)] * g.ih[2]};
-        const T a0 = __ldg(qq);
+        const T a0 = T(__ldg(qq));
         T sb = a0 * v[q], R = a0 * v[q];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          sb += __ldg(qq + (1 + d) * ne) * vg[d];
-          R += __ldg(qq + (4 + d) * ne) * vg[d];
+          sb += T(__ldg(qq + (1 + d) * ne)) * vg[d];
+          R += T(__ldg(qq + (4 + d) * ne)) * vg[d];
         }
-        const T ce = __ldg(qq + 7 * ne);
+        const T ce = T(__ldg(qq + 7 * ne));
         s[q] = J * sb;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) V[d][q] = J * (ce * vg[d] + R * __ldg(qq + (8 + d) * ne));
+        for (int d = 0; d < 3; ++d) V[d][q] = J * (ce * vg[d] + R * T(__ldg(qq + (8 + d) * ne)));
       }
       interp3(s, r[k]);
       grad_T(V, g, r[k]);
@@ -584,15 +584,15 @@ struct MomQK {
     for_qp([&](auto QC) {
       constexpr int Q = decltype(QC)::value;
       const T* q = qd + (int64_t)Q * kMomQ * ne + e;
-      const T a0 = __ldg(q);
+      const T a0 = T(__ldg(q));
       T b[3], bp[3], t[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        b[d] = __ldg(q + (1 + d) * ne);
-        bp[d] = __ldg(q + (4 + d) * ne);
-        t[d] = __ldg(q + (8 + d) * ne);
+        b[d] = T(__ldg(q + (1 + d) * ne));
+        bp[d] = T(__ldg(q + (4 + d) * ne));
+        t[d] = T(__ldg(q + (8 + d) * ne));
       }
-      const T ce = __ldg(q + 7 * ne);
+      const T ce = T(__ldg(q + 7 * ne));
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
         T v, vg[3];

@@ -11,14 +11,13 @@
 // results do not depend on scheduling.
 #pragma once
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace chns {
 
-// ---- double-float accumulator
-struct DF {
-  float hi, lo;
-};
+// ---- double-float accumulator (the DF pair of dfloat.cuh; here a faster addition that adds the
+// low parts before one renormalisation, enough for sums of same-signed or small terms)
 
 __device__ __forceinline__ DF df_zero() { return DF{0.f, 0.f}; }
 
@@ -70,6 +69,13 @@ struct Acc<float> {
   __device__ static DF zero() { return df_zero(); }
   __device__ static void fma(DF& a, float x, float y) { df_fma(a, x, y); }
   __device__ static void add(DF& a, float x) { df_addf(a, x); }
+};
+template <>
+struct Acc<DF> {  // element energies of double-float applies, summed in FP64
+  using type = double;
+  __device__ static double zero() { return 0.0; }
+  __device__ static void fma(double& a, DF x, DF y) { a += (double)(x * y); }
+  __device__ static void add(double& a, DF x) { a += (double)x; }
 };
 template <>
 struct Acc<double> {

@@ -8,92 +8,104 @@
 namespace chns {
 
 constexpr int kRhsThreads = 128;
-// gravity direction g_hat = (0, -1, 0) (Sec. 3)
-__device__ __forceinline__ double ghat(int i) { return i == 1 ? -1.0 : 0.0; }
+// gravity direction g_hat = (0, -1, 0) (Sec. 3): the sign of the y component
+__device__ __forceinline__ int ghat(int i) { return i == 1 ? -1 : 0; }
 
 struct Ptr3 {
   const double* c[3];
 };
 
+// The kernels below are written for an arithmetic type A and run in FP64 (A = double): in
+// double-float (dfloat.cuh) they measured about 3x slower, their register pressure and spills
+// outweighing the FP32 issue rate. Fields are read from and results added to FP64 arrays.
+
 // ---- CH residual at the new-time iterate (Def. weak_VMS_disc_CH):
 //   F_phi = (q, (phi - phi_k)/dt) - (grad q, u~ phi~) + 1/(Pe Cn) (grad q, grad mu~)
 //   F_mu  = -(q, mu~) + (q, psi'(phi~)) + Cn^2 (grad q, grad phi~)
+template <class A>
 __global__ void __launch_bounds__(kRhsThreads)
 k_residual_ch(MeshDev m, DevParams p, const double* __restrict__ phi, const double* __restrict__ mu,
               const double* __restrict__ phik, const double* __restrict__ muk, Ptr3 u,
               double* __restrict__ f) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= m.n_elem) return;
+  const PrmT<A>& k = p.get<A>();
   int idx[8];
   load_corners(m, e, idx);
-  const Geo<double> g = geometry<double>(m, e);
-  double a[8], b[8], pt[8], mt[8], dp[8], ue[3][8];
-  gather<double, false>(m, idx, phi, a);
-  gather<double, false>(m, idx, phik, b);
+  const Geo<A> g = geometry<A>(m, e);
+  A a[8], b[8], pt[8], mt[8], dp[8], ue[3][8];
+  gather<A, false>(m, idx, phi, a);
+  gather<A, false>(m, idx, phik, b);
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    pt[i] = 0.5 * (a[i] + b[i]);
-    dp[i] = (a[i] - b[i]) * p.d.idt;
+    pt[i] = A(0.5) * (a[i] + b[i]);
+    dp[i] = (a[i] - b[i]) * k.idt;
   }
-  gather<double, false>(m, idx, mu, a);
-  gather<double, false>(m, idx, muk, b);
+  gather<A, false>(m, idx, mu, a);
+  gather<A, false>(m, idx, muk, b);
 #pragma unroll
-  for (int i = 0; i < 8; ++i) mt[i] = 0.5 * (a[i] + b[i]);
+  for (int i = 0; i < 8; ++i) mt[i] = A(0.5) * (a[i] + b[i]);
 #pragma unroll
-  for (int d = 0; d < 3; ++d) gather<double, false>(m, idx, u.c[d], ue[d]);
+  for (int d = 0; d < 3; ++d) gather<A, false>(m, idx, u.c[d], ue[d]);
   // sum-factorised: values at the Gauss points by interp3, gradients by grad_compact, and the
   // transposes interp3 / grad_T on the per-point terms
-  double r0[8], r1[8];
-  const double J = g.detJ, kmu = p.d.inv_pecn, c2 = p.d.cn2;
-  double pv[8], mv[8], s[8], V[3][8];
+  A r0[8], r1[8];
+  const A J = g.detJ, kmu = k.inv_pecn, c2 = k.cn2;
+  A pv[8], mv[8], s[8], V[3][8];
   interp3(pt, pv);
   interp3(mt, mv);
 #pragma unroll
   for (int q = 0; q < 8; ++q) s[q] = J * (pv[q] * pv[q] * pv[q] - pv[q] - mv[q]);
   interp3(s, r1);
   {
-    double gx[4], gy[4], gz[4];
+    A gx[4], gy[4], gz[4];
     grad_compact(pt, gx, gy, gz);
+    const A jc = J * c2;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      V[0][q] = J * c2 * gx[gxi(q)] * g.ih[0];
-      V[1][q] = J * c2 * gy[gyi(q)] * g.ih[1];
-      V[2][q] = J * c2 * gz[gzi(q)] * g.ih[2];
+      V[0][q] = jc * gx[gxi(q)] * g.ih[0];
+      V[1][q] = jc * gy[gyi(q)] * g.ih[1];
+      V[2][q] = jc * gz[gzi(q)] * g.ih[2];
     }
     grad_T(V, g, r1);
   }
   interp3(dp, s);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) s[q] *= J;
+  for (int q = 0; q < 8; ++q) s[q] = s[q] * J;
   interp3(s, r0);
   {
-    double gx[4], gy[4], gz[4], uq[8];
+    A gx[4], gy[4], gz[4], uq[8];
     grad_compact(mt, gx, gy, gz);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       interp3(ue[d], uq);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const double gm = d == 0 ? gx[gxi(q)] : d == 1 ? gy[gyi(q)] : gz[gzi(q)];
+        const A gm = d == 0 ? gx[gxi(q)] : d == 1 ? gy[gyi(q)] : gz[gzi(q)];
         V[d][q] = J * (kmu * gm * g.ih[d] - uq[q] * pv[q]);
       }
     }
     grad_T(V, g, r0);
   }
-  scatter<double, false>(m, idx, r0, f);
-  scatter<double, false>(m, idx, r1, f + m.n_nodes);
+  scatter<A, false>(m, idx, r0, f);
+  scatter<A, false>(m, idx, r1, f + m.n_nodes);
 }
 
 // Forcing d_j(d_i phi d_j phi) of the trilinear interpolant at Q (pure second derivatives vanish
 // on box elements): F_i = sum_{j != i} H_ij d_j phi.
-template <int Q>
-__device__ __forceinline__ void forcing_at(const double pe[8], const Geo<double>& g,
-                                           const double gp[3], double F[3]) {
-  double hxy, hxz, hyz;
+template <int Q, class A>
+__device__ __forceinline__ void forcing_at(const A pe[8], const Geo<A>& g, const A gp[3], A F[3]) {
+  A hxy, hxz, hyz;
   hess_at<Q>(pe, g, hxy, hxz, hyz);
   F[0] = hxy * gp[1] + hxz * gp[2];
   F[1] = hxy * gp[0] + hyz * gp[2];
   F[2] = hxz * gp[0] + hyz * gp[1];
+}
+
+// rho g_i / Fr for the component i (g_hat = (0, -1, 0))
+template <class A>
+__device__ __forceinline__ A gravity(const A& rho, const PrmT<A>& k, int i) {
+  return ghat(i) == 0 ? A(0) : -(rho * k.inv_fr);
 }
 
 // ---- velocity-prediction right-hand side (Def. weak_VMS_disc), per component i:
@@ -104,45 +116,48 @@ __device__ __forceinline__ void forcing_at(const double pe[8], const Geo<double>
 // grad_compact, the per-point coefficients (tau_m and the advection and stabilisation vectors)
 // are formed once per point, and each component's test-function sums are the transposes interp3
 // and grad_T of its per-point terms.
+template <class A>
 struct MomPt {  // per-point data shared by the three components
-  double a0, b[3], bp[3], e, t[3], rho, gphi[3], F[3], pg[3];
+  A a0, b[3], bp[3], e, t[3], rho, gphi[3], F[3], pg[3];
 };
 
+template <class A>
 __global__ void __launch_bounds__(kRhsThreads)
 k_rhs_momentum(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 uk,
                const double* __restrict__ pk, double* __restrict__ b) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= m.n_elem) return;
+  const PrmT<A>& k = p.get<A>();
   int idx[8];
   load_corners(m, e, idx);
-  const Geo<double> g = geometry<double>(m, e);
-  const double J = g.detJ, cw = p.d.cw;
-  MomPt c[8];
+  const Geo<A> g = geometry<A>(m, e);
+  const A J = g.detJ, cw = k.cw;
+  MomPt<A> c[8];
   {
-    double pe[8], ue[3][8], me[8], pp[8];
-    gather<double, false>(m, idx, cf.phi, pe);
+    A pe[8], ue[3][8], me[8], pp[8];
+    gather<A, false>(m, idx, cf.phi, pe);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) gather<double, false>(m, idx, cf.u[d], ue[d]);
-    gather<double, false>(m, idx, cf.mu, me);
-    gather<double, false>(m, idx, pk, pp);
-    QpField<double> fp, fm, fr;
+    for (int d = 0; d < 3; ++d) gather<A, false>(m, idx, cf.u[d], ue[d]);
+    gather<A, false>(m, idx, cf.mu, me);
+    gather<A, false>(m, idx, pk, pp);
+    QpField<A> fp, fm, fr;
     fp.eval(pe);
     fm.eval_grad(me);
     fr.eval_grad(pp);
-    double uq[3][8];
+    A uq[3][8];
 #pragma unroll
     for (int d = 0; d < 3; ++d) interp3(ue[d], uq[d]);
     for_qp([&](auto QC) {
       constexpr int Q = decltype(QC)::value;
-      double gp[3], mg[3], uv[3];
+      A gp[3], mg[3], uv[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         gp[d] = fp.grad(Q, d, g);
         mg[d] = fm.grad(Q, d, g);
         uv[d] = uq[d][Q];
       }
-      const VmsQ<double> v = vms_point(fp.v[Q], gp, mg, uv, g, p);
-      MomPt& o = c[Q];
+      const VmsQ<A> v = vms_point(fp.v[Q], gp, mg, uv, g, p);
+      MomPt<A>& o = c[Q];
       o.a0 = v.a0;
       o.e = v.e;
       o.rho = v.rho;
@@ -159,84 +174,83 @@ k_rhs_momentum(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 uk,
   }
 #pragma unroll 1
   for (int i = 0; i < 3; ++i) {
-    double ui[8];
-    gather<double, false>(m, idx, uk.c[i], ui);
-    QpField<double> fu;
+    A ui[8];
+    gather<A, false>(m, idx, uk.c[i], ui);
+    QpField<A> fu;
     fu.eval(ui);
-    double s[8], V[3][8];
+    A s[8], V[3][8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const MomPt& o = c[q];
-      const double v = fu.v[q];
-      const double vg[3] = {fu.grad(q, 0, g), fu.grad(q, 1, g), fu.grad(q, 2, g)};
-      const double grav = o.rho * ghat(i) * p.d.inv_fr;
-      const double bdot = o.b[0] * vg[0] + o.b[1] * vg[1] + o.b[2] * vg[2];
-      const double bpdot = o.bp[0] * vg[0] + o.bp[1] * vg[1] + o.bp[2] * vg[2];
-      const double r0 = -o.a0 * v + bpdot + cw * o.F[i] + o.pg[i] - grav;
-      const double fn = o.a0 * v - bdot - o.pg[i] + grav;
+      const MomPt<A>& o = c[q];
+      const A v = fu.v[q];
+      const A vg[3] = {fu.grad(q, 0, g), fu.grad(q, 1, g), fu.grad(q, 2, g)};
+      const A grav = gravity(o.rho, k, i);
+      const A bdot = o.b[0] * vg[0] + o.b[1] * vg[1] + o.b[2] * vg[2];
+      const A bpdot = o.bp[0] * vg[0] + o.bp[1] * vg[1] + o.bp[2] * vg[2];
+      const A r0 = bpdot - o.a0 * v + cw * o.F[i] + o.pg[i] - grav;
+      const A fn = o.a0 * v - bdot - o.pg[i] + grav;
       s[q] = J * fn;
+      const A cg = cw * o.gphi[i];
 #pragma unroll
-      for (int d = 0; d < 3; ++d)
-        V[d][q] = J * (-o.e * vg[d] + cw * o.gphi[i] * o.gphi[d] - o.t[d] * r0);
+      for (int d = 0; d < 3; ++d) V[d][q] = J * (cg * o.gphi[d] - o.e * vg[d] - o.t[d] * r0);
     }
-    double r[8];
+    A r[8];
     interp3(s, r);
     grad_T(V, g, r);
-    scatter<double, true>(m, idx, r, b + i * m.n_nodes);
+    scatter<A, true>(m, idx, r, b + i * m.n_nodes);
   }
 }
 
 // Full R_m,i(v) at a point (Def. of R_m) with v~ = (v + u_k)/2, from the point values vv and
 // gradients vgr of v and ug of u_k (uv: u_k's values).
-__device__ __forceinline__ void rm_point(const VmsQ<double>& c, const DevParams& p,
-                                         const double F[3], const double pg[3],
-                                         const double vv[3], const double vgr[3][3],
-                                         const double uv[3], const double ug[3][3], double R[3],
-                                         double& div) {
+template <class A>
+__device__ __forceinline__ void rm_point(const VmsQ<A>& c, const PrmT<A>& k, const A F[3],
+                                         const A pg[3], const A vv[3], const A vgr[3][3],
+                                         const A uv[3], const A ug[3][3], A R[3], A& div) {
   div = vgr[0][0] + vgr[1][1] + vgr[2][2];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    double tg[3];
+    A tg[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) tg[d] = 0.5 * (vgr[i][d] + ug[i][d]);
-    const double adv = c.uq[0] * tg[0] + c.uq[1] * tg[1] + c.uq[2] * tg[2];
-    const double jdv = c.J[0] * tg[0] + c.J[1] * tg[1] + c.J[2] * tg[2];
-    const double edv = c.ge[0] * tg[0] + c.ge[1] * tg[1] + c.ge[2] * tg[2];
-    R[i] = c.rho * (vv[i] - uv[i]) * p.d.idt + c.rho * adv + jdv * p.d.inv_pe + p.d.cw * F[i] +
-           pg[i] - edv * p.d.inv_re - c.rho * ghat(i) * p.d.inv_fr;
+    for (int d = 0; d < 3; ++d) tg[d] = A(0.5) * (vgr[i][d] + ug[i][d]);
+    const A adv = c.uq[0] * tg[0] + c.uq[1] * tg[1] + c.uq[2] * tg[2];
+    const A jdv = c.J[0] * tg[0] + c.J[1] * tg[1] + c.J[2] * tg[2];
+    const A edv = c.ge[0] * tg[0] + c.ge[1] * tg[1] + c.ge[2] * tg[2];
+    R[i] = c.rho * (vv[i] - uv[i]) * k.idt + c.rho * adv + jdv * k.inv_pe + k.cw * F[i] + pg[i] -
+           edv * k.inv_re - gravity(c.rho, k, i);
   }
 }
 
 // The fields of the pressure-Poisson and velocity-update right-hand sides at the 8 Gauss points.
+template <class A>
 struct ProjFields {
-  QpField<double> fp, fm, fr, fv[3], fu[3];
-  double uq[3][8];
+  QpField<A> fp, fm, fr, fv[3], fu[3];
+  A uq[3][8];
   __device__ __forceinline__ void load(const MeshDev& m, const int idx[8],
                                        const CoefArgs<double>& cf, const Ptr3& v, const Ptr3& uk,
-                                       const double* pk, double pe[8]) {
-    double t[8];
-    gather<double, false>(m, idx, cf.phi, pe);
+                                       const double* pk, A pe[8]) {
+    A t[8];
+    gather<A, false>(m, idx, cf.phi, pe);
     fp.eval(pe);
-    gather<double, false>(m, idx, cf.mu, t);
+    gather<A, false>(m, idx, cf.mu, t);
     fm.eval_grad(t);
-    gather<double, false>(m, idx, pk, t);
+    gather<A, false>(m, idx, pk, t);
     fr.eval_grad(t);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      gather<double, false>(m, idx, cf.u[d], t);
+      gather<A, false>(m, idx, cf.u[d], t);
       interp3(t, uq[d]);
-      gather<double, false>(m, idx, v.c[d], t);
+      gather<A, false>(m, idx, v.c[d], t);
       fv[d].eval(t);
-      gather<double, false>(m, idx, uk.c[d], t);
+      gather<A, false>(m, idx, uk.c[d], t);
       fu[d].eval(t);
     }
   }
   // the coefficients, forcing, grad p_k and R_m at point Q
   template <int Q>
-  __device__ __forceinline__ VmsQ<double> at(const double pe[8], const Geo<double>& g,
-                                             const DevParams& p, double pg[3], double R[3],
-                                             double vv[3], double& div) const {
-    double gp[3], mg[3], uv0[3], vgr[3][3], ug[3][3], uv[3];
+  __device__ __forceinline__ VmsQ<A> at(const A pe[8], const Geo<A>& g, const DevParams& p,
+                                        A pg[3], A R[3], A vv[3], A& div) const {
+    A gp[3], mg[3], uv0[3], vgr[3][3], ug[3][3], uv[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       gp[d] = fp.grad(Q, d, g);
@@ -251,16 +265,17 @@ struct ProjFields {
         ug[d][k] = fu[d].grad(Q, k, g);
       }
     }
-    const VmsQ<double> c = vms_point(fp.v[Q], gp, mg, uv0, g, p);
-    double F[3];
+    const VmsQ<A> c = vms_point(fp.v[Q], gp, mg, uv0, g, p);
+    A F[3];
     forcing_at<Q>(pe, g, c.gphi, F);
-    rm_point(c, p, F, pg, vv, vgr, uv, ug, R, div);
+    rm_point(c, p.get<A>(), F, pg, vv, vgr, uv, ug, R, div);
     return c;
   }
 };
 
 // ---- pressure-Poisson right-hand side (Def. weak_VMS_disc_pp_vel, scalar test q):
 //   -(2/dt)(q, div v) - (2/dt)(grad q, tau R_m / rho~) + (grad q, grad p_k / rho~)
+template <class A>
 __global__ void __launch_bounds__(kRhsThreads)
 k_rhs_poisson(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 v, Ptr3 uk,
               const double* __restrict__ pk, double* __restrict__ b) {
@@ -268,29 +283,30 @@ k_rhs_poisson(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 v, Ptr3 uk,
   if (e >= m.n_elem) return;
   int idx[8];
   load_corners(m, e, idx);
-  const Geo<double> g = geometry<double>(m, e);
-  double pe[8];
-  ProjFields f;
+  const Geo<A> g = geometry<A>(m, e);
+  A pe[8];
+  ProjFields<A> f;
   f.load(m, idx, cf, v, uk, pk, pe);
-  const double J = g.detJ, k2 = p.d.k2dt;
-  double s[8], V[3][8];
+  const A J = g.detJ, k2 = p.get<A>().k2dt;
+  A s[8], V[3][8];
   for_qp([&](auto QC) {
     constexpr int Q = decltype(QC)::value;
-    double pg[3], R[3], vv[3], div;
-    const VmsQ<double> c = f.at<Q>(pe, g, p, pg, R, vv, div);
-    const double ir = 1.0 / c.rho;
+    A pg[3], R[3], vv[3], div;
+    const VmsQ<A> c = f.template at<Q>(pe, g, p, pg, R, vv, div);
+    const A jr = J / c.rho, kt = k2 * c.tau;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) V[d][Q] = J * (-k2 * c.tau * R[d] + pg[d]) * ir;
-    s[Q] = J * (-k2 * div);
+    for (int d = 0; d < 3; ++d) V[d][Q] = jr * (pg[d] - kt * R[d]);
+    s[Q] = -(J * k2 * div);
   });
-  double r[8];
+  A r[8];
   interp3(s, r);
   grad_T(V, g, r);
-  scatter<double, false>(m, idx, r, b);
+  scatter<A, false>(m, idx, r, b);
 }
 
 // ---- velocity-update right-hand side (Def. weak_VMS_disc_vel_update), per component:
 //   (w, rho~ v_i) - (w, tau R_m,i) - (dt/2)(w, d_i (p_new - p_k))
+template <class A>
 __global__ void __launch_bounds__(kRhsThreads)
 k_rhs_vu(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 v, Ptr3 uk,
          const double* __restrict__ pk, const double* __restrict__ pn, double* __restrict__ b) {
@@ -298,34 +314,34 @@ k_rhs_vu(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 v, Ptr3 uk,
   if (e >= m.n_elem) return;
   int idx[8];
   load_corners(m, e, idx);
-  const Geo<double> g = geometry<double>(m, e);
-  double pe[8];
-  ProjFields f;
+  const Geo<A> g = geometry<A>(m, e);
+  A pe[8];
+  ProjFields<A> f;
   f.load(m, idx, cf, v, uk, pk, pe);
-  QpField<double> fd;  // p_new - p_k
+  QpField<A> fd;  // p_new - p_k
   {
-    double a[8], c0[8];
-    gather<double, false>(m, idx, pn, a);
-    gather<double, false>(m, idx, pk, c0);
+    A a[8], c0[8];
+    gather<A, false>(m, idx, pn, a);
+    gather<A, false>(m, idx, pk, c0);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) a[k] -= c0[k];
+    for (int k = 0; k < 8; ++k) a[k] = a[k] - c0[k];
     fd.eval_grad(a);
   }
-  const double J = g.detJ;
-  double s[3][8];
+  const A J = g.detJ, hdt = p.get<A>().half_dt;
+  A s[3][8];
   for_qp([&](auto QC) {
     constexpr int Q = decltype(QC)::value;
-    double pg[3], R[3], vv[3], div;
-    const VmsQ<double> c = f.at<Q>(pe, g, p, pg, R, vv, div);
+    A pg[3], R[3], vv[3], div;
+    const VmsQ<A> c = f.template at<Q>(pe, g, p, pg, R, vv, div);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-      s[i][Q] = J * (c.rho * vv[i] - c.tau * R[i] - p.d.half_dt * fd.grad(Q, i, g));
+      s[i][Q] = J * (c.rho * vv[i] - c.tau * R[i] - hdt * fd.grad(Q, i, g));
   });
 #pragma unroll 1
   for (int i = 0; i < 3; ++i) {
-    double r[8];
+    A r[8];
     interp3(s[i], r);
-    scatter<double, true>(m, idx, r, b + i * m.n_nodes);
+    scatter<A, true>(m, idx, r, b + i * m.n_nodes);
   }
 }
 
@@ -393,7 +409,7 @@ chns_status residual_ch(const chns_mesh* m, const chns_params* prm, const double
   Ptr3 up{{u[0], u[1], u[2]}};
   CHNS_CUDA(cudaMemsetAsync(f, 0, 2 * m->d.n_nodes * sizeof(double), s));
   note_launch();
-  k_residual_ch<<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, phi, mu, phik, muk, up, f);
+  k_residual_ch<double><<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, phi, mu, phik, muk, up, f);
   CHNS_CUDA(cudaGetLastError());
   return CHNS_OK;
 }
@@ -412,8 +428,8 @@ chns_status rhs_momentum(const chns_mesh* m, const chns_params* prm, const chns_
   const DevParams p = make_dev_params(*prm);
   CHNS_CUDA(cudaMemsetAsync(b, 0, 3 * m->d.n_nodes * sizeof(double), s));
   note_launch();
-  k_rhs_momentum<<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, cargs(c), Ptr3{{uk[0], uk[1], uk[2]}},
-                                                 pk, b);
+  const Ptr3 u3{{uk[0], uk[1], uk[2]}};
+  k_rhs_momentum<double><<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, cargs(c), u3, pk, b);
   CHNS_CUDA(cudaGetLastError());
   return CHNS_OK;
 }
@@ -424,8 +440,8 @@ chns_status rhs_poisson(const chns_mesh* m, const chns_params* prm, const chns_c
   const DevParams p = make_dev_params(*prm);
   CHNS_CUDA(cudaMemsetAsync(b, 0, m->d.n_nodes * sizeof(double), s));
   note_launch();
-  k_rhs_poisson<<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, cargs(c), Ptr3{{v[0], v[1], v[2]}},
-                                                Ptr3{{uk[0], uk[1], uk[2]}}, pk, b);
+  const Ptr3 v3{{v[0], v[1], v[2]}}, u3{{uk[0], uk[1], uk[2]}};
+  k_rhs_poisson<double><<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, cargs(c), v3, u3, pk, b);
   CHNS_CUDA(cudaGetLastError());
   return CHNS_OK;
 }
@@ -436,8 +452,8 @@ chns_status rhs_vu(const chns_mesh* m, const chns_params* prm, const chns_coef* 
   const DevParams p = make_dev_params(*prm);
   CHNS_CUDA(cudaMemsetAsync(b, 0, 3 * m->d.n_nodes * sizeof(double), s));
   note_launch();
-  k_rhs_vu<<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, cargs(c), Ptr3{{v[0], v[1], v[2]}},
-                                           Ptr3{{uk[0], uk[1], uk[2]}}, pk, pn, b);
+  const Ptr3 v3{{v[0], v[1], v[2]}}, u3{{uk[0], uk[1], uk[2]}};
+  k_rhs_vu<double><<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, cargs(c), v3, u3, pk, pn, b);
   CHNS_CUDA(cudaGetLastError());
   return CHNS_OK;
 }
