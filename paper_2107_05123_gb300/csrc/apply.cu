@@ -571,6 +571,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_diag(MeshDev m, DevParams p, 
   const Geo<T> g = geometry<T>(m, e);
   K k;
   k.load(m, p, cf, idx, g);
+  if constexpr (K::QDATA) k.bind(cf.qd, m.n_elem, e);
   for (int a = 0; a < 8; ++a) {
     for (int s = 0; s < 4; ++s) {
       double w;
@@ -764,10 +765,20 @@ static void launch_diag(const chns_mesh* m, chns_operator op, const DevParams& p
       note_launch();
       k_diag<ChK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cf, d);
       break;
-    case CHNS_OP_MOMENTUM:
+    case CHNS_OP_MOMENTUM: {
       note_launch();
-      k_diag<MomK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cf, d);
+      // from the quadrature data of the running momentum solve when it matches this precision
+      // (the operator the solve applies; the direct form re-evaluates tau_m per point)
+      const void* qd = sizeof(T) == sizeof(double) ? m->mq.qd64 : m->mq.qd32;
+      if (m->mq.on && qd) {
+        CoefArgs<C> cq = cf;
+        cq.qd = qd;
+        k_diag<MomQK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cq, d);
+      } else {
+        k_diag<MomK<T, C>, T, S, C><<<nb, kApplyThreads, 0, s>>>(m->d, p, cf, d);
+      }
       break;
+    }
   }
 }
 

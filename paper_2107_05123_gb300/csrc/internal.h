@@ -110,6 +110,15 @@ struct chns_mesh {
     bool on = false, has32 = false;
   };
   mutable MomQState mq;
+  // inverse diagonals of the Schur preconditioner's M and H (constant coefficients: they depend
+  // on the mesh and on sa, sb only), kept between solves; key = (sa_M, sb_M, sa_H, sb_H)
+  struct SchurDiag {
+    void* d[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [FP64, FP32][M, H]
+    double key[2][4] = {};
+    bool valid[2] = {false, false};
+  };
+  mutable SchurDiag sd;
+  mutable double* qvu = nullptr;  // per-point velocity-update terms shared by the step's PP/VU
   int red_blocks = 0;
   int sm_count = 0;
   int device = 0;  // CUDA device current at chns_mesh_create (holds every device table)
@@ -234,9 +243,13 @@ chns_status residual_ch(const chns_mesh* m, const chns_params* prm, const double
                         const double* const u[3], double* f, cudaStream_t s);
 chns_status rhs_momentum(const chns_mesh* m, const chns_params* prm, const chns_coef* c,
                          const double* const uk[3], const double* pk, double* b, cudaStream_t s);
+// qvu (optional, 24 n_elem doubles): also store the velocity update's per-point terms
 chns_status rhs_poisson(const chns_mesh* m, const chns_params* prm, const chns_coef* c,
                         const double* const v[3], const double* const uk[3], const double* pk,
-                        double* b, cudaStream_t s);
+                        double* b, cudaStream_t s, double* qvu = nullptr);
+// the velocity-update right-hand side from the terms rhs_poisson stored in qvu
+chns_status rhs_vu_from(const chns_mesh* m, const chns_params* prm, const double* qvu,
+                        const double* pk, const double* pn, double* b, cudaStream_t s);
 chns_status rhs_vu(const chns_mesh* m, const chns_params* prm, const chns_coef* c,
                    const double* const v[3], const double* const uk[3], const double* pk,
                    const double* pn, double* b, cudaStream_t s);

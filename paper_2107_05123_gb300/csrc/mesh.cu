@@ -142,6 +142,9 @@ void free_mesh(chns_mesh* m) {
   dfree(w.md_part);
   dfree(m->mq.qd64);
   dfree(m->mq.qd32);
+  for (int p = 0; p < 2; ++p)
+    for (int k = 0; k < 2; ++k) dfree(m->sd.d[p][k]);
+  dfree(m->qvu);
   if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
   delete m;
 }

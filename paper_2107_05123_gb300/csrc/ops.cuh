@@ -532,6 +532,8 @@ struct MomQK {
   const AccumT<T>* qd = nullptr;  // FP64 data for double-float
   int64_t ne = 0, e = 0;
   __device__ __forceinline__ void setup(const T[NF][8], const Geo<T>&, const DevParams&) {}
+  __device__ __forceinline__ void load(const MeshDev&, const DevParams&, const CoefArgs<C>&,
+                                       const int[8], const Geo<T>&) {}
   __device__ __forceinline__ void bind(const void* q, int64_t n_elem, int64_t elem) {
     qd = static_cast<const AccumT<T>*>(q);
     ne = n_elem;

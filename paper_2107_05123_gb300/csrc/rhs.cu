@@ -275,10 +275,12 @@ struct ProjFields {
 
 // ---- pressure-Poisson right-hand side (Def. weak_VMS_disc_pp_vel, scalar test q):
 //   -(2/dt)(q, div v) - (2/dt)(grad q, tau R_m / rho~) + (grad q, grad p_k / rho~)
+// With qvu, the velocity update's per-point terms J (rho~ v_i - tau R_m,i) (the same R_m) are
+// stored as well, qvu[(q * 3 + i) * n_elem + e], for k_rhs_vu_q.
 template <class A>
 __global__ void __launch_bounds__(kRhsThreads)
 k_rhs_poisson(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 v, Ptr3 uk,
-              const double* __restrict__ pk, double* __restrict__ b) {
+              const double* __restrict__ pk, double* __restrict__ b, double* __restrict__ qvu) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= m.n_elem) return;
   int idx[8];
@@ -297,11 +299,46 @@ k_rhs_poisson(MeshDev m, DevParams p, CoefArgs<double> cf, Ptr3 v, Ptr3 uk,
 #pragma unroll
     for (int d = 0; d < 3; ++d) V[d][Q] = jr * (pg[d] - kt * R[d]);
     s[Q] = -(J * k2 * div);
+    if (qvu)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        qvu[(int64_t)(Q * 3 + i) * m.n_elem + e] = (double)(J * (c.rho * vv[i] - c.tau * R[i]));
   });
   A r[8];
   interp3(s, r);
   grad_T(V, g, r);
   scatter<A, false>(m, idx, r, b);
+}
+
+// The velocity-update right-hand side from the per-point terms stored by k_rhs_poisson (same
+// v, u_k, p_k and coefficients): only the pressure-difference term is evaluated here.
+__global__ void __launch_bounds__(kRhsThreads)
+k_rhs_vu_q(MeshDev m, DevParams p, const double* __restrict__ qvu, const double* __restrict__ pk,
+           const double* __restrict__ pn, double* __restrict__ b) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.n_elem) return;
+  int idx[8];
+  load_corners(m, e, idx);
+  const Geo<double> g = geometry<double>(m, e);
+  QpField<double> fd;  // p_new - p_k
+  {
+    double a[8], c0[8];
+    gather<double, false>(m, idx, pn, a);
+    gather<double, false>(m, idx, pk, c0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] -= c0[k];
+    fd.eval_grad(a);
+  }
+  const double jh = g.detJ * p.d.half_dt;
+#pragma unroll 1
+  for (int i = 0; i < 3; ++i) {
+    double s[8], r[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      s[q] = __ldg(qvu + (int64_t)(q * 3 + i) * m.n_elem + e) - jh * fd.grad(q, i, g);
+    interp3(s, r);
+    scatter<double, true>(m, idx, r, b + i * m.n_nodes);
+  }
 }
 
 // ---- velocity-update right-hand side (Def. weak_VMS_disc_vel_update), per component:
@@ -436,12 +473,12 @@ chns_status rhs_momentum(const chns_mesh* m, const chns_params* prm, const chns_
 
 chns_status rhs_poisson(const chns_mesh* m, const chns_params* prm, const chns_coef* c,
                         const double* const v[3], const double* const uk[3], const double* pk,
-                        double* b, cudaStream_t s) {
+                        double* b, cudaStream_t s, double* qvu) {
   const DevParams p = make_dev_params(*prm);
   CHNS_CUDA(cudaMemsetAsync(b, 0, m->d.n_nodes * sizeof(double), s));
   note_launch();
   const Ptr3 v3{{v[0], v[1], v[2]}}, u3{{uk[0], uk[1], uk[2]}};
-  k_rhs_poisson<double><<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, cargs(c), v3, u3, pk, b);
+  k_rhs_poisson<double><<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, cargs(c), v3, u3, pk, b, qvu);
   CHNS_CUDA(cudaGetLastError());
   return CHNS_OK;
 }
@@ -454,6 +491,16 @@ chns_status rhs_vu(const chns_mesh* m, const chns_params* prm, const chns_coef* 
   note_launch();
   const Ptr3 v3{{v[0], v[1], v[2]}}, u3{{uk[0], uk[1], uk[2]}};
   k_rhs_vu<double><<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, cargs(c), v3, u3, pk, pn, b);
+  CHNS_CUDA(cudaGetLastError());
+  return CHNS_OK;
+}
+
+chns_status rhs_vu_from(const chns_mesh* m, const chns_params* prm, const double* qvu,
+                        const double* pk, const double* pn, double* b, cudaStream_t s) {
+  const DevParams p = make_dev_params(*prm);
+  CHNS_CUDA(cudaMemsetAsync(b, 0, 3 * m->d.n_nodes * sizeof(double), s));
+  note_launch();
+  k_rhs_vu_q<<<nblk(m), kRhsThreads, 0, s>>>(m->d, p, qvu, pk, pn, b);
   CHNS_CUDA(cudaGetLastError());
   return CHNS_OK;
 }

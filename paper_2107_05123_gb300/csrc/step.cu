@@ -184,7 +184,8 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
     // ---- pressure Poisson (warm start from p^k)
     {
       Timer t(s);
-      rc = rhs_poisson(m, prm, &cv, vv, uk, st->p, bv, s);
+      if (!m->qvu) CHNS_CUDA(cudaMalloc(&m->qvu, (size_t)24 * m->d.n_elem * sizeof(double)));
+      rc = rhs_poisson(m, prm, &cv, vv, uk, st->p, bv, s, m->qvu);
       if (rc != CHNS_OK) return rc;
       CHNS_CUDA(cudaMemcpyAsync(pnew, st->p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
       rc = krylov_solve(m, CHNS_OP_POISSON, prm, &cv, bv, pnew, &sp->pp, &S.pp[l], s);
@@ -201,7 +202,7 @@ static chns_status step(const chns_mesh* m, chns_state* st, const chns_params* p
     // ---- velocity update
     {
       Timer t(s);
-      rc = rhs_vu(m, prm, &cv, vv, uk, st->p, pnew, bv, s);
+      rc = rhs_vu_from(m, prm, m->qvu, st->p, pnew, bv, s);
       if (rc != CHNS_OK) return rc;
       CHNS_CUDA(cudaMemcpyAsync(un, v, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
       if (has_bc) {
