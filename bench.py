@@ -49,6 +49,9 @@ WORKLOAD = "rayleigh_taylor_levels6-10"
 # DRAM bytes of one launch of the roofline kernel on the headline mesh (ncu
 # dram__bytes_read.sum + dram__bytes_write.sum, summarised under profiles/); --traffic overrides
 APPLY_DRAM_BYTES = 265.2e6  # mean of two launches (ncu capture summarised under profiles/)
+# FP64 flops per element of the standalone FP64 applies (2 DFMA + DADD + DMUL thread
+# instructions per leaf, one ncu capture on the levels 6-9 Rayleigh-Taylor mesh, profiles/)
+FP64_FLOPS_PER_ELEM = {"poisson": 423.1, "mass": 517.1, "ch": 1085.0, "momentum": 4582.5}
 # the reference arm's bounded sample of the headline workload: the same interface, box and
 # physics on levels 5-8
 SAMPLE_LEVELS = (5, 8)
@@ -451,6 +454,9 @@ def run_ours(args):
             p: {k: applies[p][k]["ms"] for k in ("poisson", "mass", "ch", "momentum")}
             for p in ("fp32", "fp64")},
         "fp64_peak_tflops": round(f64, 3),
+        "applies_fp64_alu_frac": None if not applies else {
+            k: round(FP64_FLOPS_PER_ELEM[k] * E / (applies["fp64"][k]["ms"] * 1e-3) / (f64 * 1e12), 3)
+            for k in ("poisson", "mass", "ch", "momentum")},
         "rising_drop": drop,
         "learned": learned,
         "cpu_baseline": cpu,
