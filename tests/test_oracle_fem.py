@@ -206,3 +206,44 @@ def test_tau_m_limits():
     GG = 3 * (4 / h ** 2) ** 2
     ref = (4 / co.dt ** 2 + co.C_I * (co.eta(-0.2) / (co.rho(-0.2) * co.Re)) ** 2 * GG) ** -0.5
     assert np.allclose(vs.tau, ref, rtol=1e-14)
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_tau_m_advective_limit_is_half_the_transit_time(axis):
+    """With dt and Re so large that their terms vanish, a uniform velocity U along one axis of a
+    box element gives tau_m = h_d / (2 U): half the time the flow takes to cross the element
+    along that axis (G = diag(4 / h_d^2) on the reference cell [-1, 1]^3). On the (1, 4, 1) box
+    the y sides are 4x longer, so tau_m along y is 4x that along x."""
+    a, l = octree.uniform(2)
+    m = Mesh(a, l, (1.0, 4.0, 1.0))
+    el = fem.Elem(m)
+    co = fem.Coeffs(dict(PRM, dt=1e30, Re=1e30))
+    N = m.n_nodes
+    U = 0.7
+    u = np.zeros((3, N))
+    u[axis] = U
+    vs = fem.VMSState(el, co, np.full(N, 0.3), u, np.zeros(N))
+    h = [0.25, 1.0, 0.25][axis]
+    assert np.allclose(vs.tau, h / (2 * U), rtol=1e-12)
+
+
+def test_tau_m_with_the_diffusive_flux_velocity():
+    """Adding a chemical-potential gradient along the flow: J = -(alpha / Cn) grad mu enters the
+    advective radicand as u.G.J / (rho Pe), i.e. the transit time is taken with u and the
+    diffusive flux velocity J / (rho Pe) together: tau_m = h / (2 sqrt(U (U + J_x / (rho Pe)))).
+    A sign or factor slip in that term moves tau_m by more than the tolerance."""
+    a, l = octree.uniform(2)
+    m = Mesh(a, l)
+    el = fem.Elem(m)
+    co = fem.Coeffs(dict(PRM, dt=1e30, Re=1e30))
+    N = m.n_nodes
+    U, slope, phi0 = 0.7, 0.15, 0.3
+    u = np.zeros((3, N))
+    u[0] = U
+    mu = slope * m.node_xyz[:, 0]
+    vs = fem.VMSState(el, co, np.full(N, phi0), u, mu)
+    Jx = -(co.alpha / co.Cn) * slope
+    rho = co.rho(phi0)
+    ref = 0.25 / (2 * np.sqrt(U * (U + Jx / (rho * co.Pe))))
+    assert abs(Jx / (rho * co.Pe)) > 0.05 * U  # the term matters at this tolerance
+    assert np.allclose(vs.tau, ref, rtol=1e-12)
