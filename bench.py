@@ -809,8 +809,12 @@ def _rt_setup():
     from paper_2107_05123_gb300 import capi
     from paper_2107_05123_gb300.session import Mesh
 
-    w = configs.rayleigh_taylor(6, 10, 0.005) if not os.environ.get("CHNS_BENCH_SMALL") else \
-        configs.rayleigh_taylor(6, 9, 0.005)
+    if os.environ.get("CHNS_BENCH_DROP"):
+        w = configs.rising_drop(5, 8)
+    elif os.environ.get("CHNS_BENCH_SMALL"):
+        w = configs.rayleigh_taylor(6, 9, 0.005)
+    else:
+        w = configs.rayleigh_taylor(6, 10, 0.005)
     mesh = Mesh(w.anchors, w.levels, w.extent)
     f0 = w.init(mesh.node_xyz)
     prm = capi.make_params(w.params.as_dict())
@@ -819,7 +823,8 @@ def _rt_setup():
 
 def run_apply_only(args):
     """Profiling aid: one operator apply (--apply-op, --apply-prec) on the headline mesh, a few
-    launches from a cold L2, with one timing line. CHNS_BENCH_SMALL=1 uses levels 6-9."""
+    launches from a cold L2, with one timing line. CHNS_BENCH_SMALL=1 uses levels 6-9,
+    CHNS_BENCH_DROP=1 the rising drop on levels 5-8."""
     torch, capi, w, mesh, f0, prm = _rt_setup()
     dt = torch.float32 if args.apply_prec == "fp32" else torch.float64
     prec = {"fp32": capi.FP32, "fp64": capi.FP64, "fp64df": capi.FP64_DF}[args.apply_prec]
@@ -877,12 +882,17 @@ def run_pp_only(args):
 
 def run_step_only(args):
     """Profiling aid: the headline path on the headline mesh, `--warmup` untimed steps, then one
-    step inside an NVTX range "timed_step" (for an ncu launch list restricted to that range)."""
+    step inside an NVTX range "timed_step" (for an ncu launch list restricted to that range).
+    With CHNS_BENCH_DROP=1: the rising drop (levels 5-8) with the settings of its bench line
+    (one-level preconditioners, FP32 inside FP64 refinement)."""
     torch, capi, w, mesh, f0, prm = _rt_setup()
     from paper_2107_05123_gb300.session import DeviceState, default_step_params
     mg_pp = capi.chns_mg_create(mesh.handle, degree=2)
     mg_ch = capi.chns_mg_create(mesh.handle, degree=2)
-    sp = rt_step_params(capi, default_step_params, capi.FP32, mg_pp, mg_ch)
+    if os.environ.get("CHNS_BENCH_DROP"):
+        sp = double_float(capi, default_step_params(rtol=1e-8, inner=capi.FP32, pp_check_every=8))
+    else:
+        sp = rt_step_params(capi, default_step_params, capi.FP32, mg_pp, mg_ch)
     ds = DeviceState(dict(phi=f0["phi"], mu=f0["mu"], u=f0["u"], p=f0["p"]))
     for _ in range(args.warmup):
         capi.chns_step(mesh.handle, ds.c, prm, sp)
@@ -899,6 +909,51 @@ def run_step_only(args):
                       "launches": capi.chns_kernel_launches() - l0}))
     capi.chns_mg_destroy(mg_pp)
     capi.chns_mg_destroy(mg_ch)
+
+
+def run_learned_fcg(args):
+    """Profiling aid for the learned correction: the rising drop (levels 5-8), an untrained
+    D = 64 network (seed 3, output scale 1), three flexible-CG pressure solves with it (FP32
+    inside FP64 refinement, at most 16 iterations, host check every 8), the last one inside an
+    NVTX range "fcg"; prints the solve time and one network forward time (CUDA events)."""
+    import torch
+
+    from chns_workloads import configs
+    from paper_2107_05123_gb300 import capi
+    from paper_2107_05123_gb300.session import Mesh
+
+    w = configs.rising_drop(5, 8)
+    mesh = Mesh(w.anchors, w.levels, w.extent)
+    f0 = w.init(mesh.node_xyz)
+    prm = capi.make_params(w.params.as_dict())
+    N = mesh.n_nodes
+    net = capi.chns_learned_create(64, 0, 3)
+    capi.chns_learned_set_output_scale(net, 1.0)
+    phit = torch.as_tensor(f0["phi"], device="cuda")
+    zero3 = [torch.zeros(N, dtype=torch.float64, device="cuda") for _ in range(3)]
+    b = torch.zeros(N, dtype=torch.float64, device="cuda")
+    capi.chns_rhs_poisson(mesh.handle, prm,
+                          capi.make_coef(phit, zero3, torch.as_tensor(f0["mu"], device="cuda")),
+                          zero3, zero3, torch.zeros_like(b), b)
+    solver = capi.make_solver(capi.KSP_FCG, capi.PC_LEARNED, 1e-8, 16, 30, capi.FP32, 1e-6,
+                              check_every=8, learned=net)
+    ms = None
+    for k in range(3):
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        if k == 2:
+            torch.cuda.nvtx.range_push("fcg")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        capi.chns_krylov_solve(mesh.handle, capi.OP_POISSON, prm, capi.make_coef(phit), b, x,
+                               solver, check=False)
+        e1.record()
+        torch.cuda.synchronize()
+        if k == 2:
+            torch.cuda.nvtx.range_pop()
+        ms = e0.elapsed_time(e1)
+    capi.chns_learned_destroy(net)
+    return {"mode": "learned_fcg", "n_nodes": int(N), "ms_16_iterations": round(ms, 3)}
 
 
 def run_breakup(args):
@@ -1053,7 +1108,7 @@ def main():
                     help="octree levels lmin,lmax of the many-drop breakup workload")
     ap.add_argument("--amr-every", type=int, default=2, help="steps between remeshes (amr mode)")
     ap.add_argument("--mode", choices=["bench", "apply", "pp", "step", "learned", "breakup",
-                                       "amr"],
+                                       "amr", "learned_fcg"],
                     default="bench",
                     help="apply / pp: time only one apply / the pressure solve (profiling); "
                          "learned: only the learned-preconditioner part; breakup: the many-drop "
@@ -1071,6 +1126,8 @@ def main():
         print(json.dumps(run_breakup(args)))
     elif args.mode == "amr":
         print(json.dumps(run_amr(args)))
+    elif args.mode == "learned_fcg":
+        print(json.dumps(run_learned_fcg(args)))
     elif args.impl == "reference":
         run_reference(args)
     else:

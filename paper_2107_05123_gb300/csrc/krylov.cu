@@ -1445,7 +1445,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
         if (x_zero) {
           CHNS_CUDA(cudaMemcpyAsync(r64, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         } else {
-          st = apply_op(m, op, prm, coef, x, r64, CHNS_FP64, s);
+          st = apply_op(m, op, prm, coef, x, r64, c.df ? CHNS_FP64_DF : CHNS_FP64, s);
           if (st != CHNS_OK) return st;
           note_launch();
           k_axpby<double><<<vgrid(m, n), kVecThreads, 0, s>>>(1.0, b, -1.0, r64, r64, n);
@@ -1583,7 +1583,7 @@ chns_status krylov_solve(const chns_mesh* m, chns_operator op, const chns_params
       out.rel_residual = last_rn / bnorm;
     } else {
       // true FP64 residual
-      chns_status st2 = apply_op(m, op, prm, coef, x, r64, CHNS_FP64, s);
+      chns_status st2 = apply_op(m, op, prm, coef, x, r64, c.df ? CHNS_FP64_DF : CHNS_FP64, s);
       if (st2 != CHNS_OK) return st2;
       note_launch();
       k_axpby<double><<<vgrid(m, n), kVecThreads, 0, s>>>(1.0, b, -1.0, r64, r64, n);
