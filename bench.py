@@ -168,8 +168,6 @@ def rt_step_params(capi, default_step_params, inner, mg_pp=None, mg_ch=None):
     preconditioner (H^-1 by a V-cycle when mg_ch is given, else 20 inner CG iterations), the
     pressure by flexible CG with a V-cycle when mg_pp is given, else Jacobi-PCG."""
     sp = default_step_params(rtol=1e-8, inner=inner, pp_check_every=8)
-    if inner == capi.FP32:
-        double_float(capi, sp)
     sp.ch.pc = capi.PC_SCHUR
     sp.ch.inner_its = 20
     sp.ch.max_it = 400
@@ -178,6 +176,8 @@ def rt_step_params(capi, default_step_params, inner, mg_pp=None, mg_ch=None):
     if mg_pp is not None:
         sp.pp = capi.make_solver(capi.KSP_FCG, capi.PC_MULTIGRID, 1e-8, 2000, 30, inner, 1e-6,
                                  40, check_every=2, mg=mg_pp)
+    if inner == capi.FP32:
+        double_float(capi, sp)
     return sp
 
 
