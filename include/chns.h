@@ -24,8 +24,12 @@
  *     the FP32 modes; coefficient fields are uint16 bfloat16 for CHNS_FP32_BF16COEF, where the
  *     phase field is stored shifted as bfloat16(1 + phi~) so that the relative error of
  *     rho(phi) stays below 2^-8 even for large density ratios). The
- *     library owns the mesh tables and a device workspace allocated by chns_mesh_create;
- *     nothing is allocated on later calls.
+ *     library owns the mesh tables and a device workspace allocated by chns_mesh_create.
+ *     A few buffers are added to the mesh on first use and kept until chns_mesh_destroy: the
+ *     momentum quadrature data (a momentum solve), the inverse diagonals of the Schur
+ *     preconditioner (a CH solve with CHNS_PC_SCHUR) and the velocity-update terms of chns_step
+ *     (24 doubles per leaf). chns_transfer and chns_mesh_remesh allocate temporaries; the
+ *     multigrid and learned objects own their memory.
  *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream). Applies are
  *     asynchronous. Solves and steps synchronise the stream when they read convergence scalars.
  *   - Errors: no exception crosses the ABI. Every call returns a chns_status; on failure
