@@ -12,6 +12,13 @@ namespace chns {
 
 constexpr int kApplyThreads = 128;
 
+// Coefficient fields the patch kernels gather into shared memory (none for operators that
+// ignore them).
+template <class K>
+constexpr int gathered_fields() {
+  return IgnoresFields<K>::value ? 0 : K::NF;
+}
+
 template <class K, class T, class S, class C>
 __global__ void __launch_bounds__(kApplyThreads) k_apply(MeshDev m, DevParams p, CoefArgs<C> cf,
                                                          const S* __restrict__ x, S* __restrict__ y) {
@@ -48,7 +55,7 @@ __global__ void __launch_bounds__(kPatchElems, K::MIN_CTAS)
 k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S* __restrict__ y,
               double* __restrict__ S_cg, int par, int fcg, const S* __restrict__ zcg,
               S* __restrict__ pout) {
-  constexpr int NC = K::NC, NF = K::NF;
+  constexpr int NC = K::NC, NF = gathered_fields<K>();
   // shared accumulators: the arithmetic type, or FP64 for double-float (same size)
   using U = AccumT<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -143,11 +150,11 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
                        (int)(lp.y >> 16),    (int)(lp.z & 0xffff), (int)(lp.z >> 16),
                        (int)(lp.w & 0xffff), (int)(lp.w >> 16)};
     const Geo<T> g = level_geometry<T>(m, lev);
-    T fe[NF][8];
+    T fe[K::NF][8];  // fields the operator ignores are not gathered (zero here)
 #pragma unroll
-    for (int f = 0; f < NF; ++f)
+    for (int f = 0; f < K::NF; ++f)
 #pragma unroll
-      for (int a = 0; a < 8; ++a) fe[f][a] = fs[f * kPatchSlots + sl[a]];
+      for (int a = 0; a < 8; ++a) fe[f][a] = f < NF ? fs[f * kPatchSlots + sl[a]] : T(0);
     K k;
     k.setup(fe, g, p);
     if constexpr (K::QDATA) k.bind(cf.qd, m.n_elem, e);
@@ -213,7 +220,7 @@ k_apply_patch(MeshDev m, DevParams p, CoefArgs<C> cf, const S* __restrict__ x, S
 
 template <class K, class T>
 constexpr size_t patch_smem() {
-  return (size_t)(2 * K::NC + K::NF) * kPatchSlots * sizeof(T);
+  return (size_t)(2 * K::NC + gathered_fields<K>()) * kPatchSlots * sizeof(T);
 }
 
 // Launch the patch apply, raising the dynamic shared-memory limit once per instantiation.
@@ -259,7 +266,7 @@ constexpr int kPqStage = 128;  // hanging slots per patch whose parents are stag
 
 template <class K, class T, bool CGP>
 constexpr int stream_stage_arrays() {
-  return (CGP ? 2 : 1) * K::NC + K::NF;
+  return (CGP ? 2 : 1) * K::NC + gathered_fields<K>();
 }
 template <class K, class T, bool CGP>
 constexpr size_t stream_smem() {
@@ -275,7 +282,7 @@ __global__ void __launch_bounds__(kPatchElems, K::STREAM_CTAS)
 k_apply_stream(MeshDev m, DevParams p, CoefArgs<T> cf, const T* __restrict__ x, T* __restrict__ y,
                double* __restrict__ S_cg, int par, int fcg, const T* __restrict__ zcg,
                T* __restrict__ pout) {
-  constexpr int NC = K::NC, NF = K::NF, NA = stream_stage_arrays<K, T, CGP>();
+  constexpr int NC = K::NC, NF = gathered_fields<K>(), NA = stream_stage_arrays<K, T, CGP>();
   static_assert(!K::QDATA, "per-element quadrature data is not staged by this kernel");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* vb = reinterpret_cast<T*>(smem_raw);                             // [2][NA][kPatchSlots]
@@ -431,11 +438,11 @@ k_apply_stream(MeshDev m, DevParams p, CoefArgs<T> cf, const T* __restrict__ x, 
                          (int)(lp.y >> 16),    (int)(lp.z & 0xffff), (int)(lp.z >> 16),
                          (int)(lp.w & 0xffff), (int)(lp.w >> 16)};
       const Geo<T> g = level_geometry<T>(m, lev);
-      T fe[NF][8];
+      T fe[K::NF][8];  // fields the operator ignores are not gathered (zero here)
 #pragma unroll
-      for (int f = 0; f < NF; ++f)
+      for (int f = 0; f < K::NF; ++f)
 #pragma unroll
-        for (int a = 0; a < 8; ++a) fe[f][a] = fs[f * kPatchSlots + sl[a]];
+        for (int a = 0; a < 8; ++a) fe[f][a] = f < NF ? fs[f * kPatchSlots + sl[a]] : T(0);
       K kk;
       kk.setup(fe, g, p);
       T xin[NC][8];

@@ -170,6 +170,7 @@ struct ShiftK {
   static constexpr bool DIR = false;
   static constexpr bool DIAG_PER_COMP = false;
   static constexpr int NF = 1;  // (phi~ gathered but unused: the patch kernel's layout)
+  static constexpr bool IGNORES_FIELDS = true;
   // Constant coefficients on a box: the 2x2x2 Gauss rule is exact, and the element matrices are
   // Kronecker products of the 1D Q1 matrices m = h/6 [[2, 1], [1, 2]] and k = 1/h [[1, -1],
   // [-1, 1]]: M_e = m x m x m, K_e = k x m x m + m x k x m + m x m x k. With P(a, b) = (2a + b,
@@ -615,5 +616,13 @@ template <class K, class = void>
 struct HasEnergy : std::false_type {};
 template <class K>
 struct HasEnergy<K, std::void_t<decltype(K::ENERGY)>> : std::bool_constant<K::ENERGY> {};
+
+// Operators whose element kernel never reads the coefficient fields it is handed (the shifted
+// operator's coefficients are constants): the persistent apply gathers none for them.
+template <class K, class = void>
+struct IgnoresFields : std::false_type {};
+template <class K>
+struct IgnoresFields<K, std::void_t<decltype(K::IGNORES_FIELDS)>>
+    : std::bool_constant<K::IGNORES_FIELDS> {};
 
 }  // namespace chns
