@@ -505,7 +505,10 @@ def run_drop(args, flush_l2, barrier):
 def run_learned(args):
     """The learned coarse correction on the 8-drop workload (levels 5-8, drops of radius
     0.05-0.12, Cn 0.01, density ratio 1000): training pairs from the pressure-Poisson solves of
-    `--learned-steps` time steps (iterates of FP64 Jacobi-PCG, every 8th, at most 24 per solve),
+    `--learned-steps` time steps (iterates of FP64 Jacobi-PCG, every `--learned-collect-every`th,
+    at most `--learned-collect-max` per solve, into a replay buffer of `--learned-capacity`
+    pairs; if a step fails, collection stops and the comparison starts from the state of the
+    last step that succeeded),
     energy-norm training on the GPU, then the pressure-Poisson solves of one more step from the
     same state in mixed precision with Jacobi-PCG, Chebyshev-PCG (degree 3) and FCG + learned
     correction, and the same step on the all-FP64 path (Jacobi). Returns the summary object of the
@@ -522,7 +525,7 @@ def run_learned(args):
     prm = capi.make_params(w.params.as_dict())
     f0 = w.init(mesh.node_xyz)
     D = args.learned_grid
-    net = capi.chns_learned_create(D, 4096, 1)
+    net = capi.chns_learned_create(D, args.learned_capacity, 1)
 
     def params(pp=None, collect=None):
         sp = default_step_params(rtol=1e-8, inner=capi.FP32, pp_check_every=8)
@@ -530,22 +533,26 @@ def run_learned(args):
         if pp is not None:
             sp.pp = pp
         if collect is not None:
-            sp.collect, sp.collect_every, sp.collect_max = collect, 8, 24
+            sp.collect, sp.collect_every = collect, args.learned_collect_every
+            sp.collect_max = args.learned_collect_max
         return sp
 
     ds = DeviceState(dict(phi=f0["phi"], mu=f0["mu"], u=f0["u"], p=f0["p"]))
     t0 = time.perf_counter()
     steps_done, step_error = 0, None
-    snap = ds.host()
+    snap = prev = ds.host()
     for _ in range(args.learned_steps):
         try:
             capi.chns_step(mesh.handle, ds.c, prm, params(collect=net))
-        except capi.ChnsError as e:  # a failed step leaves the state unusable: keep the last one
+        except capi.ChnsError as e:
+            # a failed step leaves the state unusable; the step from `snap` is the one that
+            # failed, so the comparison below starts from the state one step earlier, from which
+            # a step is known to succeed
             step_error = str(e)
-            ds = DeviceState(snap)
+            snap = prev
             break
         steps_done += 1
-        snap = ds.host()
+        prev, snap = snap, ds.host()
     torch.cuda.synchronize()
     t_collect = time.perf_counter() - t0
     pairs = capi.chns_learned_num_samples(net)
@@ -1100,6 +1107,12 @@ def main():
     ap.add_argument("--learned-steps", type=int, default=3,
                     help="time steps whose pressure-Poisson solves give the training pairs")
     ap.add_argument("--learned-iters", type=int, default=6000, help="training iterations")
+    ap.add_argument("--learned-capacity", type=int, default=4096,
+                    help="replay buffer of the learned mode, in pairs (7.3 MB each on the 8 drops)")
+    ap.add_argument("--learned-collect-max", type=int, default=24,
+                    help="training pairs taken from one pressure solve at most")
+    ap.add_argument("--learned-collect-every", type=int, default=8,
+                    help="iterate stride of the training pairs within one pressure solve")
     ap.add_argument("--learned-lr", type=float, default=3e-4)
     ap.add_argument("--learned-grid", type=int, default=64, help="grid size D of the network")
     ap.add_argument("--apply-op", choices=["poisson", "mass", "ch", "momentum"], default="poisson")
