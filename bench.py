@@ -522,7 +522,10 @@ def run_learned(args):
     t_all = time.perf_counter()
     w = configs.many_drops(seed=0, n=8, rmin=0.05, rmax=0.12, lmin=5, lmax=8, Cn=0.01)
     mesh = Mesh(w.anchors, w.levels, w.extent)
-    prm = capi.make_params(w.params.as_dict())
+    pd = w.params.as_dict()
+    if args.learned_dt:
+        pd["dt"] = args.learned_dt
+    prm = capi.make_params(pd)
     f0 = w.init(mesh.node_xyz)
     D = args.learned_grid
     net = capi.chns_learned_create(D, args.learned_capacity, 1)
@@ -593,7 +596,7 @@ def run_learned(args):
             rel_residual=[st.pp[l].rel_residual for l in range(2)])
     capi.chns_learned_destroy(net)
     small = _learned_small_drops(args)
-    full = {"workload": "drops8_levels5-8", "n_elem": int(mesh.n_elem),
+    full = {"workload": "drops8_levels5-8", "dt": pd["dt"], "n_elem": int(mesh.n_elem),
             "n_nodes": int(mesh.n_nodes), "grid": D, "channels": 16, "levels": 4,
             "collect_steps": steps_done, "collect_step_error": step_error, "pairs": int(pairs),
             "train_iterations": args.learned_iters, "lr": args.learned_lr,
@@ -1111,6 +1114,8 @@ def main():
                     help="replay buffer of the learned mode, in pairs (7.3 MB each on the 8 drops)")
     ap.add_argument("--learned-collect-max", type=int, default=24,
                     help="training pairs taken from one pressure solve at most")
+    ap.add_argument("--learned-dt", type=float, default=None,
+                    help="time step of the learned mode's workload (default: its own, 5e-4)")
     ap.add_argument("--learned-collect-every", type=int, default=8,
                     help="iterate stride of the training pairs within one pressure solve")
     ap.add_argument("--learned-lr", type=float, default=3e-4)
