@@ -579,10 +579,15 @@ __global__ void __launch_bounds__(kApplyThreads) k_diag(MeshDev m, DevParams p, 
   K k;
   k.load(m, p, cf, idx, g);
   if constexpr (K::QDATA) k.bind(cf.qd, m.n_elem, e);
+  // node references of the 8 corners (a regular corner itself, a hanging corner its 2 or 4
+  // parents) and their weights, read once
+  int rf[8][4];
+  double wt[8][4];
+  for (int a = 0; a < 8; ++a)
+    for (int s = 0; s < 4; ++s) rf[a][s] = corner_ref(m, idx[a], s, wt[a][s]);
   for (int a = 0; a < 8; ++a) {
     for (int s = 0; s < 4; ++s) {
-      double w;
-      int ref = corner_ref(m, idx[a], s, w);
+      const int ref = rf[a][s];
       if (ref < 0) continue;
       if (K::DIR && (ref & kDirBit)) continue;
       const int j = ref & kIdxMask;
@@ -591,8 +596,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_diag(MeshDev m, DevParams p, 
       for (int a2 = 0; a2 <= a && !seen; ++a2)
         for (int s2 = 0; s2 < 4; ++s2) {
           if (a2 == a && s2 >= s) break;
-          double w2;
-          int r2 = corner_ref(m, idx[a2], s2, w2);
+          const int r2 = rf[a2][s2];
           if (r2 >= 0 && (r2 & kIdxMask) == j) {
             seen = true;
             break;
@@ -603,9 +607,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_diag(MeshDev m, DevParams p, 
       for (int b = 0; b < 8; ++b) {
         T acc = T(0);
         for (int s2 = 0; s2 < 4; ++s2) {
-          double w2;
-          int r2 = corner_ref(m, idx[b], s2, w2);
-          if (r2 >= 0 && (r2 & kIdxMask) == j) acc += T(w2);
+          const int r2 = rf[b][s2];
+          if (r2 >= 0 && (r2 & kIdxMask) == j) acc += T(wt[b][s2]);
         }
         lv[b] = acc;
       }
